@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers and lays them out; it holds none of the
+simulator's arithmetic, so both the CUDA path and the FP64 oracle can use it.
+Every floating-point value it returns is exactly representable in float32
+(rounded once, then widened), so the two sides start from identical inputs.
+
+Recipe (all draws from numpy PCG64):
+  * lanes are filled head first: the head of every lane sits at p = 0, each
+    follower is placed behind its leader with a bumper-to-bumper gap drawn
+    from U[20, 40] m; every vehicle is 5 m long;
+  * initial speeds U[10, 30] m/s;
+  * true parameters v0 U[25, 35], T U[1, 2], s0 U[1.5, 3], a_max U[0.8, 2],
+    b U[1, 3], delta = 4;
+  * observation noise N(0, 0.5^2) m, drawn here and added by the caller to a
+    trajectory it computes itself.
+The paper's own datasets (NGSIM US-101, a non-public Singapore set, Waymo
+Open Motion) are not available; these inputs stand in for them.
+"""
+import numpy as np
+
+SEED_BASE = 20241216
+
+PARAM_NAMES = ("v0", "T", "s0", "a_max", "b", "delta")
+
+# Ranges of the true parameters (v0, T, s0, a_max, b); delta fixed at 4.
+TRUE_RANGES = ((25.0, 35.0), (1.0, 2.0), (1.5, 3.0), (0.8, 2.0), (1.0, 3.0))
+DELTA = 4.0
+
+# Zero-knowledge initial guess of Sec. IV-A: a_max 10, a_pref (b) 2, T_pref 1,
+# s_min (s0) 5, v_targ (v0) 50.  Order (v0, T, s0, a_max, b, delta).
+PLAIN_INIT = (50.0, 1.0, 5.0, 10.0, 2.0, 4.0)
+
+# Boxes of Sec. IV-A in (v0, T, s0, a_max, b) order.  The a_max box is widened
+# from [5, 10] to [0.5, 10] so that it contains the true range U[0.8, 2].
+BOX_LO = (20.0, 0.1, 1.0, 0.5, 0.1)
+BOX_HI = (60.0, 5.0, 10.0, 10.0, 5.0)
+
+A_MIN = -10.0
+LENGTH = 5.0
+GAP_RANGE = (20.0, 40.0)
+SPEED_RANGE = (10.0, 30.0)
+NOISE_STD = 0.5
+
+
+def f32(a):
+    """Round to float32 and widen back to float64."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rng_for(config_index, salt=0):
+    return np.random.Generator(np.random.PCG64(SEED_BASE + config_index + 1000 * salt))
+
+
+def lane_offsets(counts):
+    counts = np.asarray(counts, dtype=np.int64)
+    off = np.zeros(len(counts) + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    return off.astype(np.int32)
+
+
+def make_scene(counts, rng):
+    """Lanes with the given vehicle counts, head first within each lane.
+
+    Returns a dict with lane_off (int32 [L+1]), length, p_init, v_init
+    (float64 [N], float32-exact) and theta_true (float64 (6, N)).
+    """
+    counts = np.asarray(counts, dtype=np.int64)
+    lane_off = lane_offsets(counts)
+    N = int(lane_off[-1])
+    length = np.full(N, LENGTH)
+    gaps = rng.uniform(*GAP_RANGE, size=N)
+    v_init = rng.uniform(*SPEED_RANGE, size=N)
+    # positions: cumulative placement behind the head of each lane
+    p = np.empty(N)
+    for_heads = np.zeros(N, dtype=bool)
+    for_heads[lane_off[:-1][counts > 0]] = True
+    step = np.where(for_heads, 0.0, gaps + LENGTH)
+    csum = np.cumsum(step)
+    lane_start_sum = np.repeat(csum[lane_off[:-1][counts > 0]], counts[counts > 0])
+    p[:] = -(csum - lane_start_sum)
+    theta = np.empty((6, N))
+    for q, (lo, hi) in enumerate(TRUE_RANGES):
+        theta[q] = rng.uniform(lo, hi, size=N)
+    theta[5] = DELTA
+    return dict(lane_off=lane_off, length=f32(length), p_init=f32(p), v_init=f32(v_init),
+                theta_true=f32(theta))
+
+
+def plain_init(N):
+    th = np.empty((6, N))
+    for q, x in enumerate(PLAIN_INIT):
+        th[q] = x
+    return th
+
+
+def noise(rng, n_obs, N):
+    return rng.normal(0.0, NOISE_STD, size=(n_obs, N))
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def config0():
+    """Plain fit, small: 10 lanes x 100 vehicles, 100 steps, dt 0.1 s, all
+    steps observed."""
+    rng = rng_for(0)
+    sc = make_scene([100] * 10, rng)
+    sc.update(K=100, dt=0.1, obs_stride=1, noise=noise(rng, 100, 1000), name="10x100 K=100")
+    return sc
+
+
+def config1(n_lanes=20000, per_lane=100, K=1000):
+    """Paper scale: 20,000 lanes x 100 vehicles (2M), 1,000 steps, dt 0.1 s."""
+    rng = rng_for(1)
+    sc = make_scene([per_lane] * n_lanes, rng)
+    sc.update(K=K, dt=0.1, obs_stride=1, name="%dx%d K=%d" % (n_lanes, per_lane, K))
+    return sc
+
+
+def config2_tables(n_scen=4096, rng=None):
+    """Uneven scenarios: lanes U[1,64], vehicles per lane U[2,200], horizons
+    U[50,500], targets observed every 10th step."""
+    rng = rng if rng is not None else rng_for(2)
+    n_lanes = rng.integers(1, 65, size=n_scen)
+    K = rng.integers(50, 501, size=n_scen)
+    counts = [rng.integers(2, 201, size=int(L)) for L in n_lanes]
+    return n_lanes, K, counts
+
+
+def unsorted_view(sc, rng):
+    """The same vehicles in a random order, with lane ids, as a layout step
+    would receive them."""
+    lane_off = sc["lane_off"]
+    N = int(lane_off[-1])
+    lane_id = np.repeat(np.arange(len(lane_off) - 1, dtype=np.int32), np.diff(lane_off))
+    order = rng.permutation(N)
+    return dict(lane_id=lane_id[order], p_init=sc["p_init"][order], order=order)
