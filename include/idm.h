@@ -1,0 +1,206 @@
+/*
+ * libidm -- GB300 (sm_103a) library for the parallel differentiable
+ * Intelligent Driver Model simulator of arXiv 2412.16750
+ * ("Gradient-based Trajectory Optimization with Parallelized Differentiable
+ * Traffic Simulation").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Vehicle order.  Vehicles are stored lane by lane, each lane head first, so
+ *   the leader h(i) of a vehicle i that is not a lane head is i-1
+ *   (Sec. III-A).  idm_layout produces this order from unsorted input.
+ * Memory.  Every array argument is DEVICE memory owned by the caller unless
+ *   the comment says "host".  The library never frees caller memory.  The
+ *   context owns its workspace (segment tables, initial gaps, checkpoints,
+ *   reduction scratch, Adam moments), grown on demand up to the cap given to
+ *   idm_ctx_create.
+ * Streams.  Every call is asynchronous on the given cudaStream_t (passed as
+ *   void*; NULL = legacy default stream).  Outputs are valid once the stream
+ *   has reached the call.  One context must not be used by two streams at
+ *   the same time.
+ * Floating point.  State and parameters are float32 (IEEE binary32); loss
+ *   values are float64.  Positions are integrated as a float32 pair
+ *   (displacement + rounding error) so that they keep ~1e-5 m over 1,000
+ *   steps.
+ * Parameters.  idm_params_t holds six arrays of length N in the paper's
+ *   notation of Eq. 1-2: v0 = v_targ (desired speed), T = T_pref (time
+ *   headway), s0 = s_min (minimum gap), a_max, b = a_pref (comfortable
+ *   deceleration), delta (free-road exponent).
+ * Errors.  Every entry point returns IDM_OK or one of the codes below and
+ *   never aborts.  Argument errors are detected on the host before anything
+ *   is launched.  Conditions only the device can see (a lane longer than the
+ *   configured maximum, a non-finite state, a malformed lane_off) set bits
+ *   of the context's status word; idm_status synchronises the stream and
+ *   reports them.  idm_last_error returns a description of the last error.
+ */
+#ifndef IDM_H_
+#define IDM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IDM_OK 0
+#define IDM_ERR_ARG 1          /* bad argument (null pointer, size, range) */
+#define IDM_ERR_WORKSPACE 2    /* workspace would exceed the context's cap */
+#define IDM_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define IDM_ERR_NONFINITE 4    /* device status: non-finite state or gradient */
+#define IDM_ERR_TIMEOUT 5      /* reserved for bounded device waits */
+#define IDM_ERR_LANE 6         /* device status: lane longer than max_lane or lane_off malformed */
+
+/* Device status bits reported by idm_status. */
+#define IDM_STATUS_LANE_TOO_LONG 1u
+#define IDM_STATUS_BAD_LANE_OFF 2u
+#define IDM_STATUS_NONFINITE 4u
+
+/* Gap floor (m): the gap is max(p_h - p - length_h, IDM_GAP_FLOOR), with zero
+ * derivative below the floor.  The paper is silent on gaps <= 0. */
+#define IDM_GAP_FLOOR 0.1f
+
+typedef struct idm_ctx idm_ctx_t;
+
+/* Lane structure of a scene in head-first order.
+ *   lane_off[n_lanes+1] (device): lane l holds vehicles
+ *     [lane_off[l], lane_off[l+1]); lane_off[0] = 0, lane_off[n_lanes] =
+ *     n_vehicles, non-decreasing.  Empty lanes are allowed.
+ *   length[n_vehicles] (device): vehicle lengths (m); the gap of a follower
+ *     subtracts its LEADER's length (Sec. III-A).
+ *   max_lane (host value): an upper bound on the longest lane, used to pick
+ *     the kernel variant; at most idm_max_lane_supported().  A lane longer
+ *     than max_lane is not simulated and sets IDM_STATUS_LANE_TOO_LONG. */
+typedef struct {
+    int32_t n_lanes;
+    int32_t n_vehicles;
+    int32_t max_lane;
+    const int32_t *lane_off;
+    const float *length;
+} idm_scene_t;
+
+/* Per-vehicle IDM parameters (device, each [n_vehicles]). */
+typedef struct {
+    float *v0, *T, *s0, *a_max, *b, *delta;
+} idm_params_t;
+
+/* Simulation settings shared by all vehicles of a call. */
+typedef struct {
+    int32_t K;       /* number of Euler steps, >= 1 (Eq. 3) */
+    float dt;        /* step length (s), > 0 */
+    float a_min;     /* maximum deceleration bound of Sec. III-C, < 0 (paper: -10) */
+} idm_sim_t;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  workspace_cap_bytes bounds
+ * the device memory the context may hold (0 = no bound).  *ctx receives the
+ * handle.  Returns IDM_ERR_ARG if ctx is NULL. */
+int idm_ctx_create(idm_ctx_t **ctx, size_t workspace_cap_bytes);
+
+/* Release the context and its workspace (synchronises the device first).
+ * NULL is accepted. */
+int idm_ctx_destroy(idm_ctx_t *ctx);
+
+/* Description of the last error on this context (static storage owned by
+ * the context; valid until the next call on it). */
+const char *idm_last_error(const idm_ctx_t *ctx);
+
+/* Synchronise `stream` and report the device status word accumulated since
+ * the last idm_status call, then clear it.  *flags (host, may be NULL)
+ * receives the IDM_STATUS_* bits.  Returns IDM_ERR_LANE or IDM_ERR_NONFINITE
+ * when the matching bits are set, IDM_OK otherwise. */
+int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
+
+/* Tuning knobs.  vpt: vehicles per thread (1, 2, 4 or 8; 0 = choose from
+ * max_lane); ckpt_interval: steps between stored checkpoints of the adjoint
+ * (1..64; default 16); warps_per_block: 1..8 (default 8). */
+int idm_set_tuning(idm_ctx_t *ctx, int vpt, int ckpt_interval, int warps_per_block);
+
+/* Longest lane the library can simulate (vehicles). */
+int idm_max_lane_supported(void);
+
+/* Bytes of workspace a loss/gradient call on this scene would hold. */
+size_t idm_workspace_bytes(const idm_ctx_t *ctx, const idm_scene_t *scene, const idm_sim_t *sim);
+
+/* ---- scene layout (Sec. III-A: the leader is the vehicle directly ahead in
+ * the same lane) ------------------------------------------------------- */
+
+/* Order N unsorted vehicles by (lane ascending, position descending,
+ * original index ascending).
+ *   lane_id[N] (device, int32 in [0, n_lanes)), pos[N] (device, float32).
+ *   perm[N] (device out): perm[j] = original index of the j-th vehicle.
+ *   lane_off[n_lanes+1] (device out): lane CSR offsets.
+ *   *max_lane_out (device out, int32, may be NULL): longest lane.
+ * Lane ids outside [0, n_lanes) set IDM_STATUS_BAD_LANE_OFF and those
+ * vehicles are dropped from the counts.  Lanes longer than 4096 vehicles set
+ * IDM_STATUS_LANE_TOO_LONG and are left unsorted within the lane. */
+int idm_layout(idm_ctx_t *ctx, int32_t N, int32_t n_lanes, const int32_t *lane_id,
+               const float *pos, int32_t *perm, int32_t *lane_off, int32_t *max_lane_out,
+               void *stream);
+
+/* dst[j] = src[perm[j]] for j < N, for `count` float32 arrays given as
+ * arrays of device pointers in HOST memory (srcs[count], dsts[count]). */
+int idm_gather(idm_ctx_t *ctx, int32_t N, const int32_t *perm, int count,
+               const float *const *srcs, float *const *dsts, void *stream);
+
+/* ---- forward (Eq. 1-3 with the Sec. III-C bounds) -------------------- */
+
+/* Simulate sim->K steps from (p_init, v_init).
+ *   traj[(K+1)*N] (device out, may be NULL): positions, time-major
+ *     (row k = step k, row 0 = p_init).
+ *   vtraj[(K+1)*N] (device out, may be NULL): speeds, time-major.
+ * v_init must be >= 0. */
+int idm_forward(idm_ctx_t *ctx, const idm_scene_t *scene, const idm_params_t *params,
+                const float *p_init, const float *v_init, const idm_sim_t *sim,
+                float *traj, float *vtraj, void *stream);
+
+/* ---- adjoint from trajectory gradients -------------------------------- */
+
+/* Reverse-time adjoint of idm_forward for a scalar loss L whose gradients
+ * with respect to the simulated trajectory are given densely:
+ *   gP[(K+1)*N] (device): dL/dP, row k = step k (row 0 is the direct
+ *     dependence on p_init); gV[(K+1)*N] (device, may be NULL): dL/dV.
+ *   grad (device out, each [N], overwritten; any member may be NULL):
+ *     dL/dtheta for the six parameters.
+ *   grad_p_init, grad_v_init (device out [N], may be NULL).
+ * The trajectory is recomputed from checkpoints taken every ckpt_interval
+ * steps, so no trajectory input is needed. */
+int idm_backward(idm_ctx_t *ctx, const idm_scene_t *scene, const idm_params_t *params,
+                 const float *p_init, const float *v_init, const idm_sim_t *sim,
+                 const float *gP, const float *gV, idm_params_t *grad, float *grad_p_init,
+                 float *grad_v_init, void *stream);
+
+/* ---- fused squared-error loss and gradient (Sec. IV-A) --------------- */
+
+/* L = sum_i (1/n_obs) sum_{j=1..n_obs} (P[j*s, i] - targets[j-1, i])^2 with
+ * n_obs = floor(K / s), s = obs_stride >= 1 (n_obs = 0 gives L = 0).
+ *   targets[n_obs*N] (device): observed positions, row j-1 = step j*s.
+ *   loss_out (device, double, may be NULL): receives L.
+ *   grad (device out, members may be NULL): dL/dtheta.
+ *   grad_p_init, grad_v_init (device out, may be NULL). */
+int idm_loss_grad(idm_ctx_t *ctx, const idm_scene_t *scene, const idm_params_t *params,
+                  const float *p_init, const float *v_init, const idm_sim_t *sim,
+                  const float *targets, int32_t obs_stride, double *loss_out,
+                  idm_params_t *grad, float *grad_p_init, float *grad_v_init, void *stream);
+
+/* ---- gradient-based fit (Sec. IV-A, Sec. V-B) ------------------------ */
+
+/* n_iter iterations of {forward with loss, adjoint, Adam on (v0, T, s0,
+ * a_max, b), projection onto [box_lo[q], box_hi[q]]}; delta is not changed.
+ * The learning rate of iteration t (0-based) is lr0 + (lr1 - lr0) t /
+ * (n_iter - 1); Adam uses beta1 0.9, beta2 0.999, eps 1e-8, zero initial
+ * moments.  One iteration is captured in a CUDA graph and replayed.
+ *   params (device, in/out): initial guess in, fitted values out.
+ *   box_lo, box_hi (HOST, [5], order v0, T, s0, a_max, b).
+ *   loss_hist (device out, double [n_iter], may be NULL): loss at the
+ *     parameters before update t. */
+int idm_fit(idm_ctx_t *ctx, const idm_scene_t *scene, idm_params_t *params,
+            const float *p_init, const float *v_init, const idm_sim_t *sim,
+            const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
+            const float *box_lo, const float *box_hi, double *loss_hist, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDM_H_ */

@@ -1,0 +1,192 @@
+"""PyTorch-facing API over libidm: device memory and streams come from torch,
+every step of the simulation and its adjoint runs in libidm's kernels.
+
+    ctx = Context()
+    scene = Scene.from_lane_off(lane_off, length)            # CUDA tensors
+    traj = IdmFunction.apply(theta, p_init, v_init, scene, K, dt)  # (K+1, N)
+    traj.sum().backward()                                      # idm_backward
+
+``theta`` is a (6, N) float32 tensor with rows (v0, T, s0, a_max, b, delta),
+the paper's (v_targ, T_pref, s_min, a_max, a_pref, delta) of Eq. 1-2.
+"""
+from dataclasses import dataclass
+
+import torch
+
+from . import lib
+
+PARAM_NAMES = ("v0", "T", "s0", "a_max", "b", "delta")
+
+
+class Context:
+    """Owns an idm_ctx_t (workspace on the current device)."""
+
+    def __init__(self, workspace_cap_bytes=0, vpt=0, ckpt_interval=16, warps_per_block=8):
+        self.handle = lib.idm_ctx_create(workspace_cap_bytes)
+        self.set_tuning(vpt, ckpt_interval, warps_per_block)
+
+    def set_tuning(self, vpt=0, ckpt_interval=16, warps_per_block=8):
+        lib.idm_set_tuning(self.handle, vpt, ckpt_interval, warps_per_block)
+        self.tuning = (vpt, ckpt_interval, warps_per_block)
+
+    def status(self, stream=None):
+        rc, flags = lib.idm_status(self.handle, stream or torch.cuda.current_stream())
+        return rc, flags
+
+    def check_status(self):
+        rc, flags = self.status()
+        if rc != lib.IDM_OK:
+            raise lib.IdmError(rc, lib.idm_last_error(self.handle))
+        return flags
+
+    def close(self):
+        if self.handle is not None:
+            lib.idm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context():
+    dev = torch.cuda.current_device()
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context()
+    return _default_ctx[dev]
+
+
+@dataclass
+class Scene:
+    lane_off: torch.Tensor  # int32 [L+1], CUDA
+    length: torch.Tensor    # float32 [N], CUDA
+    max_lane: int
+
+    @staticmethod
+    def from_lane_off(lane_off, length, max_lane=None):
+        lane_off = lane_off.to(device="cuda", dtype=torch.int32).contiguous()
+        length = length.to(device="cuda", dtype=torch.float32).contiguous()
+        if max_lane is None:
+            max_lane = int((lane_off[1:] - lane_off[:-1]).max().item()) if lane_off.numel() > 1 else 0
+        return Scene(lane_off, length, max_lane)
+
+    @property
+    def n_vehicles(self):
+        return self.length.numel()
+
+    @property
+    def n_lanes(self):
+        return self.lane_off.numel() - 1
+
+    def c(self):
+        return lib.make_scene(self.lane_off, self.length, self.max_lane)
+
+
+def _f32(t):
+    return t.to(device="cuda", dtype=torch.float32).contiguous()
+
+
+def _stream():
+    return torch.cuda.current_stream()
+
+
+def simulate(theta, p_init, v_init, scene, K, dt, a_min=-10.0, want_speed=False, ctx=None):
+    """Positions (and speeds) over K steps, time-major (K+1, N)."""
+    ctx = ctx or default_context()
+    theta, p_init, v_init = _f32(theta), _f32(p_init), _f32(v_init)
+    N = scene.n_vehicles
+    traj = torch.empty((K + 1, N), device="cuda", dtype=torch.float32)
+    vtraj = torch.empty((K + 1, N), device="cuda", dtype=torch.float32) if want_speed else None
+    lib.idm_forward(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                    traj, vtraj, _stream())
+    return (traj, vtraj) if want_speed else traj
+
+
+def backward(theta, p_init, v_init, scene, K, dt, gP, gV=None, a_min=-10.0, ctx=None):
+    """Adjoint from dense trajectory gradients: (g_theta (6,N), g_p_init, g_v_init)."""
+    ctx = ctx or default_context()
+    theta, p_init, v_init, gP = _f32(theta), _f32(p_init), _f32(v_init), _f32(gP)
+    gV = _f32(gV) if gV is not None else None
+    N = scene.n_vehicles
+    g = torch.empty((6, N), device="cuda", dtype=torch.float32)
+    gp = torch.empty(N, device="cuda", dtype=torch.float32)
+    gv = torch.empty(N, device="cuda", dtype=torch.float32)
+    lib.idm_backward(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                     gP, gV, lib.make_params(g), gp, gv, _stream())
+    return g, gp, gv
+
+
+def loss_grad(theta, p_init, v_init, scene, K, dt, targets, obs_stride=1, a_min=-10.0, ctx=None,
+              want_state_grad=True):
+    """Fused squared-error loss (sum over vehicles of each vehicle's mean)
+    and its gradients: (loss float64 0-d tensor, g_theta, g_p_init, g_v_init)."""
+    ctx = ctx or default_context()
+    theta, p_init, v_init = _f32(theta), _f32(p_init), _f32(v_init)
+    targets = _f32(targets) if targets is not None else None
+    N = scene.n_vehicles
+    loss = torch.zeros((), device="cuda", dtype=torch.float64)
+    g = torch.empty((6, N), device="cuda", dtype=torch.float32)
+    gp = torch.empty(N, device="cuda", dtype=torch.float32) if want_state_grad else None
+    gv = torch.empty(N, device="cuda", dtype=torch.float32) if want_state_grad else None
+    lib.idm_loss_grad(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                      targets, obs_stride, loss, lib.make_params(g), gp, gv, _stream())
+    return loss, g, gp, gv
+
+
+def fit(theta, p_init, v_init, scene, K, dt, targets, obs_stride, n_iter, lr0=0.1, lr1=0.01,
+        box_lo=(20.0, 0.1, 1.0, 0.5, 0.1), box_hi=(60.0, 5.0, 10.0, 10.0, 5.0), a_min=-10.0, ctx=None):
+    """Adam fit of (v0, T, s0, a_max, b) in place on a float32 (6, N) CUDA
+    tensor; returns the float64 loss history (n_iter,)."""
+    ctx = ctx or default_context()
+    assert theta.is_cuda and theta.dtype == torch.float32 and theta.is_contiguous()
+    p_init, v_init, targets = _f32(p_init), _f32(v_init), _f32(targets)
+    hist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
+    lib.idm_fit(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi, hist, _stream())
+    return hist[:n_iter]
+
+
+def layout(lane_id, pos, n_lanes, ctx=None):
+    """Head-first lane order: (perm int32 [N], lane_off int32 [L+1], max_lane int32 [1])."""
+    ctx = ctx or default_context()
+    lane_id = lane_id.to(device="cuda", dtype=torch.int32).contiguous()
+    pos = _f32(pos)
+    N = lane_id.numel()
+    perm = torch.empty(N, device="cuda", dtype=torch.int32)
+    lane_off = torch.empty(n_lanes + 1, device="cuda", dtype=torch.int32)
+    mx = torch.zeros(1, device="cuda", dtype=torch.int32)
+    lib.idm_layout(ctx.handle, N, n_lanes, lane_id, pos, perm, lane_off, mx, _stream())
+    return perm, lane_off, mx
+
+
+def gather(perm, srcs, ctx=None):
+    """[src[perm] for src in srcs] via idm_gather (float32 arrays)."""
+    ctx = ctx or default_context()
+    srcs = [_f32(s) for s in srcs]
+    dsts = [torch.empty(perm.numel(), device="cuda", dtype=torch.float32) for _ in srcs]
+    lib.idm_gather(ctx.handle, perm.numel(), perm, srcs, dsts, _stream())
+    return dsts
+
+
+class IdmFunction(torch.autograd.Function):
+    """Differentiable simulation: forward = idm_forward, backward = idm_backward."""
+
+    @staticmethod
+    def forward(fctx, theta, p_init, v_init, scene, K, dt, a_min=-10.0, ctx=None):
+        ctx = ctx or default_context()
+        traj = simulate(theta, p_init, v_init, scene, K, dt, a_min, ctx=ctx)
+        fctx.save_for_backward(theta, p_init, v_init)
+        fctx.cfg = (scene, K, dt, a_min, ctx)
+        return traj
+
+    @staticmethod
+    def backward(fctx, gtraj):
+        theta, p_init, v_init = fctx.saved_tensors
+        scene, K, dt, a_min, ctx = fctx.cfg
+        g, gp, gv = backward(theta, p_init, v_init, scene, K, dt, gtraj.contiguous(), None, a_min, ctx=ctx)
+        return g, gp, gv, None, None, None, None, None

@@ -1,0 +1,473 @@
+// C-ABI of libidm (declared in include/idm.h): argument checks, the context
+// and its workspace, kernel-variant selection and the fit's CUDA graph.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "../../include/idm.h"
+#include "idm_internal.h"
+
+using idm::ScenDesc;
+using idm::Seg;
+using idm::SimArgs;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+enum Ctl { CTL_NSEG = 0, CTL_WORK_F = 1, CTL_WORK_B = 2, CTL_ITER = 3, CTL_N = 8 };
+
+}  // namespace
+
+struct idm_ctx {
+    int device = 0;
+    int n_sm = 1;
+    size_t cap = 0;
+    size_t held = 0;
+    char err[512] = {0};
+    int vpt_req = 0;
+    int C = 16;
+    int wpb = 8;
+    Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t fit_exec = nullptr;
+};
+
+namespace {
+
+int fail(idm_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(idm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, IDM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.n >= bytes) return IDM_OK;
+    size_t want = c->held - b.n + bytes;
+    if (c->cap && want > c->cap)
+        return fail(c, IDM_ERR_WORKSPACE, "workspace for %s needs %zu bytes in total, cap is %zu", name, want,
+                    c->cap);
+    if (b.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+        cudaFree(b.p);
+        c->held -= b.n;
+        b.p = nullptr;
+        b.n = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, IDM_ERR_WORKSPACE, "cudaMalloc of %zu bytes for %s failed: %s", bytes, name,
+                    cudaGetErrorString(e));
+    }
+    b.n = bytes;
+    c->held += bytes;
+    return IDM_OK;
+}
+
+int pick_vpt(idm_ctx *c, int max_lane, int *vpt)
+{
+    int v = c->vpt_req;
+    if (v == 0) {
+        v = 1;
+        while (32 * v < max_lane && v < 8) v <<= 1;
+    }
+    if (32 * v < max_lane)
+        return fail(c, IDM_ERR_ARG, "max_lane %d exceeds %d vehicles per warp segment (vpt %d)", max_lane, 32 * v, v);
+    *vpt = v;
+    return IDM_OK;
+}
+
+int check_scene(idm_ctx *c, const idm_scene_t *s)
+{
+    if (!s) return fail(c, IDM_ERR_ARG, "scene is NULL");
+    if (s->n_lanes < 1) return fail(c, IDM_ERR_ARG, "n_lanes must be >= 1 (got %d)", s->n_lanes);
+    if (s->n_vehicles < 0) return fail(c, IDM_ERR_ARG, "n_vehicles must be >= 0");
+    if (!s->lane_off) return fail(c, IDM_ERR_ARG, "lane_off is NULL");
+    if (s->n_vehicles > 0 && !s->length) return fail(c, IDM_ERR_ARG, "length is NULL");
+    if (s->max_lane < 0 || s->max_lane > idm_max_lane_supported())
+        return fail(c, IDM_ERR_ARG, "max_lane %d outside [0, %d]", s->max_lane, idm_max_lane_supported());
+    return IDM_OK;
+}
+
+int check_params(idm_ctx *c, const idm_params_t *p, bool all)
+{
+    if (!p) return fail(c, IDM_ERR_ARG, "params is NULL");
+    if (!p->v0 || !p->T || !p->s0 || !p->a_max || !p->b || (all && !p->delta))
+        return fail(c, IDM_ERR_ARG, "a parameter array is NULL");
+    return IDM_OK;
+}
+
+int check_sim(idm_ctx *c, const idm_sim_t *s)
+{
+    if (!s) return fail(c, IDM_ERR_ARG, "sim is NULL");
+    if (s->K < 1) return fail(c, IDM_ERR_ARG, "K must be >= 1 (got %d)", s->K);
+    if (!(s->dt > 0.0f) || !std::isfinite(s->dt)) return fail(c, IDM_ERR_ARG, "dt must be finite and > 0");
+    if (!(s->a_min < 0.0f) || !std::isfinite(s->a_min)) return fail(c, IDM_ERR_ARG, "a_min must be finite and < 0");
+    return IDM_OK;
+}
+
+// Common preparation: buffers, initial gaps and warp segments.
+struct Prep {
+    int vpt = 1;
+    int grid_f = 1, grid_b = 1;
+    int wpb_b = 1;  // warps per block of the adjoint (bounded by its shared-memory tape)
+    SimArgs a;
+};
+
+int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const float *p_init, const float *v_init,
+            const idm_sim_t *sim, bool need_ckpt, bool need_loss, int obs_stride, Prep *P, cudaStream_t st)
+{
+    int rc;
+    if ((rc = pick_vpt(c, sc->max_lane, &P->vpt))) return rc;
+    const int N = sc->n_vehicles, L = sc->n_lanes;
+    if ((rc = ensure(c, c->seg, sizeof(Seg) * (size_t)L, "segments"))) return rc;
+    if ((rc = ensure(c, c->ctl, sizeof(int) * CTL_N, "control"))) return rc;
+    if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
+    if ((rc = ensure(c, c->g0, sizeof(float) * (size_t)N, "initial gaps"))) return rc;
+    if ((rc = ensure(c, c->loss_part, sizeof(double) * (size_t)L, "loss partials"))) return rc;
+    if ((rc = ensure(c, c->loss_tmp, sizeof(double) * 2, "loss scalar"))) return rc;
+    const int n_ck = (sim->K + c->C - 1) / c->C;
+    if (need_ckpt && (rc = ensure(c, c->ckpt, sizeof(float) * 4 * (size_t)n_ck * N, "checkpoints"))) return rc;
+
+    SimArgs &a = P->a;
+    memset(&a, 0, sizeof a);
+    a.seg = (const Seg *)c->seg.p;
+    a.n_seg = (const int *)c->ctl.p + CTL_NSEG;
+    a.scen_tab = nullptr;
+    ScenDesc &s0 = a.scen0;
+    s0.veh_begin = 0;
+    s0.n_veh = N;
+    s0.K = sim->K;
+    s0.obs_stride = obs_stride > 0 ? obs_stride : 1;
+    s0.n_obs = sim->K / s0.obs_stride;
+    s0.dt = sim->dt;
+    s0.inv_dt = 1.0f / sim->dt;
+    s0.a_min = sim->a_min;
+    s0.inv_nobs = s0.n_obs > 0 ? 1.0f / (float)s0.n_obs : 0.0f;
+    s0.traj_off = s0.tgt_off = s0.ckpt_off = 0;
+    a.g0 = (const float *)c->g0.p;
+    a.v0 = pr->v0; a.T = pr->T; a.s0 = pr->s0; a.am = pr->a_max; a.b = pr->b; a.delta = pr->delta;
+    a.p_init = p_init;
+    a.v_init = v_init;
+    a.loss_part = (double *)c->loss_part.p;
+    a.ckpt = (float *)c->ckpt.p;
+    a.C = c->C;
+    a.status = (unsigned *)c->status.p;
+    a.N_total = N;
+    (void)need_loss;
+
+    CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(int) * 3, st));
+    CK(idm::launch_prep_gap(sc->lane_off, L, p_init, sc->length, N, (float *)c->g0.p, a.status, st));
+    CK(idm::launch_build_segments(sc->lane_off, L, nullptr, 0, 32 * P->vpt, N, (Seg *)c->seg.p,
+                                  (int *)c->ctl.p + CTL_NSEG, a.status, st));
+    const int warps_needed = L;
+    const int blocks_needed = (warps_needed + c->wpb - 1) / c->wpb;
+    int occ_f = idm::occupancy_blocks(P->vpt, false, false, false, false, c->wpb, 0);
+    P->grid_f = std::min(blocks_needed, c->n_sm * occ_f);
+    P->grid_f = P->grid_f < 1 ? 1 : P->grid_f;
+    return IDM_OK;
+}
+
+int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L)
+{
+    const size_t smem_max = 227 * 1024;
+    const size_t per_warp = idm::backward_smem_bytes(P->vpt, dense, c->C, 1);
+    if (per_warp > smem_max)
+        return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per warp exceeds shared memory; lower "
+                                    "ckpt_interval", per_warp);
+    P->wpb_b = std::min<int>(c->wpb, (int)(smem_max / per_warp));
+    size_t smem = per_warp * P->wpb_b;
+    int occ_b = idm::occupancy_blocks(P->vpt, true, dense, adam, want_delta, P->wpb_b, smem);
+    int blocks_needed = (L + P->wpb_b - 1) / P->wpb_b;
+    P->grid_b = std::min(blocks_needed, c->n_sm * occ_b);
+    P->grid_b = P->grid_b < 1 ? 1 : P->grid_b;
+    return IDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int idm_max_lane_supported(void) { return 256; }
+
+int idm_ctx_create(idm_ctx_t **ctx, size_t workspace_cap_bytes)
+{
+    if (!ctx) return IDM_ERR_ARG;
+    *ctx = nullptr;
+    idm_ctx *c = new (std::nothrow) idm_ctx();
+    if (!c) return IDM_ERR_WORKSPACE;
+    c->cap = workspace_cap_bytes;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return IDM_ERR_CUDA;
+    }
+    *ctx = c;
+    return IDM_OK;
+}
+
+int idm_ctx_destroy(idm_ctx_t *c)
+{
+    if (!c) return IDM_OK;
+    cudaDeviceSynchronize();
+    if (c->fit_exec) cudaGraphExecDestroy(c->fit_exec);
+    Buf *bufs[] = {&c->seg, &c->ctl, &c->status, &c->g0, &c->ckpt, &c->loss_part, &c->loss_tmp,
+                   &c->adam_m, &c->adam_v, &c->lay_counts, &c->lay_cursor};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return IDM_OK;
+}
+
+const char *idm_last_error(const idm_ctx_t *c) { return c ? c->err : "no context"; }
+
+int idm_set_tuning(idm_ctx_t *c, int vpt, int ckpt_interval, int warps_per_block)
+{
+    if (!c) return IDM_ERR_ARG;
+    if (!(vpt == 0 || vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8))
+        return fail(c, IDM_ERR_ARG, "vpt must be 0, 1, 2, 4 or 8");
+    if (ckpt_interval < 1 || ckpt_interval > 64) return fail(c, IDM_ERR_ARG, "ckpt_interval must be in [1, 64]");
+    if (warps_per_block < 1 || warps_per_block > 8) return fail(c, IDM_ERR_ARG, "warps_per_block must be in [1, 8]");
+    c->vpt_req = vpt;
+    c->C = ckpt_interval;
+    c->wpb = warps_per_block;
+    return IDM_OK;
+}
+
+size_t idm_workspace_bytes(const idm_ctx_t *c, const idm_scene_t *s, const idm_sim_t *sim)
+{
+    if (!c || !s || !sim || sim->K < 1) return 0;
+    size_t N = (size_t)s->n_vehicles, L = (size_t)s->n_lanes;
+    size_t n_ck = (size_t)((sim->K + c->C - 1) / c->C);
+    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * L + 16 + 16 * n_ck * N;
+}
+
+int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st));
+    unsigned h = 0;
+    if (c->status.p) {
+        CK(cudaMemcpy(&h, c->status.p, sizeof h, cudaMemcpyDeviceToHost));
+        CK(cudaMemset(c->status.p, 0, sizeof(unsigned)));
+    }
+    if (flags) *flags = h;
+    if (h & (IDM_STATUS_LANE_TOO_LONG | IDM_STATUS_BAD_LANE_OFF))
+        return fail(c, IDM_ERR_LANE, "device status 0x%x: lane longer than the segment or malformed lanes", h);
+    if (h & IDM_STATUS_NONFINITE) return fail(c, IDM_ERR_NONFINITE, "device status 0x%x: non-finite value", h);
+    return IDM_OK;
+}
+
+int idm_layout(idm_ctx_t *c, int32_t N, int32_t n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,
+               int32_t *lane_off, int32_t *max_lane_out, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    if (N < 0 || n_lanes < 1) return fail(c, IDM_ERR_ARG, "need N >= 0 and n_lanes >= 1");
+    if (N > 0 && (!lane_id || !pos || !perm)) return fail(c, IDM_ERR_ARG, "lane_id, pos and perm are required");
+    if (!lane_off) return fail(c, IDM_ERR_ARG, "lane_off is required");
+    int rc;
+    if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
+    if ((rc = ensure(c, c->lay_counts, sizeof(int) * (size_t)n_lanes, "layout counts"))) return rc;
+    if ((rc = ensure(c, c->lay_cursor, sizeof(int) * (size_t)n_lanes, "layout cursor"))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(idm::launch_layout(N, n_lanes, lane_id, pos, perm, lane_off, max_lane_out, (int *)c->lay_counts.p,
+                          (int *)c->lay_cursor.p, (unsigned *)c->status.p, st));
+    return IDM_OK;
+}
+
+int idm_gather(idm_ctx_t *c, int32_t N, const int32_t *perm, int count, const float *const *srcs,
+               float *const *dsts, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    if (N < 0 || count < 0) return fail(c, IDM_ERR_ARG, "N and count must be >= 0");
+    if (N > 0 && count > 0 && (!perm || !srcs || !dsts)) return fail(c, IDM_ERR_ARG, "perm, srcs, dsts required");
+    for (int q = 0; q < count; ++q)
+        if (!srcs[q] || !dsts[q]) return fail(c, IDM_ERR_ARG, "array %d is NULL", q);
+    CK(idm::launch_gather(N, perm, count, srcs, dsts, (cudaStream_t)stream));
+    return IDM_OK;
+}
+
+int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *params, const float *p_init,
+                const float *v_init, const idm_sim_t *sim, float *traj, float *vtraj, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    int rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if (scene->n_vehicles > 0 && (!p_init || !v_init)) return fail(c, IDM_ERR_ARG, "p_init and v_init are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    Prep P;
+    if ((rc = prepare(c, scene, params, p_init, v_init, sim, false, false, 1, &P, st))) return rc;
+    P.a.work = (int *)c->ctl.p + CTL_WORK_F;
+    P.a.traj = traj;
+    P.a.vtraj = vtraj;
+    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, false, P.a, P.grid_f, c->wpb, st));
+    return IDM_OK;
+}
+
+int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *params, const float *p_init,
+                 const float *v_init, const idm_sim_t *sim, const float *gP, const float *gV, idm_params_t *grad,
+                 float *grad_p_init, float *grad_v_init, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    int rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if (scene->n_vehicles > 0 && (!p_init || !v_init || !gP))
+        return fail(c, IDM_ERR_ARG, "p_init, v_init and gP are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    Prep P;
+    if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, false, 1, &P, st))) return rc;
+    if ((rc = backward_grid(c, &P, true, false, grad && grad->delta, scene->n_lanes))) return rc;
+    P.a.work = (int *)c->ctl.p + CTL_WORK_F;
+    CK(idm::launch_forward(P.vpt, false, false, false, true, P.a, P.grid_f, c->wpb, st));
+    P.a.work = (int *)c->ctl.p + CTL_WORK_B;
+    P.a.gP = gP;
+    P.a.gV = gV;
+    if (grad) {
+        P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
+        P.a.g_am = grad->a_max; P.a.g_b = grad->b; P.a.g_delta = grad->delta;
+    }
+    P.a.g_p_init = grad_p_init;
+    P.a.g_v_init = grad_v_init;
+    CK(idm::launch_backward(P.vpt, true, false, grad && grad->delta, P.a, P.grid_b, P.wpb_b, st));
+    return IDM_OK;
+}
+
+int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *params, const float *p_init,
+                  const float *v_init, const idm_sim_t *sim, const float *targets, int32_t obs_stride,
+                  double *loss_out, idm_params_t *grad, float *grad_p_init, float *grad_v_init, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    int rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
+    if (scene->n_vehicles > 0 && (!p_init || !v_init)) return fail(c, IDM_ERR_ARG, "p_init and v_init are required");
+    if (sim->K / obs_stride > 0 && scene->n_vehicles > 0 && !targets)
+        return fail(c, IDM_ERR_ARG, "targets are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    Prep P;
+    if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, true, obs_stride, &P, st))) return rc;
+    const bool want_delta = grad && grad->delta;
+    if ((rc = backward_grid(c, &P, false, false, want_delta, scene->n_lanes))) return rc;
+    P.a.targets = targets;
+    P.a.work = (int *)c->ctl.p + CTL_WORK_F;
+    CK(idm::launch_forward(P.vpt, false, false, true, true, P.a, P.grid_f, c->wpb, st));
+    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, loss_out ? loss_out : (double *)c->loss_tmp.p, nullptr,
+                                 nullptr, st));
+    P.a.work = (int *)c->ctl.p + CTL_WORK_B;
+    if (grad) {
+        P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
+        P.a.g_am = grad->a_max; P.a.g_b = grad->b; P.a.g_delta = grad->delta;
+    }
+    P.a.g_p_init = grad_p_init;
+    P.a.g_v_init = grad_v_init;
+    CK(idm::launch_backward(P.vpt, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
+    return IDM_OK;
+}
+
+int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const float *p_init, const float *v_init,
+            const idm_sim_t *sim, const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
+            const float *box_lo, const float *box_hi, double *loss_hist, void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    int rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
+    if (n_iter < 0) return fail(c, IDM_ERR_ARG, "n_iter must be >= 0");
+    if (!box_lo || !box_hi) return fail(c, IDM_ERR_ARG, "box_lo and box_hi (host) are required");
+    for (int q = 0; q < 5; ++q)
+        if (!(box_lo[q] <= box_hi[q])) return fail(c, IDM_ERR_ARG, "box_lo[%d] > box_hi[%d]", q, q);
+    if (!(lr0 >= 0.0f) || !(lr1 >= 0.0f)) return fail(c, IDM_ERR_ARG, "learning rates must be >= 0");
+    if (scene->n_vehicles > 0 && (!p_init || !v_init)) return fail(c, IDM_ERR_ARG, "p_init and v_init are required");
+    if (sim->K / obs_stride > 0 && scene->n_vehicles > 0 && !targets)
+        return fail(c, IDM_ERR_ARG, "targets are required");
+    if (n_iter == 0) return IDM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prep P;
+    if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, true, obs_stride, &P, st))) return rc;
+    if ((rc = backward_grid(c, &P, false, true, false, scene->n_lanes))) return rc;
+    const size_t N = (size_t)scene->n_vehicles;
+    if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
+    if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
+    CK(cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, st));
+    CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
+    CK(cudaMemsetAsync((int *)c->ctl.p + CTL_ITER, 0, sizeof(int), st));
+
+    SimArgs a = P.a;
+    a.targets = targets;
+    a.adam_m = (float *)c->adam_m.p;
+    a.adam_v = (float *)c->adam_v.p;
+    a.iter = (const int *)c->ctl.p + CTL_ITER;
+    a.n_iter = n_iter;
+    a.lr0 = lr0;
+    a.lr1 = lr1;
+    for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
+
+    // capture one iteration on the context's stream
+    cudaStream_t cs = c->cap_stream;
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, st));
+    CK(cudaStreamWaitEvent(cs, ev, 0));
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
+    if (e == cudaSuccess) {
+        a.work = (int *)c->ctl.p + CTL_WORK_F;
+        e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, c->wpb, cs);
+    }
+    if (e == cudaSuccess) {
+        a.work = (int *)c->ctl.p + CTL_WORK_B;
+        e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
+    }
+    if (e == cudaSuccess)
+        e = idm::launch_loss_finalize(a.loss_part, a.n_seg, nullptr, (int *)c->ctl.p + CTL_ITER, loss_hist, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit iteration"); }
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+    if (c->fit_exec) {
+        CK(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(c->fit_exec);
+        c->fit_exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&c->fit_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    for (int it = 0; it < n_iter; ++it) CK(cudaGraphLaunch(c->fit_exec, st));
+    return IDM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// Device arithmetic of the modified IDM step (Eq. 1-3 and the softplus
+// bounds of Sec. III-C, arXiv 2412.16750) and of its partial derivatives.
+//
+// Every rounding in the state update is written with explicit _rn
+// intrinsics so that the forward kernel and the recompute inside the adjoint
+// kernel produce bit-identical trajectories (no contraction freedom).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/idm.h"
+
+namespace idm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Softplus pieces: e = exp(-|x|) and sp(x) = max(x,0) + log(1 + e).
+struct Soft {
+    float e;   // exp(-|x|)
+    float sp;  // softplus(x)
+};
+
+__device__ __forceinline__ Soft softplus(float x)
+{
+    Soft s;
+    s.e = __expf(-fabsf(x));
+    s.sp = __fadd_rn(fmaxf(x, 0.0f), __logf(__fadd_rn(1.0f, s.e)));
+    return s;
+}
+
+// Logistic sigmoid from the e = exp(-|x|) already computed for softplus.
+__device__ __forceinline__ float sigmoid_from(float x, float e)
+{
+    float d = rcp_approx(__fadd_rn(1.0f, e));
+    return x >= 0.0f ? d : __fmul_rn(e, d);
+}
+
+// Per-vehicle constants of one call.
+struct VehConst {
+    float inv_v0;  // 1 / v0
+    float T, s0, am, c;  // c = 1 / (2 sqrt(a_max b)), Eq. 1
+    float delta;
+};
+
+__device__ __forceinline__ VehConst make_const(float v0, float T, float s0, float am, float b, float delta)
+{
+    VehConst k;
+    k.inv_v0 = __frcp_rn(v0);
+    k.T = T;
+    k.s0 = s0;
+    k.am = am;
+    k.c = __fmul_rn(0.5f, rsqrtf(__fmul_rn(am, b)));
+    k.delta = delta;
+    return k;
+}
+
+// Ghost slots (padding at the end of a warp segment) and lane heads never
+// feed a real vehicle; these constants keep their arithmetic finite.
+__device__ __forceinline__ VehConst ghost_const()
+{
+    VehConst k;
+    k.inv_v0 = 1.0f; k.T = 0.0f; k.s0 = 0.0f; k.am = 1.0f; k.c = 0.5f; k.delta = 4.0f;
+    return k;
+}
+
+// (v / v0)^delta, with the delta == 4 case as two squarings.
+__device__ __forceinline__ float pow_delta(float r, float delta)
+{
+    if (delta == 4.0f) {
+        float r2 = __fmul_rn(r, r);
+        return __fmul_rn(r2, r2);
+    }
+    return r > 0.0f ? __powf(r, delta) : 0.0f;
+}
+
+// Bounded acceleration a* of one vehicle from its speed v, its raw gap
+// (p_h - p - length_h; +inf for a lane head) and its leader's speed vh.
+__device__ __forceinline__ float accel_star(float v, float gap_raw, float vh, const VehConst &k,
+                                            float inv_dt, float a_min)
+{
+    float gap = gap_raw < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : gap_raw;
+    float dv = __fsub_rn(v, vh);                                   // Sec. III-A
+    float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);    // Eq. 1
+    Soft s1 = softplus(s_opt);                                     // Sec. III-C
+    float z = __fmul_rn(s1.sp, rcp_approx(gap));                   // 0 for a head
+    float r = __fmul_rn(v, k.inv_v0);
+    float rd = pow_delta(r, k.delta);
+    float a = __fmul_rn(k.am, __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z)));  // Eq. 2
+    float lbv = -__fmul_rn(v, inv_dt);
+    float a_lb = lbv > a_min ? lbv : a_min;                        // Sec. III-C
+    Soft s2 = softplus(__fsub_rn(a, a_lb));
+    return __fadd_rn(a_lb, s2.sp);
+}
+
+// Vehicle state: displacement since step 0 as an unevaluated float pair
+// (xh + xl), speed, and raw gap to the leader.
+struct State {
+    float xh, xl, v, gap;
+};
+
+// Explicit Euler step (Eq. 3): positions use the old speeds, so the gap
+// moves by dt (vh - v); the displacement is accumulated with TwoSum plus the
+// exact rounding error of dt*v, so xh + xl stays within ~1e-10 relative.
+__device__ __forceinline__ void euler(State &s, float a_star, float vh, float dt)
+{
+    float d = __fmul_rn(dt, s.v);
+    float d_err = __fmaf_rn(dt, s.v, -d);
+    float t = __fadd_rn(s.xh, d);
+    float bb = __fsub_rn(t, s.xh);
+    float err = __fadd_rn(__fsub_rn(s.xh, __fsub_rn(t, bb)), __fsub_rn(d, bb));
+    s.xh = t;
+    s.xl = __fadd_rn(s.xl, __fadd_rn(err, d_err));
+    s.gap = __fmaf_rn(dt, __fsub_rn(vh, s.v), s.gap);
+    s.v = __fmaf_rn(dt, a_star, s.v);
+}
+
+// p_init + xh + xl - y, evaluated with TwoSum so the residual keeps the
+// precision of the pair even when p_init is kilometres from zero.
+__device__ __forceinline__ float residual(float p_init, const State &s, float y)
+{
+    float t = __fadd_rn(p_init, s.xh);
+    float bb = __fsub_rn(t, p_init);
+    float err = __fadd_rn(__fsub_rn(p_init, __fsub_rn(t, bb)), __fsub_rn(s.xh, bb));
+    return __fadd_rn(__fsub_rn(t, y), __fadd_rn(err, s.xl));
+}
+
+__device__ __forceinline__ float position(float p_init, const State &s)
+{
+    float t = __fadd_rn(p_init, s.xh);
+    float bb = __fsub_rn(t, p_init);
+    float err = __fadd_rn(__fsub_rn(p_init, __fsub_rn(t, bb)), __fsub_rn(s.xh, bb));
+    return __fadd_rn(t, __fadd_rn(err, s.xl));
+}
+
+// Leader values in the strided slot mapping: slot q = lane + 32 j; the
+// leader of slot q is q-1 (thread lane-1, same j; for lane 0, thread 31 of
+// j-1).  Slot 0 has no leader in the segment (it is a lane head) and gets 0.
+template <int VPT>
+__device__ __forceinline__ void leader_vals(const float (&x)[VPT], float (&out)[VPT], int lane)
+{
+    float rot[VPT];
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 31) & 31);
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+        float prev = j > 0 ? rot[j - 1] : 0.0f;
+        out[j] = lane == 0 ? prev : rot[j];
+    }
+}
+
+// Follower values: slot q receives from slot q+1 (thread lane+1, same j;
+// for lane 31, thread 0 of j+1).  The last slot gets 0.
+template <int VPT>
+__device__ __forceinline__ void follower_vals(const float (&x)[VPT], float (&out)[VPT], int lane)
+{
+    float rot[VPT];
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 1) & 31);
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+        float nxt = j + 1 < VPT ? rot[j + 1] : 0.0f;
+        out[j] = lane == 31 ? nxt : rot[j];
+    }
+}
+
+}  // namespace idm
+
+namespace idm {
+
+// Terms of one reverse step for one vehicle (the adjoint of accel_star and
+// euler).  mu = dt * (adjoint of the vehicle's step-(k+1) speed).  With
+// sigma2 = d a* / d a, sigma1 = d s* / d s_opt, S = d a / d s*,
+// G = d a / d gap and W = mu sigma2 S sigma1:
+//   own_p  = mu d a*/d p          = -mu sigma2 G
+//   own_v  = mu d a*/d v          (own speed, incl. the a_lb branch)
+//   lead_p = mu d a*/d p_leader   = +mu sigma2 G       (sent to the leader)
+//   lead_v = mu d a*/d v_leader   = W (-c v)           (sent to the leader)
+// and the parameter-gradient increments, factored so that per-vehicle
+// constants multiply once at the end:
+//   w = W, w_v = W v, w_vdv = W v dv, f_a = mu sigma2 (1 - r^delta - z^2),
+//   f_rd = mu sigma2 r^delta, f_rdlnr = mu sigma2 r^delta ln r.
+struct AdjTerms {
+    float own_p, own_v, lead_p, lead_v;
+    float w, w_v, w_vdv, f_a, f_rd, f_rdlnr;
+};
+
+template <bool WANT_DELTA>
+__device__ __forceinline__ AdjTerms adjoint_terms(float mu, float v, float gap_raw, float vh,
+                                                  const VehConst &k, float inv_dt, float a_min)
+{
+    AdjTerms t;
+    const bool floored = gap_raw < IDM_GAP_FLOOR;
+    float gap = floored ? IDM_GAP_FLOOR : gap_raw;
+    float dv = __fsub_rn(v, vh);
+    float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);
+    Soft s1 = softplus(s_opt);
+    float sig1 = sigmoid_from(s_opt, s1.e);
+    float inv_gap = rcp_approx(gap);
+    float z = __fmul_rn(s1.sp, inv_gap);
+    float r = __fmul_rn(v, k.inv_v0);
+    float rd, rdm1;
+    if (k.delta == 4.0f) {
+        float r2 = __fmul_rn(r, r);
+        rd = __fmul_rn(r2, r2);
+        rdm1 = __fmul_rn(r2, r);
+    } else {
+        rd = r > 0.0f ? __powf(r, k.delta) : 0.0f;
+        rdm1 = r > 0.0f ? __powf(r, k.delta - 1.0f) : (k.delta > 1.0f ? 0.0f : (k.delta == 1.0f ? 1.0f : INFINITY));
+    }
+    float free_and_int = __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z));
+    float a = __fmul_rn(k.am, free_and_int);
+    float lbv = -__fmul_rn(v, inv_dt);
+    const bool beta = lbv > a_min;
+    float a_lb = beta ? lbv : a_min;
+    float x2 = __fsub_rn(a, a_lb);
+    float e2 = __expf(-fabsf(x2));
+    float d2 = rcp_approx(__fadd_rn(1.0f, e2));
+    float sig2 = x2 >= 0.0f ? d2 : __fmul_rn(e2, d2);       // sigma(x2)
+    float one_m_sig2 = x2 >= 0.0f ? __fmul_rn(e2, d2) : d2; // sigma(-x2)
+
+    float S = -2.0f * k.am * z * inv_gap;     // d a / d s*
+    float G = floored ? 0.0f : -S * z;        // d a / d gap = 2 a_max z^2 / gap
+    float ms2 = mu * sig2;
+    float W = ms2 * S * sig1;
+    t.own_p = -ms2 * G;
+    t.lead_p = ms2 * G;
+    t.lead_v = -W * k.c * v;
+    float dfree_dv = -k.am * k.delta * rdm1 * k.inv_v0;
+    t.own_v = ms2 * dfree_dv + W * (k.T + k.c * (v + dv)) - (beta ? mu * one_m_sig2 * inv_dt : 0.0f);
+    t.w = W;
+    t.w_v = W * v;
+    t.w_vdv = W * v * dv;
+    t.f_a = ms2 * free_and_int;
+    t.f_rd = ms2 * rd;
+    t.f_rdlnr = (WANT_DELTA && rd > 0.0f) ? ms2 * rd * __logf(r) : 0.0f;
+    return t;
+}
+
+}  // namespace idm

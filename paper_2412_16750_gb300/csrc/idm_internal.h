@@ -1,0 +1,83 @@
+// Internal types shared by the kernels and the C-ABI layer of libidm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace idm {
+
+// One scenario: a contiguous range of lanes/vehicles simulated with its own
+// horizon, step and observation stride.  Time-major arrays of the scenario
+// ([K+1][n_veh] trajectories, [n_obs][n_veh] targets, checkpoints) start at
+// the given element offsets.
+struct ScenDesc {
+    int veh_begin;      // first vehicle (global index)
+    int n_veh;          // vehicles in the scenario (row length of its arrays)
+    int K;              // steps
+    int obs_stride;     // observed steps are k = s, 2s, ... <= K
+    int n_obs;          // floor(K / s)
+    float dt, inv_dt, a_min;
+    float inv_nobs;     // 1 / n_obs (0 if none)
+    int pad;
+    long long traj_off;  // element offset of row 0 of the trajectories
+    long long tgt_off;   // element offset of the targets (row j-1 = step j*s)
+    long long ckpt_off;  // element offset of the checkpoints
+};
+
+// One warp segment: whole lanes packed into at most 32*VPT slots.
+struct Seg {
+    int veh_begin;  // global index of slot 0
+    int n_veh;      // occupied slots
+    int scen;       // scenario index
+    int pad;
+};
+
+// Everything a simulation kernel reads or writes (passed by value).
+struct SimArgs {
+    const Seg *seg;
+    const int *n_seg;
+    int *work;                  // persistent work counter (zeroed before launch)
+    const ScenDesc *scen_tab;   // NULL: every segment uses scen0
+    ScenDesc scen0;
+    const float *g0;            // initial raw gap (+inf for lane heads)
+    const float *v0, *T, *s0, *am, *b, *delta;
+    const float *p_init, *v_init;
+    float *traj, *vtraj;
+    const float *targets;
+    double *loss_part;          // [n_seg] per-segment loss
+    float *ckpt;
+    int C;                      // checkpoint interval (steps)
+    unsigned *status;
+    // adjoint
+    const float *gP, *gV;       // dense trajectory gradients (scenario-local time-major)
+    float *g_v0, *g_T, *g_s0, *g_am, *g_b, *g_delta, *g_p_init, *g_v_init;
+    // Adam (fit)
+    float *adam_m, *adam_v;     // [5][N_total]
+    const int *iter;            // 0-based iteration counter (device)
+    int n_iter;
+    int N_total;
+    float lr0, lr1;
+    float lo[5], hi[5];
+};
+
+// Launchers (idm_sim.cu).  Return cudaError_t of the launch.
+cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_init, const float *length,
+                            int N, float *g0, unsigned *status, cudaStream_t st);
+cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *scen_lane_off, int n_scen,
+                                  int cap, int N, Seg *seg, int *n_seg, unsigned *status, cudaStream_t st);
+cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt, const SimArgs &a,
+                           int grid, int wpb, cudaStream_t st);
+cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
+                            int grid, int wpb, cudaStream_t st);
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb);
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, int *iter,
+                                 double *hist, cudaStream_t st);
+int occupancy_blocks(int vpt, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
+
+// Layout (idm_layout.cu).
+cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,
+                          int32_t *lane_off, int32_t *max_lane, int *counts, int *cursor, unsigned *status,
+                          cudaStream_t st);
+cudaError_t launch_gather(int N, const int32_t *perm, int count, const float *const *srcs, float *const *dsts,
+                          cudaStream_t st);
+
+}  // namespace idm

@@ -1,0 +1,640 @@
+// Simulation kernels of libidm for sm_103a: initial gaps, lane packing into
+// warp segments, the fused forward (Eq. 1-3 with the Sec. III-C bounds,
+// squared-error loss, checkpoints) and the reverse-time adjoint with
+// checkpoint recompute (arXiv 2412.16750, Sec. III and IV-A).
+//
+// Mapping.  Vehicles are ordered lane by lane, head first.  Whole lanes are
+// packed into warp segments of at most 32*VPT vehicles; slot q of a segment
+// lives in register j = q / 32 of thread q % 32, so every per-step load or
+// store of a segment is one contiguous 128-byte row per register.  The
+// leader of slot q is slot q-1, fetched by one warp shuffle; lanes never
+// cross a segment, so a warp runs all K steps of its lanes with no
+// inter-warp synchronisation.  Warps take segments from a global atomic
+// counter (persistent grid).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "idm_device.cuh"
+#include "idm_internal.h"
+
+namespace idm {
+
+// ---------------------------------------------------------------------------
+// Initial gaps g0[i] = p_init[i-1] - p_init[i] - length[i-1] (Sec. III-A),
+// +inf for lane heads.
+// ---------------------------------------------------------------------------
+__global__ void gap_kernel(const float *p_init, const float *length, int N, float *g0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (i == 0) { g0[0] = INFINITY; return; }
+    double g = (double)p_init[i - 1] - (double)p_init[i] - (double)length[i - 1];
+    g0[i] = (float)g;
+}
+
+__global__ void head_kernel(const int *lane_off, int n_lanes, int N, float *g0, unsigned *status)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_lanes) return;
+    int a = lane_off[l], e = lane_off[l + 1];
+    bool bad = e < a || a < 0 || e > N || (l == 0 && a != 0) || (l == n_lanes - 1 && e != N);
+    if (bad) { atomicOr(status, IDM_STATUS_BAD_LANE_OFF); return; }
+    if (a < e) g0[a] = INFINITY;
+}
+
+cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_init, const float *length,
+                            int N, float *g0, unsigned *status, cudaStream_t st)
+{
+    if (N > 0) gap_kernel<<<(N + 255) / 256, 256, 0, st>>>(p_init, length, N, g0);
+    if (n_lanes > 0) head_kernel<<<(n_lanes + 255) / 256, 256, 0, st>>>(lane_off, n_lanes, N, g0, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Lane packing: each of 1024 threads packs a contiguous chunk of lanes
+// greedily into segments of at most `cap` vehicles (never across a scenario
+// boundary); a block scan places the chunks' segments.  A lane longer than
+// cap is skipped and flagged.
+// ---------------------------------------------------------------------------
+constexpr int BUILD_THREADS = 1024;
+
+template <bool EMIT>
+__device__ int pack_lanes(const int *lane_off, int l0, int l1, const int *scen_lane_off, int n_scen, int cap,
+                          int N, Seg *out, unsigned *status)
+{
+    int cnt = 0, fill = 0, seg_begin = 0, cur_scen = -1;
+    int s = 0;
+    if (scen_lane_off) {  // scenario of lane l0
+        int lo = 0, hi = n_scen - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (scen_lane_off[mid] <= l0) lo = mid; else hi = mid - 1;
+        }
+        s = lo;
+    }
+    for (int l = l0; l < l1; ++l) {
+        if (scen_lane_off)
+            while (s + 1 < n_scen && scen_lane_off[s + 1] <= l) ++s;
+        int a = lane_off[l], e = lane_off[l + 1], n = e - a;
+        if (a < 0 || e > N || n < 0) {  // malformed: never read outside [0, N)
+            if (EMIT) atomicOr(status, IDM_STATUS_BAD_LANE_OFF);
+            if (fill > 0) {
+                if (EMIT) out[cnt] = Seg{seg_begin, fill, cur_scen < 0 ? 0 : cur_scen, 0};
+                ++cnt;
+                fill = 0;
+            }
+            continue;
+        }
+        if (n == 0) continue;
+        bool close = fill > 0 && (fill + n > cap || s != cur_scen);
+        if (n > cap) {
+            if (EMIT) atomicOr(status, IDM_STATUS_LANE_TOO_LONG);
+            close = fill > 0;
+        }
+        if (close) {
+            if (EMIT) out[cnt] = Seg{seg_begin, fill, cur_scen < 0 ? 0 : cur_scen, 0};
+            ++cnt;
+            fill = 0;
+        }
+        if (n > cap) continue;
+        if (fill == 0) { seg_begin = a; cur_scen = s; }
+        fill += n;
+    }
+    if (fill > 0) {
+        if (EMIT) out[cnt] = Seg{seg_begin, fill, cur_scen < 0 ? 0 : cur_scen, 0};
+        ++cnt;
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(BUILD_THREADS)
+build_segments_kernel(const int *lane_off, int n_lanes, const int *scen_lane_off, int n_scen, int cap, int N,
+                      Seg *seg, int *n_seg, unsigned *status)
+{
+    __shared__ int sc[BUILD_THREADS];
+    const int t = threadIdx.x;
+    const int per = (n_lanes + BUILD_THREADS - 1) / BUILD_THREADS;
+    const int l0 = min(n_lanes, t * per), l1 = min(n_lanes, l0 + per);
+    int cnt = pack_lanes<false>(lane_off, l0, l1, scen_lane_off, n_scen, cap, N, nullptr, status);
+    sc[t] = cnt;
+    __syncthreads();
+    for (int off = 1; off < BUILD_THREADS; off <<= 1) {  // inclusive Hillis-Steele scan
+        int v = t >= off ? sc[t - off] : 0;
+        __syncthreads();
+        sc[t] += v;
+        __syncthreads();
+    }
+    int base = sc[t] - cnt;
+    pack_lanes<true>(lane_off, l0, l1, scen_lane_off, n_scen, cap, N, seg + base, status);
+    if (t == BUILD_THREADS - 1) *n_seg = sc[t];
+}
+
+cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *scen_lane_off, int n_scen,
+                                  int cap, int N, Seg *seg, int *n_seg, unsigned *status, cudaStream_t st)
+{
+    build_segments_kernel<<<1, BUILD_THREADS, 0, st>>>(lane_off, n_lanes, scen_lane_off, n_scen, cap, N, seg,
+                                                       n_seg, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int next_segment(int *work, int lane)
+{
+    int s = 0;
+    if (lane == 0) s = atomicAdd(work, 1);
+    return __shfl_sync(FULL, s, 0);
+}
+
+// Kahan-compensated float accumulation.
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    float y = __fsub_rn(x, comp);
+    float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+__device__ __forceinline__ double warp_sum_double(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+template <int VPT>
+__device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, VehConst (&kc)[VPT],
+                                              State (&st)[VPT], float (&pin)[VPT], bool (&valid)[VPT])
+{
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+        const int q = lane + 32 * j;
+        valid[j] = q < sg.n_veh;
+        if (valid[j]) {
+            const int gi = sg.veh_begin + q;
+            kc[j] = make_const(a.v0[gi], a.T[gi], a.s0[gi], a.am[gi], a.b[gi], a.delta[gi]);
+            st[j] = State{0.0f, 0.0f, a.v_init[gi], a.g0[gi]};
+            pin[j] = a.p_init[gi];
+        } else {
+            kc[j] = ghost_const();
+            st[j] = State{0.0f, 0.0f, 0.0f, INFINITY};
+            pin[j] = 0.0f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward: K steps per segment, optional trajectory / speed output, fused
+// squared-error loss, checkpoints every C steps.
+// ---------------------------------------------------------------------------
+template <int VPT>
+__global__ void __launch_bounds__(512)
+forward_kernel(SimArgs a, bool want_traj, bool want_vtraj, bool want_loss, bool want_ckpt)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const int s_idx = next_segment(a.work, lane);
+        if (s_idx >= *a.n_seg) break;
+        const Seg sg = a.seg[s_idx];
+        const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
+        const int Ns = sc.n_veh;
+        const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
+
+        VehConst kc[VPT];
+        State st[VPT];
+        float pin[VPT];
+        bool valid[VPT];
+        load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
+
+        float lsum = 0.0f, lcomp = 0.0f;
+        int next_obs = sc.obs_stride, obs_row = 0;
+        int next_ck = 0, ck_idx = 0;
+        for (int k = 0;; ++k) {
+            if (want_ckpt && k == next_ck && k < sc.K) {
+                float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    const int q = lane + 32 * j;
+                    base[q] = st[j].xh;
+                    base[(size_t)Ns + q] = st[j].xl;
+                    base[2 * (size_t)Ns + q] = st[j].v;
+                    base[3 * (size_t)Ns + q] = st[j].gap;
+                }
+                next_ck += a.C;
+                ++ck_idx;
+            }
+            if (want_traj || want_vtraj) {
+                const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    const int q = lane + 32 * j;
+                    if (want_traj) a.traj[row + q] = position(pin[j], st[j]);
+                    if (want_vtraj) a.vtraj[row + q] = st[j].v;
+                }
+            }
+            if (want_loss && k == next_obs && obs_row < sc.n_obs) {
+                const float *y = a.targets + sc.tgt_off + (size_t)obs_row * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
+                    kahan_add(lsum, lcomp, __fmul_rn(r, r));
+                }
+                next_obs += sc.obs_stride;
+                ++obs_row;
+            }
+            if (k == sc.K) break;
+
+            float vcur[VPT], vh[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
+            leader_vals<VPT>(vcur, vh, lane);
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                float as = accel_star(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
+                euler(st[j], as, vh[j], sc.dt);
+            }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j)
+            if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].xh))) bad = true;
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+        if (want_loss) {
+            double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
+            if (lane == 0) a.loss_part[s_idx] = part;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint.  Per segment of C steps (last first): reload the checkpoint,
+// recompute the C steps into a shared-memory tape of (v, raw gap[, seed]),
+// then run the reverse recurrences
+//   lp_k = seed_k + lp_{k+1} + mu A_p + mu_f A_ph(f)
+//   lv_k = dt lp_{k+1} + lv_{k+1} + mu A_v + mu_f A_vh(f)
+// with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle.
+// Parameter gradients accumulate per segment in float and across segments
+// with Kahan compensation.
+// ---------------------------------------------------------------------------
+template <int VPT, bool DENSE>
+__device__ __forceinline__ float *tape_base(float *smem, int C)
+{
+    const int per_warp = (DENSE ? 2 : 3) * C * 32 * VPT;
+    return smem + (threadIdx.x >> 5) * per_warp;
+}
+
+template <int VPT, bool DENSE, bool ADAM>
+__global__ void __launch_bounds__(256)
+backward_kernel(SimArgs a, bool want_delta)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    constexpr int SL = 32 * VPT;
+    float *tv = tape_base<VPT, DENSE>(smem, a.C);
+    float *tg = tv + a.C * SL;
+    float *tr = tg + a.C * SL;  // seeds (MSE only)
+
+    for (;;) {
+        const int s_idx = next_segment(a.work, lane);
+        if (s_idx >= *a.n_seg) break;
+        const Seg sg = a.seg[s_idx];
+        const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
+        const int Ns = sc.n_veh;
+        const int lb = sg.veh_begin - sc.veh_begin;
+        const float dt = sc.dt;
+        const float seed_scale = 2.0f * sc.inv_nobs;
+
+        VehConst kc[VPT];
+        State st[VPT];
+        float pin[VPT];
+        bool valid[VPT];
+        load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
+
+        float lp[VPT], lv[VPT];
+        float acc[6][VPT], cmp[6][VPT];
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            lp[j] = 0.0f;
+            lv[j] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) { acc[q][j] = 0.0f; cmp[q][j] = 0.0f; }
+        }
+
+        const int n_ck = (sc.K + a.C - 1) / a.C;
+        for (int cs = n_ck - 1; cs >= 0; --cs) {
+            const int c0 = cs * a.C;
+            const int n = min(a.C, sc.K - c0);
+            {
+                const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    const int q = lane + 32 * j;
+                    st[j] = State{base[q], base[(size_t)Ns + q], base[2 * (size_t)Ns + q], base[3 * (size_t)Ns + q]};
+                }
+            }
+            // recompute the segment into the tape
+            for (int s = 0; s < n; ++s) {
+                const int k = c0 + s;
+                float *rv = tv + s * SL, *rg = tg + s * SL;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    rv[lane + 32 * j] = st[j].v;
+                    rg[lane + 32 * j] = st[j].gap;
+                }
+                if (!DENSE) {
+                    const bool obs = k >= 1 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
+                    if (obs) {
+                        const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
+                        float *rr = tr + s * SL;
+#pragma unroll
+                        for (int j = 0; j < VPT; ++j) {
+                            float r = valid[j] ? residual(pin[j], st[j], __ldg(y + lane + 32 * j)) : 0.0f;
+                            rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
+                        }
+                    }
+                }
+                float vcur[VPT], vh[VPT];
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
+                leader_vals<VPT>(vcur, vh, lane);
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    float as = accel_star(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
+                    euler(st[j], as, vh[j], dt);
+                }
+            }
+            if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
+                if (DENSE) {
+                    const size_t row = sc.traj_off + (size_t)sc.K * Ns + lb;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j) {
+                        if (!valid[j]) continue;
+                        lp[j] = a.gP[row + lane + 32 * j];
+                        lv[j] = a.gV ? a.gV[row + lane + 32 * j] : 0.0f;
+                    }
+                } else {
+                    const int k = sc.K;
+                    const bool obs = (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs && sc.n_obs > 0;
+                    if (obs) {
+                        const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
+#pragma unroll
+                        for (int j = 0; j < VPT; ++j)
+                            if (valid[j])
+                                lp[j] = __fmul_rn(seed_scale, residual(pin[j], st[j], __ldg(y + lane + 32 * j)));
+                    }
+                }
+            }
+            __syncwarp();
+
+            float sacc[6][VPT];
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) sacc[q][j] = 0.0f;
+
+            for (int s = n - 1; s >= 0; --s) {
+                const int k = c0 + s;
+                const float *rv = tv + s * SL, *rg = tg + s * SL;
+                float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    const int q = lane + 32 * j;
+                    const float v = rv[q];
+                    const float gap = rg[q];
+                    const float vh = q > 0 ? rv[q - 1] : 0.0f;
+                    const float mu = __fmul_rn(dt, lv[j]);
+                    AdjTerms t;
+                    if (want_delta)
+                        t = adjoint_terms<true>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
+                    else
+                        t = adjoint_terms<false>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
+                    own_p[j] = t.own_p;
+                    own_v[j] = t.own_v;
+                    to_lp[j] = t.lead_p;
+                    to_lv[j] = t.lead_v;
+                    sacc[0][j] += t.w;
+                    sacc[1][j] += t.w_v;
+                    sacc[2][j] += t.w_vdv;
+                    sacc[3][j] += t.f_a;
+                    sacc[4][j] += t.f_rd;
+                    sacc[5][j] += t.f_rdlnr;
+                }
+                float from_p[VPT], from_v[VPT];
+                follower_vals<VPT>(to_lp, from_p, lane);
+                follower_vals<VPT>(to_lv, from_v, lane);
+                float seed_p[VPT], seed_v[VPT];
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) { seed_p[j] = 0.0f; seed_v[j] = 0.0f; }
+                if (DENSE) {
+                    const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j) {
+                        if (!valid[j]) continue;
+                        seed_p[j] = a.gP[row + lane + 32 * j];
+                        if (a.gV) seed_v[j] = a.gV[row + lane + 32 * j];
+                    }
+                } else {
+                    const bool obs = k >= 1 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
+                    if (obs) {
+                        const float *rr = tr + s * SL;
+#pragma unroll
+                        for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    float nlp = lp[j] + own_p[j] + from_p[j] + seed_p[j];
+                    float nlv = dt * lp[j] + lv[j] + own_v[j] + from_v[j] + seed_v[j];
+                    lp[j] = nlp;
+                    lv[j] = nlv;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) kahan_add(acc[q][j], cmp[q][j], sacc[q][j]);
+            __syncwarp();
+        }
+
+        // epilogue: parameter gradients from the factored sums
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            if (!valid[j]) continue;
+            const int q = lane + 32 * j;
+            const int gi = sg.veh_begin + q;
+            const float v0 = a.v0[gi], b = a.b[gi];
+            const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
+            const float W = acc[0][j] - cmp[0][j], Wv = acc[1][j] - cmp[1][j], Wvdv = acc[2][j] - cmp[2][j];
+            const float Fa = acc[3][j] - cmp[3][j], Frd = acc[4][j] - cmp[4][j], Fl = acc[5][j] - cmp[5][j];
+            float g[6];
+            g[0] = am * dl * Frd / v0;                 // v0
+            g[1] = Wv;                                 // T
+            g[2] = W;                                  // s0
+            g[3] = Fa - Wvdv * c / (2.0f * am);        // a_max
+            g[4] = -Wvdv * c / (2.0f * b);             // b
+            g[5] = -am * Fl;                           // delta
+            for (int p = 0; p < 6; ++p) bad |= !isfinite(g[p]);
+            if (ADAM) {
+                const int it = *a.iter;
+                const int t = it + 1;
+                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
+                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
+#pragma unroll
+                for (int p = 0; p < 5; ++p) {
+                    const size_t mi = (size_t)p * a.N_total + gi;
+                    float m = 0.9f * a.adam_m[mi] + 0.1f * g[p];
+                    float vv = 0.999f * a.adam_v[mi] + 0.001f * g[p] * g[p];
+                    a.adam_m[mi] = m;
+                    a.adam_v[mi] = vv;
+                    float x = th[p][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+                    x = fminf(fmaxf(x, a.lo[p]), a.hi[p]);
+                    th[p][gi] = x;
+                }
+            } else {
+                if (a.g_v0) a.g_v0[gi] = g[0];
+                if (a.g_T) a.g_T[gi] = g[1];
+                if (a.g_s0) a.g_s0[gi] = g[2];
+                if (a.g_am) a.g_am[gi] = g[3];
+                if (a.g_b) a.g_b[gi] = g[4];
+                if (a.g_delta) a.g_delta[gi] = g[5];
+                if (a.g_p_init) a.g_p_init[gi] = lp[j];
+                if (a.g_v_init) a.g_v_init[gi] = lv[j];
+            }
+        }
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic loss reduction over segments (fixed order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+loss_finalize_kernel(const double *part, const int *n_seg, double *out, int *iter, double *hist)
+{
+    __shared__ double sh[1024];
+    const int n = *n_seg;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (out) *out = sh[0];
+        if (iter) {
+            if (hist) hist[*iter] = sh[0];
+            *iter += 1;
+        }
+    }
+}
+
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, int *iter,
+                                 double *hist, cudaStream_t st)
+{
+    loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, out, iter, hist);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt, const SimArgs &a, int grid,
+                           int wpb, cudaStream_t st)
+{
+    dim3 blk(32 * wpb);
+    switch (vpt) {
+    case 1: forward_kernel<1><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
+    case 2: forward_kernel<2><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
+    case 4: forward_kernel<4><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
+    case 8: forward_kernel<8><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb)
+{
+    return (size_t)(dense_seed ? 2 : 3) * C * 32 * vpt * sizeof(float) * wpb;
+}
+
+template <int VPT, bool DENSE, bool ADAM>
+static cudaError_t launch_bwd_t(const SimArgs &a, bool want_delta, int grid, int wpb, cudaStream_t st)
+{
+    size_t smem = backward_smem_bytes(VPT, DENSE, a.C, wpb);
+    auto fn = backward_kernel<VPT, DENSE, ADAM>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, 32 * wpb, smem, st>>>(a, want_delta);
+    return cudaGetLastError();
+}
+
+template <int VPT>
+static cudaError_t launch_bwd_v(bool dense, bool adam, bool want_delta, const SimArgs &a, int grid, int wpb,
+                                cudaStream_t st)
+{
+    if (dense) return adam ? cudaErrorInvalidValue : launch_bwd_t<VPT, true, false>(a, want_delta, grid, wpb, st);
+    return adam ? launch_bwd_t<VPT, false, true>(a, want_delta, grid, wpb, st)
+                : launch_bwd_t<VPT, false, false>(a, want_delta, grid, wpb, st);
+}
+
+cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a, int grid,
+                            int wpb, cudaStream_t st)
+{
+    switch (vpt) {
+    case 1: return launch_bwd_v<1>(dense_seed, adam, want_delta, a, grid, wpb, st);
+    case 2: return launch_bwd_v<2>(dense_seed, adam, want_delta, a, grid, wpb, st);
+    case 4: return launch_bwd_v<4>(dense_seed, adam, want_delta, a, grid, wpb, st);
+    case 8: return launch_bwd_v<8>(dense_seed, adam, want_delta, a, grid, wpb, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+static int occ(F fn, int wpb, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * wpb, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+int occupancy_blocks(int vpt, bool backward, bool dense, bool adam, bool want_delta, int wpb, size_t smem)
+{
+    (void)want_delta;
+    if (!backward) {
+        switch (vpt) {
+        case 1: return occ(forward_kernel<1>, wpb, 0);
+        case 2: return occ(forward_kernel<2>, wpb, 0);
+        case 4: return occ(forward_kernel<4>, wpb, 0);
+        case 8: return occ(forward_kernel<8>, wpb, 0);
+        }
+        return 1;
+    }
+#define OCC_B(V)                                                                  \
+    if (vpt == V) {                                                               \
+        if (dense) return occ(backward_kernel<V, true, false>, wpb, smem);        \
+        if (adam) {                                                               \
+            cudaFuncSetAttribute(backward_kernel<V, false, true>,                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            return occ(backward_kernel<V, false, true>, wpb, smem);               \
+        }                                                                         \
+        cudaFuncSetAttribute(backward_kernel<V, false, false>,                    \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        return occ(backward_kernel<V, false, false>, wpb, smem);                  \
+    }
+    OCC_B(1) OCC_B(2) OCC_B(4) OCC_B(8)
+#undef OCC_B
+    return 1;
+}
+
+}  // namespace idm

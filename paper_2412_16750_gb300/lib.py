@@ -1,0 +1,214 @@
+"""ctypes binding of libidm (include/idm.h): same names, argument marshalling only.
+
+Every compute step runs inside libidm's CUDA kernels; this module only turns
+Python values into C structs and raw pointers.  It raises ``RuntimeError``
+when the library has not been built -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libidm.so")
+
+IDM_OK = 0
+IDM_ERR_ARG = 1
+IDM_ERR_WORKSPACE = 2
+IDM_ERR_CUDA = 3
+IDM_ERR_NONFINITE = 4
+IDM_ERR_TIMEOUT = 5
+IDM_ERR_LANE = 6
+
+IDM_STATUS_LANE_TOO_LONG = 1
+IDM_STATUS_BAD_LANE_OFF = 2
+IDM_STATUS_NONFINITE = 4
+
+GAP_FLOOR = 0.1
+
+_vp = ctypes.c_void_p
+
+
+class idm_scene_t(ctypes.Structure):
+    _fields_ = [("n_lanes", ctypes.c_int32), ("n_vehicles", ctypes.c_int32), ("max_lane", ctypes.c_int32),
+                ("lane_off", _vp), ("length", _vp)]
+
+
+class idm_params_t(ctypes.Structure):
+    _fields_ = [("v0", _vp), ("T", _vp), ("s0", _vp), ("a_max", _vp), ("b", _vp), ("delta", _vp)]
+
+
+class idm_sim_t(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("dt", ctypes.c_float), ("a_min", ctypes.c_float)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "idm_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_size_t]),
+    "idm_ctx_destroy": (ctypes.c_int, [_vp]),
+    "idm_last_error": (ctypes.c_char_p, [_vp]),
+    "idm_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), _vp]),
+    "idm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "idm_max_lane_supported": (ctypes.c_int, []),
+    "idm_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_sim_t)]),
+    "idm_layout": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "idm_gather": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int, ctypes.POINTER(_vp),
+                                  ctypes.POINTER(_vp), _vp]),
+    "idm_forward": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                   ctypes.POINTER(idm_sim_t), _vp, _vp, _vp]),
+    "idm_backward": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                    ctypes.POINTER(idm_sim_t), _vp, _vp, ctypes.POINTER(idm_params_t), _vp, _vp,
+                                    _vp]),
+    "idm_loss_grad": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                     ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, _vp,
+                                     ctypes.POINTER(idm_params_t), _vp, _vp, _vp]),
+    "idm_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                               ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                               ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                               _vp, _vp]),
+}
+
+_lib = None
+
+
+def exported_symbols():
+    """Names the header declares (the binding's table)."""
+    return sorted(_SIGS)
+
+
+def load(path=None):
+    """Load libidm.so; raises RuntimeError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libidm.so is not built (%s); run __graft_entry__.build() -- there is no CPU "
+                           "fallback" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class IdmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libidm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def check(ctx, rc):
+    if rc != IDM_OK:
+        msg = load().idm_last_error(ctx)
+        raise IdmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def ptr(t):
+    """Raw device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- same-name thin wrappers ------------------------------------------------
+
+def idm_ctx_create(workspace_cap_bytes=0):
+    h = _vp()
+    rc = load().idm_ctx_create(ctypes.byref(h), workspace_cap_bytes)
+    if rc != IDM_OK:
+        raise IdmError(rc, "idm_ctx_create failed")
+    return h
+
+
+def idm_ctx_destroy(ctx):
+    return load().idm_ctx_destroy(ctx)
+
+
+def idm_last_error(ctx):
+    m = load().idm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def idm_status(ctx, stream=None):
+    flags = ctypes.c_uint32(0)
+    rc = load().idm_status(ctx, ctypes.byref(flags), stream_ptr(stream))
+    return rc, flags.value
+
+
+def idm_set_tuning(ctx, vpt=0, ckpt_interval=16, warps_per_block=8):
+    return check(ctx, load().idm_set_tuning(ctx, vpt, ckpt_interval, warps_per_block))
+
+
+def idm_max_lane_supported():
+    return load().idm_max_lane_supported()
+
+
+def idm_workspace_bytes(ctx, scene, sim):
+    return load().idm_workspace_bytes(ctx, ctypes.byref(scene), ctypes.byref(sim))
+
+
+def idm_layout(ctx, N, n_lanes, lane_id, pos, perm, lane_off, max_lane_out=None, stream=None):
+    return check(ctx, load().idm_layout(ctx, N, n_lanes, ptr(lane_id), ptr(pos), ptr(perm), ptr(lane_off),
+                                        ptr(max_lane_out), stream_ptr(stream)))
+
+
+def idm_gather(ctx, N, perm, srcs, dsts, stream=None):
+    n = len(srcs)
+    s = (_vp * max(n, 1))(*[t.data_ptr() for t in srcs])
+    d = (_vp * max(n, 1))(*[t.data_ptr() for t in dsts])
+    return check(ctx, load().idm_gather(ctx, N, ptr(perm), n, s, d, stream_ptr(stream)))
+
+
+def idm_forward(ctx, scene, params, p_init, v_init, sim, traj=None, vtraj=None, stream=None):
+    return check(ctx, load().idm_forward(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
+                                         ctypes.byref(sim), ptr(traj), ptr(vtraj), stream_ptr(stream)))
+
+
+def idm_backward(ctx, scene, params, p_init, v_init, sim, gP, gV=None, grad=None, grad_p_init=None,
+                 grad_v_init=None, stream=None):
+    return check(ctx, load().idm_backward(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init),
+                                          ptr(v_init), ctypes.byref(sim), ptr(gP), ptr(gV),
+                                          ctypes.byref(grad) if grad is not None else None, ptr(grad_p_init),
+                                          ptr(grad_v_init), stream_ptr(stream)))
+
+
+def idm_loss_grad(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, loss_out=None, grad=None,
+                  grad_p_init=None, grad_v_init=None, stream=None):
+    return check(ctx, load().idm_loss_grad(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init),
+                                           ptr(v_init), ctypes.byref(sim), ptr(targets), obs_stride,
+                                           ptr(loss_out), ctypes.byref(grad) if grad is not None else None,
+                                           ptr(grad_p_init), ptr(grad_v_init), stream_ptr(stream)))
+
+
+def idm_fit(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi,
+            loss_hist=None, stream=None):
+    lo = (ctypes.c_float * 5)(*box_lo)
+    hi = (ctypes.c_float * 5)(*box_hi)
+    return check(ctx, load().idm_fit(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
+                                     ctypes.byref(sim), ptr(targets), obs_stride, n_iter, lr0, lr1, lo, hi,
+                                     ptr(loss_hist), stream_ptr(stream)))
+
+
+# ---- struct builders ---------------------------------------------------------
+
+def make_scene(lane_off, length, max_lane):
+    """lane_off (int32 CUDA tensor [L+1]), length (float32 CUDA tensor [N])."""
+    return idm_scene_t(lane_off.numel() - 1, length.numel(), int(max_lane), lane_off.data_ptr(),
+                       length.data_ptr())
+
+
+def make_params(theta):
+    """theta: float32 CUDA tensor (6, N), rows v0, T, s0, a_max, b, delta (contiguous rows)."""
+    return idm_params_t(*[theta[q].data_ptr() for q in range(6)])
+
+
+def make_sim(K, dt, a_min=-10.0):
+    return idm_sim_t(int(K), float(dt), float(a_min))

@@ -1,0 +1,65 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports
+every entry point include/idm.h declares.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "idm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|int|size_t)\s*\**\s*(idm_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2412_16750_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("idm_ctx_create", "idm_ctx_destroy", "idm_forward", "idm_backward", "idm_loss_grad", "idm_fit",
+                 "idm_layout", "idm_status", "idm_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(libpath):
+    from paper_2412_16750_gb300 import lib
+    assert set(lib.exported_symbols()) == set(header_functions())
+    lib.load(libpath)
+
+
+def test_query_without_device(libpath):
+    from paper_2412_16750_gb300 import lib
+    lib.load(libpath)
+    assert lib.idm_max_lane_supported() == 256
+
+
+def test_null_context_is_rejected(libpath):
+    from paper_2412_16750_gb300 import lib
+    L = lib.load(libpath)
+    assert L.idm_ctx_create(None, 0) == lib.IDM_ERR_ARG
+    assert L.idm_ctx_destroy(None) == lib.IDM_OK
+    assert L.idm_set_tuning(None, 0, 16, 8) == lib.IDM_ERR_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2412_16750_gb300 import lib
+    saved = lib._lib
+    try:
+        lib._lib = None
+        with pytest.raises(RuntimeError, match="no CPU"):
+            lib.load(str(tmp_path / "nope.so"))
+    finally:
+        lib._lib = saved

@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (the workload statement's bar):
+  * positions: max |p_gpu - p_oracle| <= 1e-3 m over 100 steps;
+  * gradients: for each of the six parameters, ||g_gpu - g_ref|| / ||g_ref||
+    <= 1e-4, and every element within 1e-3 * max |g_ref|;
+  * integer work (layout permutation): bit-exact.
+Both sides start from identical float32-representable inputs (dt is the
+float32 value of 0.1 on both sides).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_16750_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = float(np.float32(0.1))
+A_MIN = -10.0
+POS_TOL = 1e-3
+GRAD_RTOL = 1e-4
+GRAD_ELEM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_16750_gb300 import api as _api
+    return _api
+
+
+def cuda(x, dtype=None):
+    dtype = dtype or torch.float32
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def scene_of(api, sc):
+    return api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+
+
+def grad_close(g, ref, rtol=GRAD_RTOL, elem=GRAD_ELEM, rows=range(6)):
+    for q in rows:
+        nr = np.linalg.norm(ref[q])
+        if nr == 0.0:
+            assert np.max(np.abs(g[q])) <= 1e-30 + 1e-6 * np.max(np.abs(ref)), q
+            continue
+        err = np.linalg.norm(g[q] - ref[q]) / nr
+        assert err <= rtol, "param %d: relative error %.3g" % (q, err)
+        assert np.max(np.abs(g[q] - ref[q])) <= elem * np.max(np.abs(ref[q])), q
+
+
+def oracle_loss_grad(sc, theta, Y, K, stride):
+    P, V = oracle.forward(sc["lane_off"], sc["length"], theta, sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    L, gP = oracle.mse_seed(P, Y, stride)
+    g, gp, gv = oracle.adjoint(sc["lane_off"], sc["length"], theta, K, DT, P, V, gP, None, A_MIN)
+    return L, g, gp, gv, P
+
+
+def noisy_targets(sc, K, stride, rng):
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    n_obs = K // stride
+    N = P.shape[1]
+    return synth.f32(P[stride::stride][:n_obs] + rng.normal(0, 0.5, size=(n_obs, N)))
+
+
+def run_loss_grad(api, sc, theta, Y, K, stride, ctx=None):
+    scn = scene_of(api, sc)
+    loss, g, gp, gv = api.loss_grad(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT,
+                                    cuda(Y) if Y.size else None, stride, A_MIN, ctx=ctx)
+    torch.cuda.synchronize()
+    return loss.item(), g.double().cpu().numpy(), gp.double().cpu().numpy(), gv.double().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# config 0: 10 lanes x 100 vehicles, 100 steps
+# ---------------------------------------------------------------------------
+
+def test_forward_config0(api):
+    sc = synth.config0()
+    K = sc["K"]
+    P, V = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    traj, vtraj = api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc),
+                               K, DT, A_MIN, want_speed=True)
+    traj = traj.double().cpu().numpy()
+    vtraj = vtraj.double().cpu().numpy()
+    assert np.max(np.abs(traj - P)) <= POS_TOL
+    assert np.max(np.abs(vtraj - V)) <= 1e-4
+    np.testing.assert_array_equal(traj[0], sc["p_init"])
+
+
+@pytest.mark.parametrize("init", ["plain", "near_truth"])
+def test_loss_grad_config0(api, init):
+    sc = synth.config0()
+    K, s = sc["K"], sc["obs_stride"]
+    Y = noisy_targets(sc, K, s, np.random.default_rng(100))
+    if init == "plain":
+        theta = synth.plain_init(1000)
+    else:
+        theta = synth.f32(sc["theta_true"] * np.random.default_rng(101).uniform(0.95, 1.05, size=(6, 1000)))
+        theta[5] = 4.0
+    L, g, gp, gv, _ = oracle_loss_grad(sc, theta, Y, K, s)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, theta, Y, K, s)
+    assert Lg == pytest.approx(L, rel=1e-5)
+    grad_close(gg, g)
+    grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+
+
+def test_backward_dense_seeds(api):
+    sc = synth.config0()
+    K = 60
+    rng = np.random.default_rng(102)
+    N = 1000
+    gP = synth.f32(rng.normal(size=(K + 1, N)))
+    gV = synth.f32(rng.normal(size=(K + 1, N)))
+    theta = sc["theta_true"]
+    P, V = oracle.forward(sc["lane_off"], sc["length"], theta, sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    g, gp, gv = oracle.adjoint(sc["lane_off"], sc["length"], theta, K, DT, P, V, gP, gV, A_MIN)
+    gg, gpg, gvg = api.backward(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT,
+                                cuda(gP), cuda(gV), A_MIN)
+    grad_close(gg.double().cpu().numpy(), g)
+    grad_close(np.stack([gpg.double().cpu().numpy(), gvg.double().cpu().numpy()]), np.stack([gp, gv]),
+               rows=range(2))
+
+
+def test_autograd_function(api):
+    sc = synth.config0()
+    K = 40
+    rng = np.random.default_rng(103)
+    w = synth.f32(rng.normal(size=(K + 1, 1000)))
+    th = cuda(sc["theta_true"]).requires_grad_(True)
+    p0 = cuda(sc["p_init"]).requires_grad_(True)
+    v0 = cuda(sc["v_init"]).requires_grad_(True)
+    traj = api.IdmFunction.apply(th, p0, v0, scene_of(api, sc), K, DT, A_MIN)
+    (traj * cuda(w)).sum().backward()
+    P, V = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    g, gp, gv = oracle.adjoint(sc["lane_off"], sc["length"], sc["theta_true"], K, DT, P, V, w, None, A_MIN)
+    grad_close(th.grad.double().cpu().numpy(), g)
+    grad_close(np.stack([p0.grad.double().cpu().numpy(), v0.grad.double().cpu().numpy()]), np.stack([gp, gv]),
+               rows=range(2))
+
+
+# ---------------------------------------------------------------------------
+# edge shapes, kernel variants, checkpoint intervals
+# ---------------------------------------------------------------------------
+
+EDGE_COUNTS = [1, 2, 3, 33, 0, 17, 31, 32, 1, 5]
+
+
+@pytest.mark.parametrize("vpt,C", [(2, 1), (2, 7), (4, 16), (8, 5), (0, 64)])
+def test_edge_lanes(api, vpt, C):
+    rng = np.random.default_rng(104)
+    sc = synth.make_scene(EDGE_COUNTS, rng)
+    K, s = 37, 3
+    Y = noisy_targets(sc, K, s, rng)
+    N = int(sc["lane_off"][-1])
+    theta = synth.f32(sc["theta_true"] * rng.uniform(0.8, 1.2, size=(6, N)))
+    L, g, gp, gv, _ = oracle_loss_grad(sc, theta, Y, K, s)
+    ctx = api.Context(vpt=vpt, ckpt_interval=C, warps_per_block=4)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, theta, Y, K, s, ctx=ctx)
+    assert ctx.check_status() == 0
+    assert Lg == pytest.approx(L, rel=1e-5)
+    grad_close(gg, g)
+    grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+
+
+def test_single_step(api):
+    rng = np.random.default_rng(105)
+    sc = synth.make_scene([4, 9], rng)
+    Y = noisy_targets(sc, 1, 1, rng)
+    L, g, gp, gv, _ = oracle_loss_grad(sc, sc["theta_true"], Y, 1, 1)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, sc["theta_true"], Y, 1, 1)
+    assert Lg == pytest.approx(L, rel=1e-5)
+    grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+    grad_close(gg, g, rows=[0, 3, 5])
+
+
+def test_stride_beyond_horizon(api):
+    rng = np.random.default_rng(106)
+    sc = synth.make_scene([6, 6], rng)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, sc["theta_true"], np.zeros((0, 12)), 9, 10)
+    assert Lg == 0.0 and np.all(gg == 0.0) and np.all(gpg == 0.0) and np.all(gvg == 0.0)
+
+
+def test_long_horizon_positions(api):
+    """1,000 steps: the float32 pair keeps positions close to FP64."""
+    rng = np.random.default_rng(107)
+    sc = synth.make_scene([100] * 4, rng)
+    K = 1000
+    P, V = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    traj = api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT,
+                        A_MIN).double().cpu().numpy()
+    assert np.max(np.abs(traj - P)) <= 5e-3
+
+
+# ---------------------------------------------------------------------------
+# fit, layout
+# ---------------------------------------------------------------------------
+
+def test_fit_config0(api):
+    sc = synth.config0()
+    K, s = sc["K"], sc["obs_stride"]
+    Y = noisy_targets(sc, K, s, np.random.default_rng(108))
+    n_iter = 5
+    th0 = synth.plain_init(1000)
+    th_ref, hist_ref = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, DT, Y, s, n_iter,
+                                  0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    th = cuda(th0)
+    hist = api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, cuda(Y), s, n_iter, 0.1,
+                   0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(hist.cpu().numpy(), hist_ref, rtol=1e-5)
+    np.testing.assert_allclose(th.double().cpu().numpy(), th_ref, rtol=1e-4, atol=1e-5)
+
+
+def test_layout_bitexact(api):
+    rng = np.random.default_rng(109)
+    N, L = 20000, 613
+    lane = rng.integers(0, L, size=N).astype(np.int32)
+    pos = synth.f32(rng.uniform(-3000, 0, size=N))
+    pos[::11] = pos[3]
+    pos[::13] = 0.0
+    pos[::17] = -0.0
+    perm_ref, off_ref = oracle.layout(lane, pos, L)
+    perm, off, mx = api.layout(cuda(lane, torch.int32), cuda(pos), L)
+    np.testing.assert_array_equal(perm.cpu().numpy(), perm_ref)
+    np.testing.assert_array_equal(off.cpu().numpy(), off_ref)
+    assert int(mx.item()) == int(np.diff(off_ref).max())
+    dst = api.gather(perm, [cuda(pos)])[0].cpu().numpy()
+    np.testing.assert_array_equal(dst, pos[perm_ref].astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# errors and status
+# ---------------------------------------------------------------------------
+
+def test_argument_errors(api):
+    from paper_2412_16750_gb300 import lib
+    sc = synth.make_scene([3, 3], np.random.default_rng(110))
+    scn = scene_of(api, sc)
+    th, p0, v0 = cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"])
+    with pytest.raises(lib.IdmError) as e:
+        api.simulate(th, p0, v0, scn, 0, DT)
+    assert e.value.code == lib.IDM_ERR_ARG
+    with pytest.raises(lib.IdmError) as e:
+        api.simulate(th, p0, v0, scn, 5, -0.1)
+    assert e.value.code == lib.IDM_ERR_ARG
+    with pytest.raises(lib.IdmError) as e:
+        api.loss_grad(th, p0, v0, scn, 5, DT, cuda(np.zeros((5, 6))), 0)
+    assert e.value.code == lib.IDM_ERR_ARG
+    big = api.Scene(scn.lane_off, scn.length, 300)
+    with pytest.raises(lib.IdmError) as e:
+        api.simulate(th, p0, v0, big, 5, DT)
+    assert e.value.code == lib.IDM_ERR_ARG
+    ctx = api.Context(workspace_cap_bytes=64)
+    with pytest.raises(lib.IdmError) as e:
+        api.loss_grad(th, p0, v0, scn, 5, DT, cuda(np.zeros((5, 6))), 1, ctx=ctx)
+    assert e.value.code == lib.IDM_ERR_WORKSPACE
+
+
+def test_device_status_lane_too_long(api):
+    from paper_2412_16750_gb300 import lib
+    sc = synth.make_scene([40, 3], np.random.default_rng(111))
+    ctx = api.Context(vpt=1)
+    scn = api.Scene(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]), 32)  # understated max_lane
+    traj = api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 5, DT, ctx=ctx)
+    rc, flags = ctx.status()
+    assert rc == lib.IDM_ERR_LANE and flags & lib.IDM_STATUS_LANE_TOO_LONG
+    # the short lane is still simulated
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], 5, DT, A_MIN)
+    np.testing.assert_allclose(traj[:, 40:].double().cpu().numpy(), P[:, 40:], atol=POS_TOL)
+    assert ctx.status()[0] == lib.IDM_OK  # cleared
+
+
+def test_device_status_bad_lane_off(api):
+    from paper_2412_16750_gb300 import lib
+    sc = synth.make_scene([4, 4, 4], np.random.default_rng(112))
+    ctx = api.Context()
+    bad = np.array([0, 9, 4, 12], dtype=np.int32)  # not monotone
+    scn = api.Scene(cuda(bad, torch.int32), cuda(sc["length"]), 9)
+    api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 3, DT, ctx=ctx)
+    rc, flags = ctx.status()
+    assert rc == lib.IDM_ERR_LANE and flags & lib.IDM_STATUS_BAD_LANE_OFF
+    over = np.array([0, 4, 8, 99], dtype=np.int32)  # past the last vehicle: never read
+    scn = api.Scene(cuda(over, torch.int32), cuda(sc["length"]), 91)
+    api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 3, DT, ctx=ctx)
+    rc, flags = ctx.status()
+    assert rc == lib.IDM_ERR_LANE and flags & lib.IDM_STATUS_BAD_LANE_OFF
+
+
+def test_device_status_nonfinite(api):
+    from paper_2412_16750_gb300 import lib
+    sc = synth.make_scene([5], np.random.default_rng(113))
+    th = sc["theta_true"].copy()
+    th[3, 2] = np.nan
+    ctx = api.Context()
+    api.simulate(cuda(th), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), 4, DT, ctx=ctx)
+    rc, flags = ctx.status()
+    assert rc == lib.IDM_ERR_NONFINITE and flags & lib.IDM_STATUS_NONFINITE
+
+
+# ---------------------------------------------------------------------------
+# full size: 20,000 lanes x 100 vehicles x 1,000 steps, sampled lanes
+# ---------------------------------------------------------------------------
+
+def test_full_size_sampled_lanes(api):
+    """The paper-scale workload in the launch configuration the benchmark
+    uses; the oracle recomputes 12 sampled lanes (lanes are independent)."""
+    sc = synth.config1()
+    K = sc["K"]
+    N = int(sc["lane_off"][-1])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(20241217)
+    p0, v0 = cuda(sc["p_init"]), cuda(sc["v_init"])
+    k = torch.arange(1, K + 1, device="cuda", dtype=torch.float32)[:, None]
+    Y = (p0[None, :] + k * DT * v0[None, :] + 0.5 * torch.randn((K, N), device="cuda", generator=gen)).contiguous()
+    theta = synth.plain_init(N)
+    th = cuda(theta)
+    loss, g, gp, gv = api.loss_grad(th, p0, v0, scene_of(api, sc), K, DT, Y, 1, A_MIN)
+    torch.cuda.synchronize()
+    lanes = np.random.default_rng(114).choice(20000, size=12, replace=False)
+    lo = sc["lane_off"]
+    g = g.double().cpu().numpy()
+    gp = gp.double().cpu().numpy()
+    for l in lanes:
+        a, e = int(lo[l]), int(lo[l + 1])
+        sub = dict(lane_off=np.array([0, e - a], dtype=np.int32), length=sc["length"][a:e], p_init=sc["p_init"][a:e],
+                   v_init=sc["v_init"][a:e])
+        Ys = Y[:, a:e].double().cpu().numpy()
+        L, gr, gpr, gvr, P = oracle_loss_grad(sub, theta[:, a:e], Ys, K, 1)
+        grad_close(g[:, a:e], gr)
+        grad_close(gp[None, a:e], gpr[None], rows=[0])
+    # forward positions of the sampled lanes over all 1,000 steps
+    traj = api.simulate(th, p0, v0, scene_of(api, sc), K, DT, A_MIN)
+    for l in lanes[:4]:
+        a, e = int(lo[l]), int(lo[l + 1])
+        P, _ = oracle.forward(np.array([0, e - a], dtype=np.int32), sc["length"][a:e], theta[:, a:e],
+                              sc["p_init"][a:e], sc["v_init"][a:e], K, DT, A_MIN)
+        assert np.max(np.abs(traj[:, a:e].double().cpu().numpy() - P)) <= 5e-3
