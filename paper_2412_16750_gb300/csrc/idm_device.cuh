@@ -70,10 +70,13 @@ __device__ __forceinline__ VehConst ghost_const()
     return k;
 }
 
-// (v / v0)^delta, with the delta == 4 case as two squarings.
+// (v / v0)^delta.  D4: every vehicle of the warp has delta == 4 (decided
+// once per segment), so the power is two squarings and the step body has no
+// per-vehicle branch.
+template <bool D4>
 __device__ __forceinline__ float pow_delta(float r, float delta)
 {
-    if (delta == 4.0f) {
+    if (D4) {
         float r2 = __fmul_rn(r, r);
         return __fmul_rn(r2, r2);
     }
@@ -82,6 +85,7 @@ __device__ __forceinline__ float pow_delta(float r, float delta)
 
 // Bounded acceleration a* of one vehicle from its speed v, its raw gap
 // (p_h - p - length_h; +inf for a lane head) and its leader's speed vh.
+template <bool D4>
 __device__ __forceinline__ float accel_star(float v, float gap_raw, float vh, const VehConst &k,
                                             float inv_dt, float a_min)
 {
@@ -91,7 +95,7 @@ __device__ __forceinline__ float accel_star(float v, float gap_raw, float vh, co
     Soft s1 = softplus(s_opt);                                     // Sec. III-C
     float z = __fmul_rn(s1.sp, rcp_approx(gap));                   // 0 for a head
     float r = __fmul_rn(v, k.inv_v0);
-    float rd = pow_delta(r, k.delta);
+    float rd = pow_delta<D4>(r, k.delta);
     float a = __fmul_rn(k.am, __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z)));  // Eq. 2
     float lbv = -__fmul_rn(v, inv_dt);
     float a_lb = lbv > a_min ? lbv : a_min;                        // Sec. III-C
@@ -191,7 +195,7 @@ struct AdjTerms {
     float w, w_v, w_vdv, f_a, f_rd, f_rdlnr;
 };
 
-template <bool WANT_DELTA>
+template <bool WANT_DELTA, bool D4>
 __device__ __forceinline__ AdjTerms adjoint_terms(float mu, float v, float gap_raw, float vh,
                                                   const VehConst &k, float inv_dt, float a_min)
 {
@@ -206,7 +210,7 @@ __device__ __forceinline__ AdjTerms adjoint_terms(float mu, float v, float gap_r
     float z = __fmul_rn(s1.sp, inv_gap);
     float r = __fmul_rn(v, k.inv_v0);
     float rd, rdm1;
-    if (k.delta == 4.0f) {
+    if (D4) {
         float r2 = __fmul_rn(r, r);
         rd = __fmul_rn(r2, r2);
         rdm1 = __fmul_rn(r2, r);

@@ -185,13 +185,98 @@ __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, i
     }
 }
 
+
+// True when every occupied slot of the warp segment has delta == 4, so the
+// step body can use the squaring form of (v/v0)^delta with no branch.
+template <int VPT>
+__device__ __forceinline__ bool segment_is_d4(const VehConst (&kc)[VPT], const bool (&valid)[VPT])
+{
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j)
+        if (valid[j] && kc[j].delta != 4.0f) ok = false;
+    return __all_sync(FULL, ok);
+}
+
 // ---------------------------------------------------------------------------
 // Forward: K steps per segment, optional trajectory / speed output, fused
 // squared-error loss, checkpoints every C steps.
 // ---------------------------------------------------------------------------
+struct FwdFlags {
+    bool traj, vtraj, loss, ckpt;
+};
+
+template <int VPT, bool D4>
+__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, int lane,
+                                                const VehConst (&kc)[VPT], State (&st)[VPT], const float (&pin)[VPT],
+                                                const bool (&valid)[VPT], FwdFlags f)
+{
+    const int Ns = sc.n_veh;
+    float lsum = 0.0f, lcomp = 0.0f;
+    int next_obs = sc.obs_stride, obs_row = 0;
+    int next_ck = 0, ck_idx = 0;
+    for (int k = 0;; ++k) {
+        if (f.ckpt && k == next_ck && k < sc.K) {
+            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + lb;
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if (!valid[j]) continue;
+                const int q = lane + 32 * j;
+                base[q] = st[j].xh;
+                base[(size_t)Ns + q] = st[j].xl;
+                base[2 * (size_t)Ns + q] = st[j].v;
+                base[3 * (size_t)Ns + q] = st[j].gap;
+            }
+            next_ck += a.C;
+            ++ck_idx;
+        }
+        if (f.traj || f.vtraj) {
+            const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if (!valid[j]) continue;
+                const int q = lane + 32 * j;
+                if (f.traj) a.traj[row + q] = position(pin[j], st[j]);
+                if (f.vtraj) a.vtraj[row + q] = st[j].v;
+            }
+        }
+        if (f.loss && k == next_obs && obs_row < sc.n_obs) {
+            const float *y = a.targets + sc.tgt_off + (size_t)obs_row * Ns + lb;
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if (!valid[j]) continue;
+                float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
+                kahan_add(lsum, lcomp, __fmul_rn(r, r));
+            }
+            next_obs += sc.obs_stride;
+            ++obs_row;
+        }
+        if (k == sc.K) break;
+
+        float vcur[VPT], vh[VPT];
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
+        leader_vals<VPT>(vcur, vh, lane);
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
+            euler(st[j], as, vh[j], sc.dt);
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j)
+        if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].xh))) bad = true;
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (f.loss) {
+        double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.loss_part[s_idx] = part;
+    }
+}
+
 template <int VPT>
 __global__ void __launch_bounds__(512)
-forward_kernel(SimArgs a, bool want_traj, bool want_vtraj, bool want_loss, bool want_ckpt)
+forward_kernel(SimArgs a, FwdFlags f)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -199,75 +284,16 @@ forward_kernel(SimArgs a, bool want_traj, bool want_vtraj, bool want_loss, bool 
         if (s_idx >= *a.n_seg) break;
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
-        const int Ns = sc.n_veh;
         const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
-
         VehConst kc[VPT];
         State st[VPT];
         float pin[VPT];
         bool valid[VPT];
         load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
-
-        float lsum = 0.0f, lcomp = 0.0f;
-        int next_obs = sc.obs_stride, obs_row = 0;
-        int next_ck = 0, ck_idx = 0;
-        for (int k = 0;; ++k) {
-            if (want_ckpt && k == next_ck && k < sc.K) {
-                float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + lb;
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    const int q = lane + 32 * j;
-                    base[q] = st[j].xh;
-                    base[(size_t)Ns + q] = st[j].xl;
-                    base[2 * (size_t)Ns + q] = st[j].v;
-                    base[3 * (size_t)Ns + q] = st[j].gap;
-                }
-                next_ck += a.C;
-                ++ck_idx;
-            }
-            if (want_traj || want_vtraj) {
-                const size_t row = sc.traj_off + (size_t)k * Ns + lb;
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    const int q = lane + 32 * j;
-                    if (want_traj) a.traj[row + q] = position(pin[j], st[j]);
-                    if (want_vtraj) a.vtraj[row + q] = st[j].v;
-                }
-            }
-            if (want_loss && k == next_obs && obs_row < sc.n_obs) {
-                const float *y = a.targets + sc.tgt_off + (size_t)obs_row * Ns + lb;
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
-                    kahan_add(lsum, lcomp, __fmul_rn(r, r));
-                }
-                next_obs += sc.obs_stride;
-                ++obs_row;
-            }
-            if (k == sc.K) break;
-
-            float vcur[VPT], vh[VPT];
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-            leader_vals<VPT>(vcur, vh, lane);
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                float as = accel_star(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
-                euler(st[j], as, vh[j], sc.dt);
-            }
-        }
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < VPT; ++j)
-            if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].xh))) bad = true;
-        if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
-        if (want_loss) {
-            double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
-            if (lane == 0) a.loss_part[s_idx] = part;
-        }
+        if (segment_is_d4<VPT>(kc, valid))
+            forward_segment<VPT, true>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f);
+        else
+            forward_segment<VPT, false>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f);
     }
 }
 
@@ -278,8 +304,8 @@ forward_kernel(SimArgs a, bool want_traj, bool want_vtraj, bool want_loss, bool 
 //   lp_k = seed_k + lp_{k+1} + mu A_p + mu_f A_ph(f)
 //   lv_k = dt lp_{k+1} + lv_{k+1} + mu A_v + mu_f A_vh(f)
 // with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle.
-// Parameter gradients accumulate per segment in float and across segments
-// with Kahan compensation.
+// Parameter gradients accumulate in float per checkpoint segment and the
+// segment sums are added into the totals (pairwise-style summation).
 // ---------------------------------------------------------------------------
 template <int VPT, bool DENSE>
 __device__ __forceinline__ float *tape_base(float *smem, int C)
@@ -288,229 +314,235 @@ __device__ __forceinline__ float *tape_base(float *smem, int C)
     return smem + (threadIdx.x >> 5) * per_warp;
 }
 
-template <int VPT, bool DENSE, bool ADAM>
+template <int VPT, bool DENSE, bool ADAM, bool WD, bool D4>
+__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int lb,
+                                                 int lane, float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
+                                                 const float (&pin)[VPT], const bool (&valid)[VPT])
+{
+    constexpr int SL = 32 * VPT;
+    float *tg = tv + a.C * SL;
+    float *tr = tg + a.C * SL;  // seeds (MSE only)
+    const int Ns = sc.n_veh;
+    const float dt = sc.dt;
+    const float seed_scale = 2.0f * sc.inv_nobs;
+
+    float lp[VPT], lv[VPT];
+    float acc[6][VPT];
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+        lp[j] = 0.0f;
+        lv[j] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q][j] = 0.0f;
+    }
+
+    const int n_ck = (sc.K + a.C - 1) / a.C;
+    for (int cs = n_ck - 1; cs >= 0; --cs) {
+        const int c0 = cs * a.C;
+        const int n = min(a.C, sc.K - c0);
+        {
+            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + lb;
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                if (!valid[j]) continue;
+                const int q = lane + 32 * j;
+                st[j] = State{base[q], base[(size_t)Ns + q], base[2 * (size_t)Ns + q], base[3 * (size_t)Ns + q]};
+            }
+        }
+        // recompute the segment into the tape
+        int obs_k = ((c0 + sc.obs_stride - 1) / sc.obs_stride) * sc.obs_stride;  // first observed step >= c0
+        if (obs_k == 0) obs_k = sc.obs_stride;
+        for (int s = 0; s < n; ++s) {
+            const int k = c0 + s;
+            float *rv = tv + s * SL, *rg = tg + s * SL;
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                rv[lane + 32 * j] = st[j].v;
+                rg[lane + 32 * j] = st[j].gap;
+            }
+            if (!DENSE && k == obs_k) {
+                if (k / sc.obs_stride <= sc.n_obs) {
+                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
+                    float *rr = tr + s * SL;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j) {
+                        float r = valid[j] ? residual(pin[j], st[j], __ldg(y + lane + 32 * j)) : 0.0f;
+                        rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
+                    }
+                }
+                obs_k += sc.obs_stride;
+            }
+            float vcur[VPT], vh[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
+            leader_vals<VPT>(vcur, vh, lane);
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
+                euler(st[j], as, vh[j], dt);
+            }
+        }
+        if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)sc.K * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    lp[j] = a.gP[row + lane + 32 * j];
+                    lv[j] = a.gV ? a.gV[row + lane + 32 * j] : 0.0f;
+                }
+            } else {
+                const int k = sc.K;
+                const bool obs = sc.n_obs > 0 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
+                if (obs) {
+                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j)
+                        if (valid[j]) lp[j] = __fmul_rn(seed_scale, residual(pin[j], st[j], __ldg(y + lane + 32 * j)));
+                }
+            }
+        }
+        __syncwarp();
+
+        float sacc[6][VPT];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) sacc[q][j] = 0.0f;
+
+        // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
+        int obs_hi = ((c0 + n - 1) / sc.obs_stride) * sc.obs_stride;
+        for (int s = n - 1; s >= 0; --s) {
+            const int k = c0 + s;
+            const float *rv = tv + s * SL, *rg = tg + s * SL;
+            float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                const int q = lane + 32 * j;
+                const float v = rv[q];
+                const float gap = rg[q];
+                const float vh = q > 0 ? rv[q - 1] : 0.0f;
+                const float mu = __fmul_rn(dt, lv[j]);
+                AdjTerms t = adjoint_terms<WD, D4>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
+                own_p[j] = t.own_p;
+                own_v[j] = t.own_v;
+                to_lp[j] = t.lead_p;
+                to_lv[j] = t.lead_v;
+                sacc[0][j] += t.w;
+                sacc[1][j] += t.w_v;
+                sacc[2][j] += t.w_vdv;
+                sacc[3][j] += t.f_a;
+                sacc[4][j] += t.f_rd;
+                if (WD) sacc[5][j] += t.f_rdlnr;
+            }
+            float from_p[VPT], from_v[VPT];
+            follower_vals<VPT>(to_lp, from_p, lane);
+            follower_vals<VPT>(to_lv, from_v, lane);
+            float seed_p[VPT], seed_v[VPT];
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) { seed_p[j] = 0.0f; seed_v[j] = 0.0f; }
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    if (!valid[j]) continue;
+                    seed_p[j] = a.gP[row + lane + 32 * j];
+                    if (a.gV) seed_v[j] = a.gV[row + lane + 32 * j];
+                }
+            } else if (k == obs_hi) {
+                if (k >= 1 && k / sc.obs_stride <= sc.n_obs) {
+                    const float *rr = tr + s * SL;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
+                }
+                obs_hi -= sc.obs_stride;
+            }
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) {
+                float nlp = lp[j] + own_p[j] + from_p[j] + seed_p[j];
+                float nlv = dt * lp[j] + lv[j] + own_v[j] + from_v[j] + seed_v[j];
+                lp[j] = nlp;
+                lv[j] = nlv;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int j = 0; j < VPT; ++j) acc[q][j] += sacc[q][j];
+        __syncwarp();
+    }
+
+    // epilogue: parameter gradients from the factored sums
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < VPT; ++j) {
+        if (!valid[j]) continue;
+        const int q = lane + 32 * j;
+        const int gi = sg.veh_begin + q;
+        const float v0 = a.v0[gi], b = a.b[gi];
+        const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
+        float g[6];
+        g[0] = am * dl * acc[4][j] / v0;                 // v0
+        g[1] = acc[1][j];                                // T
+        g[2] = acc[0][j];                                // s0
+        g[3] = acc[3][j] - acc[2][j] * c / (2.0f * am);  // a_max
+        g[4] = -acc[2][j] * c / (2.0f * b);              // b
+        g[5] = -am * acc[5][j];                          // delta
+        for (int p = 0; p < 6; ++p) bad |= !isfinite(g[p]);
+        if (ADAM) {
+            const int it = *a.iter;
+            const int t = it + 1;
+            const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+            const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
+            float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                            const_cast<float *>(a.am), const_cast<float *>(a.b)};
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                const size_t mi = (size_t)p * a.N_total + gi;
+                float m = 0.9f * a.adam_m[mi] + 0.1f * g[p];
+                float vv = 0.999f * a.adam_v[mi] + 0.001f * g[p] * g[p];
+                a.adam_m[mi] = m;
+                a.adam_v[mi] = vv;
+                float x = th[p][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+                x = fminf(fmaxf(x, a.lo[p]), a.hi[p]);
+                th[p][gi] = x;
+            }
+        } else {
+            if (a.g_v0) a.g_v0[gi] = g[0];
+            if (a.g_T) a.g_T[gi] = g[1];
+            if (a.g_s0) a.g_s0[gi] = g[2];
+            if (a.g_am) a.g_am[gi] = g[3];
+            if (a.g_b) a.g_b[gi] = g[4];
+            if (a.g_delta) a.g_delta[gi] = WD ? g[5] : 0.0f;
+            if (a.g_p_init) a.g_p_init[gi] = lp[j];
+            if (a.g_v_init) a.g_v_init[gi] = lv[j];
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+}
+
+template <int VPT, bool DENSE, bool ADAM, bool WD>
 __global__ void __launch_bounds__(256)
-backward_kernel(SimArgs a, bool want_delta)
+backward_kernel(SimArgs a)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
-    constexpr int SL = 32 * VPT;
     float *tv = tape_base<VPT, DENSE>(smem, a.C);
-    float *tg = tv + a.C * SL;
-    float *tr = tg + a.C * SL;  // seeds (MSE only)
-
     for (;;) {
         const int s_idx = next_segment(a.work, lane);
         if (s_idx >= *a.n_seg) break;
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
-        const int Ns = sc.n_veh;
         const int lb = sg.veh_begin - sc.veh_begin;
-        const float dt = sc.dt;
-        const float seed_scale = 2.0f * sc.inv_nobs;
-
         VehConst kc[VPT];
         State st[VPT];
         float pin[VPT];
         bool valid[VPT];
         load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
-
-        float lp[VPT], lv[VPT];
-        float acc[6][VPT], cmp[6][VPT];
-#pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            lp[j] = 0.0f;
-            lv[j] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) { acc[q][j] = 0.0f; cmp[q][j] = 0.0f; }
-        }
-
-        const int n_ck = (sc.K + a.C - 1) / a.C;
-        for (int cs = n_ck - 1; cs >= 0; --cs) {
-            const int c0 = cs * a.C;
-            const int n = min(a.C, sc.K - c0);
-            {
-                const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + lb;
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    const int q = lane + 32 * j;
-                    st[j] = State{base[q], base[(size_t)Ns + q], base[2 * (size_t)Ns + q], base[3 * (size_t)Ns + q]};
-                }
-            }
-            // recompute the segment into the tape
-            for (int s = 0; s < n; ++s) {
-                const int k = c0 + s;
-                float *rv = tv + s * SL, *rg = tg + s * SL;
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    rv[lane + 32 * j] = st[j].v;
-                    rg[lane + 32 * j] = st[j].gap;
-                }
-                if (!DENSE) {
-                    const bool obs = k >= 1 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
-                    if (obs) {
-                        const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
-                        float *rr = tr + s * SL;
-#pragma unroll
-                        for (int j = 0; j < VPT; ++j) {
-                            float r = valid[j] ? residual(pin[j], st[j], __ldg(y + lane + 32 * j)) : 0.0f;
-                            rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
-                        }
-                    }
-                }
-                float vcur[VPT], vh[VPT];
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-                leader_vals<VPT>(vcur, vh, lane);
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    float as = accel_star(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
-                    euler(st[j], as, vh[j], dt);
-                }
-            }
-            if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
-                if (DENSE) {
-                    const size_t row = sc.traj_off + (size_t)sc.K * Ns + lb;
-#pragma unroll
-                    for (int j = 0; j < VPT; ++j) {
-                        if (!valid[j]) continue;
-                        lp[j] = a.gP[row + lane + 32 * j];
-                        lv[j] = a.gV ? a.gV[row + lane + 32 * j] : 0.0f;
-                    }
-                } else {
-                    const int k = sc.K;
-                    const bool obs = (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs && sc.n_obs > 0;
-                    if (obs) {
-                        const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
-#pragma unroll
-                        for (int j = 0; j < VPT; ++j)
-                            if (valid[j])
-                                lp[j] = __fmul_rn(seed_scale, residual(pin[j], st[j], __ldg(y + lane + 32 * j)));
-                    }
-                }
-            }
-            __syncwarp();
-
-            float sacc[6][VPT];
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) sacc[q][j] = 0.0f;
-
-            for (int s = n - 1; s >= 0; --s) {
-                const int k = c0 + s;
-                const float *rv = tv + s * SL, *rg = tg + s * SL;
-                float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    const int q = lane + 32 * j;
-                    const float v = rv[q];
-                    const float gap = rg[q];
-                    const float vh = q > 0 ? rv[q - 1] : 0.0f;
-                    const float mu = __fmul_rn(dt, lv[j]);
-                    AdjTerms t;
-                    if (want_delta)
-                        t = adjoint_terms<true>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
-                    else
-                        t = adjoint_terms<false>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
-                    own_p[j] = t.own_p;
-                    own_v[j] = t.own_v;
-                    to_lp[j] = t.lead_p;
-                    to_lv[j] = t.lead_v;
-                    sacc[0][j] += t.w;
-                    sacc[1][j] += t.w_v;
-                    sacc[2][j] += t.w_vdv;
-                    sacc[3][j] += t.f_a;
-                    sacc[4][j] += t.f_rd;
-                    sacc[5][j] += t.f_rdlnr;
-                }
-                float from_p[VPT], from_v[VPT];
-                follower_vals<VPT>(to_lp, from_p, lane);
-                follower_vals<VPT>(to_lv, from_v, lane);
-                float seed_p[VPT], seed_v[VPT];
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) { seed_p[j] = 0.0f; seed_v[j] = 0.0f; }
-                if (DENSE) {
-                    const size_t row = sc.traj_off + (size_t)k * Ns + lb;
-#pragma unroll
-                    for (int j = 0; j < VPT; ++j) {
-                        if (!valid[j]) continue;
-                        seed_p[j] = a.gP[row + lane + 32 * j];
-                        if (a.gV) seed_v[j] = a.gV[row + lane + 32 * j];
-                    }
-                } else {
-                    const bool obs = k >= 1 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
-                    if (obs) {
-                        const float *rr = tr + s * SL;
-#pragma unroll
-                        for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    float nlp = lp[j] + own_p[j] + from_p[j] + seed_p[j];
-                    float nlv = dt * lp[j] + lv[j] + own_v[j] + from_v[j] + seed_v[j];
-                    lp[j] = nlp;
-                    lv[j] = nlv;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) kahan_add(acc[q][j], cmp[q][j], sacc[q][j]);
-            __syncwarp();
-        }
-
-        // epilogue: parameter gradients from the factored sums
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            if (!valid[j]) continue;
-            const int q = lane + 32 * j;
-            const int gi = sg.veh_begin + q;
-            const float v0 = a.v0[gi], b = a.b[gi];
-            const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
-            const float W = acc[0][j] - cmp[0][j], Wv = acc[1][j] - cmp[1][j], Wvdv = acc[2][j] - cmp[2][j];
-            const float Fa = acc[3][j] - cmp[3][j], Frd = acc[4][j] - cmp[4][j], Fl = acc[5][j] - cmp[5][j];
-            float g[6];
-            g[0] = am * dl * Frd / v0;                 // v0
-            g[1] = Wv;                                 // T
-            g[2] = W;                                  // s0
-            g[3] = Fa - Wvdv * c / (2.0f * am);        // a_max
-            g[4] = -Wvdv * c / (2.0f * b);             // b
-            g[5] = -am * Fl;                           // delta
-            for (int p = 0; p < 6; ++p) bad |= !isfinite(g[p]);
-            if (ADAM) {
-                const int it = *a.iter;
-                const int t = it + 1;
-                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
-                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
-                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
-                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
-#pragma unroll
-                for (int p = 0; p < 5; ++p) {
-                    const size_t mi = (size_t)p * a.N_total + gi;
-                    float m = 0.9f * a.adam_m[mi] + 0.1f * g[p];
-                    float vv = 0.999f * a.adam_v[mi] + 0.001f * g[p] * g[p];
-                    a.adam_m[mi] = m;
-                    a.adam_v[mi] = vv;
-                    float x = th[p][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
-                    x = fminf(fmaxf(x, a.lo[p]), a.hi[p]);
-                    th[p][gi] = x;
-                }
-            } else {
-                if (a.g_v0) a.g_v0[gi] = g[0];
-                if (a.g_T) a.g_T[gi] = g[1];
-                if (a.g_s0) a.g_s0[gi] = g[2];
-                if (a.g_am) a.g_am[gi] = g[3];
-                if (a.g_b) a.g_b[gi] = g[4];
-                if (a.g_delta) a.g_delta[gi] = g[5];
-                if (a.g_p_init) a.g_p_init[gi] = lp[j];
-                if (a.g_v_init) a.g_v_init[gi] = lv[j];
-            }
-        }
-        if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+        if (segment_is_d4<VPT>(kc, valid))
+            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, lb, lane, tv, kc, st, pin, valid);
+        else
+            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, lb, lane, tv, kc, st, pin, valid);
     }
 }
 
@@ -553,11 +585,12 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt,
                            int wpb, cudaStream_t st)
 {
     dim3 blk(32 * wpb);
+    FwdFlags f{traj, vtraj, loss, ckpt};
     switch (vpt) {
-    case 1: forward_kernel<1><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
-    case 2: forward_kernel<2><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
-    case 4: forward_kernel<4><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
-    case 8: forward_kernel<8><<<grid, blk, 0, st>>>(a, traj, vtraj, loss, ckpt); break;
+    case 1: forward_kernel<1><<<grid, blk, 0, st>>>(a, f); break;
+    case 2: forward_kernel<2><<<grid, blk, 0, st>>>(a, f); break;
+    case 4: forward_kernel<4><<<grid, blk, 0, st>>>(a, f); break;
+    case 8: forward_kernel<8><<<grid, blk, 0, st>>>(a, f); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -568,73 +601,59 @@ size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb)
     return (size_t)(dense_seed ? 2 : 3) * C * 32 * vpt * sizeof(float) * wpb;
 }
 
-template <int VPT, bool DENSE, bool ADAM>
-static cudaError_t launch_bwd_t(const SimArgs &a, bool want_delta, int grid, int wpb, cudaStream_t st)
+// Kernel variants of the adjoint: seeds from dense gradients or from targets,
+// fused Adam or gradient output, with or without the delta gradient.
+template <int VPT>
+static void *backward_fn(bool dense, bool adam, bool wd)
 {
-    size_t smem = backward_smem_bytes(VPT, DENSE, a.C, wpb);
-    auto fn = backward_kernel<VPT, DENSE, ADAM>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, 32 * wpb, smem, st>>>(a, want_delta);
-    return cudaGetLastError();
+    if (dense) return wd ? (void *)backward_kernel<VPT, true, false, true> : (void *)backward_kernel<VPT, true, false, false>;
+    if (adam) return (void *)backward_kernel<VPT, false, true, false>;
+    return wd ? (void *)backward_kernel<VPT, false, false, true> : (void *)backward_kernel<VPT, false, false, false>;
 }
 
-template <int VPT>
-static cudaError_t launch_bwd_v(bool dense, bool adam, bool want_delta, const SimArgs &a, int grid, int wpb,
-                                cudaStream_t st)
+static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd)
 {
-    if (dense) return adam ? cudaErrorInvalidValue : launch_bwd_t<VPT, true, false>(a, want_delta, grid, wpb, st);
-    return adam ? launch_bwd_t<VPT, false, true>(a, want_delta, grid, wpb, st)
-                : launch_bwd_t<VPT, false, false>(a, want_delta, grid, wpb, st);
+    switch (vpt) {
+    case 1: return backward_fn<1>(dense, adam, wd);
+    case 2: return backward_fn<2>(dense, adam, wd);
+    case 4: return backward_fn<4>(dense, adam, wd);
+    case 8: return backward_fn<8>(dense, adam, wd);
+    }
+    return nullptr;
 }
 
 cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a, int grid,
                             int wpb, cudaStream_t st)
 {
-    switch (vpt) {
-    case 1: return launch_bwd_v<1>(dense_seed, adam, want_delta, a, grid, wpb, st);
-    case 2: return launch_bwd_v<2>(dense_seed, adam, want_delta, a, grid, wpb, st);
-    case 4: return launch_bwd_v<4>(dense_seed, adam, want_delta, a, grid, wpb, st);
-    case 8: return launch_bwd_v<8>(dense_seed, adam, want_delta, a, grid, wpb, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename F>
-static int occ(F fn, int wpb, size_t smem)
-{
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * wpb, smem) != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
+    if (dense_seed && adam) return cudaErrorInvalidValue;
+    void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam);
+    if (!fn) return cudaErrorInvalidValue;
+    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, wpb);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    SimArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
 int occupancy_blocks(int vpt, bool backward, bool dense, bool adam, bool want_delta, int wpb, size_t smem)
 {
-    (void)want_delta;
+    void *fn = nullptr;
     if (!backward) {
         switch (vpt) {
-        case 1: return occ(forward_kernel<1>, wpb, 0);
-        case 2: return occ(forward_kernel<2>, wpb, 0);
-        case 4: return occ(forward_kernel<4>, wpb, 0);
-        case 8: return occ(forward_kernel<8>, wpb, 0);
+        case 1: fn = (void *)forward_kernel<1>; break;
+        case 2: fn = (void *)forward_kernel<2>; break;
+        case 4: fn = (void *)forward_kernel<4>; break;
+        case 8: fn = (void *)forward_kernel<8>; break;
         }
-        return 1;
+    } else {
+        fn = backward_fn_v(vpt, dense, adam, want_delta && !adam);
+        if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-#define OCC_B(V)                                                                  \
-    if (vpt == V) {                                                               \
-        if (dense) return occ(backward_kernel<V, true, false>, wpb, smem);        \
-        if (adam) {                                                               \
-            cudaFuncSetAttribute(backward_kernel<V, false, true>,                 \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-            return occ(backward_kernel<V, false, true>, wpb, smem);               \
-        }                                                                         \
-        cudaFuncSetAttribute(backward_kernel<V, false, false>,                    \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        return occ(backward_kernel<V, false, false>, wpb, smem);                  \
-    }
-    OCC_B(1) OCC_B(2) OCC_B(4) OCC_B(8)
-#undef OCC_B
-    return 1;
+    if (!fn) return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * wpb, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
 }
 
 }  // namespace idm
