@@ -140,9 +140,16 @@ int idm_layout(idm_ctx_t *ctx, int32_t N, int32_t n_lanes, const int32_t *lane_i
                void *stream);
 
 /* dst[j] = src[perm[j]] for j < N, for `count` float32 arrays given as
- * arrays of device pointers in HOST memory (srcs[count], dsts[count]). */
+ * arrays of device pointers in HOST memory (srcs[count], dsts[count]).
+ * Every perm[j] must lie in [0, N) (idm_layout's output does). */
 int idm_gather(idm_ctx_t *ctx, int32_t N, const int32_t *perm, int count,
                const float *const *srcs, float *const *dsts, void *stream);
+
+/* Column gather of a row-major [n_rows][N] float32 matrix whose columns are
+ * vehicles (e.g. observed targets): dst[r*N + j] = src[r*N + perm[j]].
+ * Every perm[j] must lie in [0, N).  src and dst must not overlap. */
+int idm_gather_rows(idm_ctx_t *ctx, int32_t N, int32_t n_rows, const int32_t *perm,
+                    const float *src, float *dst, void *stream);
 
 /* ---- forward (Eq. 1-3 with the Sec. III-C bounds) -------------------- */
 
@@ -190,7 +197,9 @@ int idm_loss_grad(idm_ctx_t *ctx, const idm_scene_t *scene, const idm_params_t *
  * a_max, b), projection onto [box_lo[q], box_hi[q]]}; delta is not changed.
  * The learning rate of iteration t (0-based) is lr0 + (lr1 - lr0) t /
  * (n_iter - 1); Adam uses beta1 0.9, beta2 0.999, eps 1e-8, zero initial
- * moments.  One iteration is captured in a CUDA graph and replayed.
+ * moments.  The n_iter iterations (1 <= n_iter <= 100000) are captured once
+ * into a CUDA graph, cached on the context for calls with identical
+ * arguments, and launched on `stream` as one graph.
  *   params (device, in/out): initial guess in, fitted values out.
  *   box_lo, box_hi (HOST, [5], order v0, T, s0, a_max, b).
  *   loss_hist (device out, double [n_iter], may be NULL): loss at the
@@ -199,6 +208,17 @@ int idm_fit(idm_ctx_t *ctx, const idm_scene_t *scene, idm_params_t *params,
             const float *p_init, const float *v_init, const idm_sim_t *sim,
             const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
             const float *box_lo, const float *box_hi, double *loss_hist, void *stream);
+
+/* ---- measurement ------------------------------------------------------ */
+
+/* When on, idm_fit records CUDA events around every forward and adjoint
+ * launch of its graph (on the launching stream). */
+int idm_set_profiling(idm_ctx_t *ctx, int on);
+
+/* Synchronise `stream`, then report the summed device time (ms) of the
+ * forward and adjoint launches of the last profiled idm_fit and the number
+ * of iterations recorded (*n_launches).  Any output pointer may be NULL. */
+int idm_phase_times(idm_ctx_t *ctx, void *stream, double *fwd_ms, double *bwd_ms, int32_t *n_launches);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include <new>
 
@@ -40,6 +41,11 @@ struct idm_ctx {
     Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t fit_exec = nullptr;
+    unsigned char fit_key[512] = {0};  // arguments the cached fit graph was captured with
+    size_t fit_key_len = 0;
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;       // per fit iteration: fwd begin/end, adjoint begin/end
+    int ev_used = 0;                   // iterations recorded by the cached graph
 };
 
 namespace {
@@ -242,6 +248,7 @@ int idm_ctx_destroy(idm_ctx_t *c)
     if (!c) return IDM_OK;
     cudaDeviceSynchronize();
     if (c->fit_exec) cudaGraphExecDestroy(c->fit_exec);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     Buf *bufs[] = {&c->seg, &c->ctl, &c->status, &c->g0, &c->ckpt, &c->loss_part, &c->loss_tmp,
                    &c->adam_m, &c->adam_v, &c->lay_counts, &c->lay_cursor};
     for (Buf *b : bufs)
@@ -384,8 +391,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     P.a.targets = targets;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     CK(idm::launch_forward(P.vpt, false, false, true, true, P.a, P.grid_f, c->wpb, st));
-    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, loss_out ? loss_out : (double *)c->loss_tmp.p, nullptr,
-                                 nullptr, st));
+    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     if (grad) {
         P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
@@ -405,7 +411,7 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
     int rc;
     if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
     if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
-    if (n_iter < 0) return fail(c, IDM_ERR_ARG, "n_iter must be >= 0");
+    if (n_iter < 0 || n_iter > 100000) return fail(c, IDM_ERR_ARG, "n_iter must be in [0, 100000]");
     if (!box_lo || !box_hi) return fail(c, IDM_ERR_ARG, "box_lo and box_hi (host) are required");
     for (int q = 0; q < 5; ++q)
         if (!(box_lo[q] <= box_hi[q])) return fail(c, IDM_ERR_ARG, "box_lo[%d] > box_hi[%d]", q, q);
@@ -421,52 +427,113 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
     const size_t N = (size_t)scene->n_vehicles;
     if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
     if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
-    CK(cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, st));
-    CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
-    CK(cudaMemsetAsync((int *)c->ctl.p + CTL_ITER, 0, sizeof(int), st));
 
     SimArgs a = P.a;
     a.targets = targets;
     a.adam_m = (float *)c->adam_m.p;
     a.adam_v = (float *)c->adam_v.p;
-    a.iter = (const int *)c->ctl.p + CTL_ITER;
     a.n_iter = n_iter;
     a.lr0 = lr0;
     a.lr1 = lr1;
     for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
 
-    // capture one iteration on the context's stream
-    cudaStream_t cs = c->cap_stream;
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CK(cudaEventRecord(ev, st));
-    CK(cudaStreamWaitEvent(cs, ev, 0));
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
-    if (e == cudaSuccess) {
-        a.work = (int *)c->ctl.p + CTL_WORK_F;
-        e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, c->wpb, cs);
+    // The graph depends on every launch argument; reuse it when they repeat.
+    struct Key {
+        SimArgs a;
+        int vpt, grid_f, grid_b, wpb, wpb_b, n_iter, profiling;
+        const double *hist;
+    } key;
+    memset(&key, 0, sizeof key);
+    key.a = a;
+    key.vpt = P.vpt; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = c->wpb; key.wpb_b = P.wpb_b;
+    key.n_iter = n_iter; key.profiling = c->profiling; key.hist = loss_hist;
+    static_assert(sizeof(Key) <= sizeof(((idm_ctx *)0)->fit_key), "fit key too large");
+    const bool cached = c->fit_exec && c->fit_key_len == sizeof key && memcmp(c->fit_key, &key, sizeof key) == 0;
+
+    if (!cached) {
+        if (c->profiling && (int)c->ev.size() < 4 * n_iter) {
+            while ((int)c->ev.size() < 4 * n_iter) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                c->ev.push_back(e);
+            }
+        }
+        // capture the whole fit (n_iter unrolled iterations) on the context's stream
+        cudaStream_t cs = c->cap_stream;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, cs);
+        for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+            a.iter = it;
+            e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) {
+                a.work = (int *)c->ctl.p + CTL_WORK_F;
+                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, c->wpb, cs);
+            }
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess)
+                e = idm::launch_loss_finalize(a.loss_part, a.n_seg, loss_hist ? loss_hist + it : nullptr, cs);
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) {
+                a.work = (int *)c->ctl.p + CTL_WORK_B;
+                e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
+            }
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit"); }
+        if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+        if (c->fit_exec) {
+            CK(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(c->fit_exec);
+            c->fit_exec = nullptr;
+            c->fit_key_len = 0;
+        }
+        e = cudaGraphInstantiate(&c->fit_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        memcpy(c->fit_key, &key, sizeof key);
+        c->fit_key_len = sizeof key;
+        c->ev_used = c->profiling ? n_iter : 0;
     }
-    if (e == cudaSuccess) {
-        a.work = (int *)c->ctl.p + CTL_WORK_B;
-        e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
+    CK(cudaGraphLaunch(c->fit_exec, st));
+    return IDM_OK;
+}
+
+int idm_set_profiling(idm_ctx_t *c, int on)
+{
+    if (!c) return IDM_ERR_ARG;
+    c->profiling = on ? 1 : 0;
+    return IDM_OK;
+}
+
+int idm_phase_times(idm_ctx_t *c, void *stream, double *fwd_ms, double *bwd_ms, int32_t *n_launches)
+{
+    if (!c) return IDM_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    double f = 0.0, b = 0.0;
+    for (int it = 0; it < c->ev_used; ++it) {
+        float x = 0.0f, y = 0.0f;
+        CK(cudaEventElapsedTime(&x, c->ev[4 * it], c->ev[4 * it + 1]));
+        CK(cudaEventElapsedTime(&y, c->ev[4 * it + 2], c->ev[4 * it + 3]));
+        f += x;
+        b += y;
     }
-    if (e == cudaSuccess)
-        e = idm::launch_loss_finalize(a.loss_part, a.n_seg, nullptr, (int *)c->ctl.p + CTL_ITER, loss_hist, cs);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    cudaEventDestroy(ev);
-    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit iteration"); }
-    if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-    if (c->fit_exec) {
-        CK(cudaDeviceSynchronize());
-        cudaGraphExecDestroy(c->fit_exec);
-        c->fit_exec = nullptr;
-    }
-    e = cudaGraphInstantiate(&c->fit_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-    for (int it = 0; it < n_iter; ++it) CK(cudaGraphLaunch(c->fit_exec, st));
+    if (fwd_ms) *fwd_ms = f;
+    if (bwd_ms) *bwd_ms = b;
+    if (n_launches) *n_launches = c->ev_used;
+    return IDM_OK;
+}
+
+int idm_gather_rows(idm_ctx_t *c, int32_t N, int32_t n_rows, const int32_t *perm, const float *src, float *dst,
+                    void *stream)
+{
+    if (!c) return IDM_ERR_ARG;
+    if (N < 0 || n_rows < 0) return fail(c, IDM_ERR_ARG, "N and n_rows must be >= 0");
+    if (N > 0 && n_rows > 0 && (!perm || !src || !dst)) return fail(c, IDM_ERR_ARG, "perm, src and dst are required");
+    CK(idm::launch_gather_rows(N, n_rows, perm, src, dst, (cudaStream_t)stream));
     return IDM_OK;
 }
 

@@ -52,7 +52,7 @@ struct SimArgs {
     float *g_v0, *g_T, *g_s0, *g_am, *g_b, *g_delta, *g_p_init, *g_v_init;
     // Adam (fit)
     float *adam_m, *adam_v;     // [5][N_total]
-    const int *iter;            // 0-based iteration counter (device)
+    int iter;                   // 0-based iteration of the fit
     int n_iter;
     int N_total;
     float lr0, lr1;
@@ -69,8 +69,8 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt,
 cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
 size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb);
-cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, int *iter,
-                                 double *hist, cudaStream_t st);
+size_t forward_smem_bytes(int vpt, int wpb);
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, cudaStream_t st);
 int occupancy_blocks(int vpt, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
 
 // Layout (idm_layout.cu).
@@ -79,5 +79,6 @@ cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const floa
                           cudaStream_t st);
 cudaError_t launch_gather(int N, const int32_t *perm, int count, const float *const *srcs, float *const *dsts,
                           cudaStream_t st);
+cudaError_t launch_gather_rows(int N, int n_rows, const int32_t *perm, const float *src, float *dst, cudaStream_t st);
 
 }  // namespace idm

@@ -156,4 +156,23 @@ cudaError_t launch_gather(int N, const int32_t *perm, int count, const float *co
     return cudaGetLastError();
 }
 
+// dst[r][j] = src[r][perm[j]] for a row-major [n_rows][N] matrix (columns
+// are vehicles): coalesced writes, gathered reads.
+__global__ void gather_rows_kernel(int N, int n_rows, const int32_t *perm, const float *src, float *dst)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int s = perm[j];
+    for (int r = blockIdx.y; r < n_rows; r += gridDim.y) dst[(size_t)r * N + j] = src[(size_t)r * N + s];
+}
+
+cudaError_t launch_gather_rows(int N, int n_rows, const int32_t *perm, const float *src, float *dst, cudaStream_t st)
+{
+    if (N > 0 && n_rows > 0) {
+        dim3 grid((N + 255) / 256, n_rows < 64 ? n_rows : 64);
+        gather_rows_kernel<<<grid, 256, 0, st>>>(N, n_rows, perm, src, dst);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace idm

@@ -164,6 +164,30 @@ __device__ __forceinline__ double warp_sum_double(double x)
     return x;
 }
 
+// Asynchronous 4-byte global->shared copies (cp.async, completion tracked
+// per thread in commit groups).
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Observed-target rows are prefetched FWD_PD rows ahead into a ring of
+// FWD_RING rows per warp; the slot written is never the one just read.
+constexpr int FWD_RING = 4;
+constexpr int FWD_PD = 3;
+
+template <int VPT>
+__device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, int lane, const bool (&valid)[VPT])
+{
+#pragma unroll
+    for (int j = 0; j < VPT; ++j)
+        if (valid[j]) cp_async4(dst + lane + 32 * j, src_row + lane + 32 * j);
+}
+
 template <int VPT>
 __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, VehConst (&kc)[VPT],
                                               State (&st)[VPT], float (&pin)[VPT], bool (&valid)[VPT])
@@ -209,12 +233,21 @@ struct FwdFlags {
 template <int VPT, bool D4>
 __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, int lane,
                                                 const VehConst (&kc)[VPT], State (&st)[VPT], const float (&pin)[VPT],
-                                                const bool (&valid)[VPT], FwdFlags f)
+                                                const bool (&valid)[VPT], FwdFlags f, float *ring)
 {
+    constexpr int SL = 32 * VPT;
     const int Ns = sc.n_veh;
     float lsum = 0.0f, lcomp = 0.0f;
     int next_obs = sc.obs_stride, obs_row = 0;
     int next_ck = 0, ck_idx = 0;
+    const float *ybase = a.targets + sc.tgt_off + lb;
+    if (f.loss) {
+#pragma unroll
+        for (int r = 0; r < FWD_PD; ++r) {
+            if (r < sc.n_obs) prefetch_row<VPT>(ring + r * SL, ybase + (size_t)r * Ns, lane, valid);
+            cp_async_commit();
+        }
+    }
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
             float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + lb;
@@ -241,13 +274,17 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             }
         }
         if (f.loss && k == next_obs && obs_row < sc.n_obs) {
-            const float *y = a.targets + sc.tgt_off + (size_t)obs_row * Ns + lb;
+            cp_async_wait<FWD_PD - 1>();
+            const float *y = ring + (obs_row % FWD_RING) * SL;
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
-                float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
+                float r = residual(pin[j], st[j], y[lane + 32 * j]);
                 kahan_add(lsum, lcomp, __fmul_rn(r, r));
             }
+            const int nr = obs_row + FWD_PD;
+            if (nr < sc.n_obs) prefetch_row<VPT>(ring + (nr % FWD_RING) * SL, ybase + (size_t)nr * Ns, lane, valid);
+            cp_async_commit();
             next_obs += sc.obs_stride;
             ++obs_row;
         }
@@ -263,6 +300,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             euler(st[j], as, vh[j], sc.dt);
         }
     }
+    if (f.loss) cp_async_wait<0>();
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < VPT; ++j)
@@ -278,7 +316,9 @@ template <int VPT>
 __global__ void __launch_bounds__(512)
 forward_kernel(SimArgs a, FwdFlags f)
 {
+    extern __shared__ float fsmem[];
     const int lane = threadIdx.x & 31;
+    float *ring = fsmem + (threadIdx.x >> 5) * FWD_RING * 32 * VPT;
     for (;;) {
         const int s_idx = next_segment(a.work, lane);
         if (s_idx >= *a.n_seg) break;
@@ -291,9 +331,9 @@ forward_kernel(SimArgs a, FwdFlags f)
         bool valid[VPT];
         load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            forward_segment<VPT, true>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f);
+            forward_segment<VPT, true>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f, ring);
         else
-            forward_segment<VPT, false>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f);
+            forward_segment<VPT, false>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f, ring);
     }
 }
 
@@ -307,10 +347,12 @@ forward_kernel(SimArgs a, FwdFlags f)
 // Parameter gradients accumulate in float per checkpoint segment and the
 // segment sums are added into the totals (pairwise-style summation).
 // ---------------------------------------------------------------------------
+// Per-warp shared memory of the adjoint: tape v[C][SL], gap[C][SL],
+// (MSE) targets-then-seeds[C][SL], and the six gradient totals [6][SL].
 template <int VPT, bool DENSE>
 __device__ __forceinline__ float *tape_base(float *smem, int C)
 {
-    const int per_warp = (DENSE ? 2 : 3) * C * 32 * VPT;
+    const int per_warp = ((DENSE ? 2 : 3) * C + 6) * 32 * VPT;
     return smem + (threadIdx.x >> 5) * per_warp;
 }
 
@@ -321,25 +363,34 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 {
     constexpr int SL = 32 * VPT;
     float *tg = tv + a.C * SL;
-    float *tr = tg + a.C * SL;  // seeds (MSE only)
+    float *tr = tg + a.C * SL;                         // targets, then seeds (MSE only)
+    float *acc = tv + (DENSE ? 2 : 3) * a.C * SL;      // gradient totals [6][SL]
     const int Ns = sc.n_veh;
     const float dt = sc.dt;
     const float seed_scale = 2.0f * sc.inv_nobs;
 
     float lp[VPT], lv[VPT];
-    float acc[6][VPT];
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
         lp[j] = 0.0f;
         lv[j] = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q][j] = 0.0f;
+        for (int q = 0; q < 6; ++q) acc[q * SL + lane + 32 * j] = 0.0f;
     }
 
     const int n_ck = (sc.K + a.C - 1) / a.C;
     for (int cs = n_ck - 1; cs >= 0; --cs) {
         const int c0 = cs * a.C;
         const int n = min(a.C, sc.K - c0);
+        // first observed step >= max(c0, 1)
+        int obs_k = ((c0 + sc.obs_stride - 1) / sc.obs_stride) * sc.obs_stride;
+        if (obs_k == 0) obs_k = sc.obs_stride;
+        if (!DENSE) {  // fetch the segment's observed targets into the seed tape
+            for (int k = obs_k; k < c0 + n && k / sc.obs_stride <= sc.n_obs; k += sc.obs_stride)
+                prefetch_row<VPT>(tr + (k - c0) * SL, a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb,
+                                  lane, valid);
+            cp_async_commit();
+        }
         {
             const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + lb;
 #pragma unroll
@@ -349,9 +400,8 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 st[j] = State{base[q], base[(size_t)Ns + q], base[2 * (size_t)Ns + q], base[3 * (size_t)Ns + q]};
             }
         }
+        if (!DENSE) cp_async_wait<0>();
         // recompute the segment into the tape
-        int obs_k = ((c0 + sc.obs_stride - 1) / sc.obs_stride) * sc.obs_stride;  // first observed step >= c0
-        if (obs_k == 0) obs_k = sc.obs_stride;
         for (int s = 0; s < n; ++s) {
             const int k = c0 + s;
             float *rv = tv + s * SL, *rg = tg + s * SL;
@@ -362,11 +412,10 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             }
             if (!DENSE && k == obs_k) {
                 if (k / sc.obs_stride <= sc.n_obs) {
-                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
                     float *rr = tr + s * SL;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) {
-                        float r = valid[j] ? residual(pin[j], st[j], __ldg(y + lane + 32 * j)) : 0.0f;
+                        float r = valid[j] ? residual(pin[j], st[j], rr[lane + 32 * j]) : 0.0f;
                         rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
                     }
                 }
@@ -468,7 +517,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) acc[q][j] += sacc[q][j];
+            for (int j = 0; j < VPT; ++j) acc[q * SL + lane + 32 * j] += sacc[q][j];
         __syncwarp();
     }
 
@@ -481,16 +530,18 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         const int gi = sg.veh_begin + q;
         const float v0 = a.v0[gi], b = a.b[gi];
         const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
+        const float A0 = acc[0 * SL + q], A1 = acc[1 * SL + q], A2 = acc[2 * SL + q];
+        const float A3 = acc[3 * SL + q], A4 = acc[4 * SL + q], A5 = acc[5 * SL + q];
         float g[6];
-        g[0] = am * dl * acc[4][j] / v0;                 // v0
-        g[1] = acc[1][j];                                // T
-        g[2] = acc[0][j];                                // s0
-        g[3] = acc[3][j] - acc[2][j] * c / (2.0f * am);  // a_max
-        g[4] = -acc[2][j] * c / (2.0f * b);              // b
-        g[5] = -am * acc[5][j];                          // delta
+        g[0] = am * dl * A4 / v0;                 // v0
+        g[1] = A1;                                // T
+        g[2] = A0;                                // s0
+        g[3] = A3 - A2 * c / (2.0f * am);         // a_max
+        g[4] = -A2 * c / (2.0f * b);              // b
+        g[5] = -am * A5;                          // delta
         for (int p = 0; p < 6; ++p) bad |= !isfinite(g[p]);
         if (ADAM) {
-            const int it = *a.iter;
+            const int it = a.iter;
             const int t = it + 1;
             const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
             const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
@@ -522,7 +573,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 }
 
 template <int VPT, bool DENSE, bool ADAM, bool WD>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (VPT <= 4 ? 2 : 1))
 backward_kernel(SimArgs a)
 {
     extern __shared__ float smem[];
@@ -550,7 +601,7 @@ backward_kernel(SimArgs a)
 // Deterministic loss reduction over segments (fixed order).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-loss_finalize_kernel(const double *part, const int *n_seg, double *out, int *iter, double *hist)
+loss_finalize_kernel(const double *part, const int *n_seg, double *out)
 {
     __shared__ double sh[1024];
     const int n = *n_seg;
@@ -562,19 +613,12 @@ loss_finalize_kernel(const double *part, const int *n_seg, double *out, int *ite
         if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (out) *out = sh[0];
-        if (iter) {
-            if (hist) hist[*iter] = sh[0];
-            *iter += 1;
-        }
-    }
+    if (threadIdx.x == 0 && out) *out = sh[0];
 }
 
-cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, int *iter,
-                                 double *hist, cudaStream_t st)
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, cudaStream_t st)
 {
-    loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, out, iter, hist);
+    loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, out);
     return cudaGetLastError();
 }
 
@@ -584,22 +628,29 @@ cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, doub
 cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt, const SimArgs &a, int grid,
                            int wpb, cudaStream_t st)
 {
-    dim3 blk(32 * wpb);
     FwdFlags f{traj, vtraj, loss, ckpt};
+    void *fn = nullptr;
     switch (vpt) {
-    case 1: forward_kernel<1><<<grid, blk, 0, st>>>(a, f); break;
-    case 2: forward_kernel<2><<<grid, blk, 0, st>>>(a, f); break;
-    case 4: forward_kernel<4><<<grid, blk, 0, st>>>(a, f); break;
-    case 8: forward_kernel<8><<<grid, blk, 0, st>>>(a, f); break;
+    case 1: fn = (void *)forward_kernel<1>; break;
+    case 2: fn = (void *)forward_kernel<2>; break;
+    case 4: fn = (void *)forward_kernel<4>; break;
+    case 8: fn = (void *)forward_kernel<8>; break;
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    const size_t smem = forward_smem_bytes(vpt, wpb);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    SimArgs args = a;
+    void *params[] = {&args, &f};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
 size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb)
 {
-    return (size_t)(dense_seed ? 2 : 3) * C * 32 * vpt * sizeof(float) * wpb;
+    return (size_t)((dense_seed ? 2 : 3) * C + 6) * 32 * vpt * sizeof(float) * wpb;
 }
+
+size_t forward_smem_bytes(int vpt, int wpb) { return (size_t)FWD_RING * 32 * vpt * sizeof(float) * wpb; }
 
 // Kernel variants of the adjoint: seeds from dense gradients or from targets,
 // fused Adam or gradient output, with or without the delta gradient.
@@ -646,6 +697,8 @@ int occupancy_blocks(int vpt, bool backward, bool dense, bool adam, bool want_de
         case 4: fn = (void *)forward_kernel<4>; break;
         case 8: fn = (void *)forward_kernel<8>; break;
         }
+        smem = forward_smem_bytes(vpt, wpb);
+        if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
         fn = backward_fn_v(vpt, dense, adam, want_delta && !adam);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

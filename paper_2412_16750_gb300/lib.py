@@ -60,6 +60,10 @@ _SIGS = {
     "idm_loss_grad": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
                                      ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, _vp,
                                      ctypes.POINTER(idm_params_t), _vp, _vp, _vp]),
+    "idm_gather_rows": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    "idm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "idm_phase_times": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int32)]),
     "idm_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
                                ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -165,6 +169,20 @@ def idm_gather(ctx, N, perm, srcs, dsts, stream=None):
     s = (_vp * max(n, 1))(*[t.data_ptr() for t in srcs])
     d = (_vp * max(n, 1))(*[t.data_ptr() for t in dsts])
     return check(ctx, load().idm_gather(ctx, N, ptr(perm), n, s, d, stream_ptr(stream)))
+
+
+def idm_gather_rows(ctx, N, n_rows, perm, src, dst, stream=None):
+    return check(ctx, load().idm_gather_rows(ctx, N, n_rows, ptr(perm), ptr(src), ptr(dst), stream_ptr(stream)))
+
+
+def idm_set_profiling(ctx, on):
+    return check(ctx, load().idm_set_profiling(ctx, 1 if on else 0))
+
+
+def idm_phase_times(ctx, stream=None):
+    f, b, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int32(0)
+    check(ctx, load().idm_phase_times(ctx, stream_ptr(stream), ctypes.byref(f), ctypes.byref(b), ctypes.byref(n)))
+    return f.value, b.value, n.value
 
 
 def idm_forward(ctx, scene, params, p_init, v_init, sim, traj=None, vtraj=None, stream=None):
