@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable IDM fit at paper scale on GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch):
+  20,000 lanes x 100 vehicles (2,000,000 vehicles), 1,000 Euler steps of
+  dt = 0.1 s, targets = the true trajectory + N(0, 0.5^2) m noise at every
+  step.  The batch arrives unsorted; a step runs
+    layout   idm_layout (sort by lane / position) + idm_gather of the
+             per-vehicle arrays + idm_gather_rows of the targets,
+    fit      idm_fit: --iters iterations of {fused forward + squared-error
+             loss + checkpoints, adjoint with checkpoint recompute + fused
+             Adam/projection}, from the paper's zero-knowledge initial guess.
+  The metric counts forward+backward vehicle-steps: iters x N x K per step.
+
+Lines printed (rank 0, one JSON line):
+  value     device throughput, inputs resident in HBM before the timed region;
+  e2e       the same steps with every input copied host->device (pinned) and
+            the fitted parameters + loss history copied back, inside the timer;
+  roofline  the adjoint kernel (the dominant one), timed with CUDA events
+            recorded inside the fit graph on its stream;
+  cpu_baseline  the FP64 oracle on a bounded sample, single-threaded.
+
+--impl reference times the FP64 CPU oracle (the only reference available:
+the paper ships no code) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank fits its own 2M-vehicle batch (lanes are
+independent, no data-path collective): weak scaling.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd vehicle-steps/s at 2M vehicles; time-to-fit 0.5 m RMSE, learned vs plain"
+UNIT = "vehicle-steps/s"
+DT = float(np.float32(0.1))
+A_MIN = -10.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--lanes", type=int, default=20000)
+    p.add_argument("--per-lane", type=int, default=100)
+    p.add_argument("--K", type=int, default=1000)
+    p.add_argument("--iters", type=int, default=100, help="Adam iterations per step")
+    p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--vpt", type=int, default=4)
+    p.add_argument("--G", type=int, default=4, help="warps per segment")
+    p.add_argument("--ckpt", type=int, default=8)
+    p.add_argument("--wpb", type=int, default=8)
+    return p.parse_args()
+
+
+def workload_name(a):
+    return ("%d lanes x %d vehicles (%.1fM), %d steps, dt 0.1 s; per step: layout + %d-iteration Adam fit"
+            % (a.lanes, a.per_lane, a.lanes * a.per_lane / 1e6, a.K, a.iters))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(n_lanes=10, per_lane=100, K=1000, iters=3, seed=0):
+    """Time the FP64 oracle fit (forward + loss + adjoint + Adam) on a bounded
+    sample of the workload.  Returns (vehicle-steps/s, seconds, description)."""
+    import oracle
+    from paper_2412_16750_gb300 import synth
+    sc = synth.make_scene([per_lane] * n_lanes, synth.rng_for(1, seed))
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    Y = synth.f32(P[1:] + synth.rng_for(1, seed + 1).normal(0, 0.5, size=P[1:].shape))
+    th = synth.plain_init(n_lanes * per_lane)
+    t0 = time.perf_counter()
+    oracle.fit(sc["lane_off"], sc["length"], th, sc["p_init"], sc["v_init"], K, DT, Y, 1, iters, 0.1, 0.01,
+               synth.BOX_LO, synth.BOX_HI, A_MIN)
+    dt = time.perf_counter() - t0
+    units = iters * n_lanes * per_lane * K
+    desc = "%d lanes x %d vehicles x %d steps, %d fit iterations, FP64 single thread" % (n_lanes, per_lane, K, iters)
+    return units / dt, dt, desc
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return 0
+    for _ in range(max(1, min(a.warmup, 1))):
+        oracle_sample(iters=1)
+    times, vals = [], []
+    desc = ""
+    for _ in range(a.steps):
+        v, dt, desc = oracle_sample(iters=1)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_ginst(sm_mhz, n_sm):
+    """FP32-pipe instruction issue peak: n_SM x 128 lanes x clock (Ginstr/s)."""
+    return n_sm * 128 * sm_mhz * 1e6 / 1e9
+
+
+# Algorithmic FP32 operations per vehicle-step of the adjoint launch
+# (recompute of the forward step + reverse step + gradient accumulation),
+# counted from the method's formulas; see the design notes.
+ADJ_OPS_PER_VS = 130.0
+FWD_OPS_PER_VS = 45.0
+
+
+def adjoint_traffic_per_vs():
+    """DRAM bytes per vehicle-step of the adjoint from the committed ncu
+    summary, or None if absent / taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "adjoint_kernel_2M.md")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_sim.cu"), "rb").read()
+    src += open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_device.cuh"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    got_sha, bytes_vs = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_sha256_16:"):
+            got_sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_vehicle_step:"):
+            bytes_vs = float(line.split(":", 1)[1].strip())
+    return bytes_vs if (got_sha == sha and bytes_vs) else None
+
+
+def run_gpu(a, rank, world, local_rank):
+    import torch
+    from paper_2412_16750_gb300 import api, lib, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # ---- synthetic batch (seeded per rank), unsorted arrival order -------
+    rng = synth.rng_for(1, rank)
+    counts = [a.per_lane] * a.lanes
+    sc = synth.make_scene(counts, rng)
+    N = int(sc["lane_off"][-1])
+    L = a.lanes
+    K = a.K
+    ctx = api.Context(vpt=a.vpt, warps_per_segment=a.G, ckpt_interval=a.ckpt, warps_per_block=a.wpb)
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    scene_sorted = api.Scene.from_lane_off(cu(sc["lane_off"], torch.int32), cu(sc["length"]), a.per_lane)
+    th_true = cu(sc["theta_true"])
+    p_sorted, v_sorted = cu(sc["p_init"]), cu(sc["v_init"])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20241216 + 1000 * rank)
+    traj = api.simulate(th_true, p_sorted, v_sorted, scene_sorted, K, DT, A_MIN, ctx=ctx)
+    Y_sorted = traj[1:]
+    Y_sorted.add_(0.5 * torch.randn(Y_sorted.shape, device=dev, generator=gen))
+    order = torch.as_tensor(rng.permutation(N), device=dev)
+    lane_id = torch.repeat_interleave(torch.arange(L, device=dev, dtype=torch.int32),
+                                      torch.as_tensor(np.diff(sc["lane_off"]), device=dev))
+    # arrival-order inputs (device resident)
+    u_lane = lane_id[order].contiguous()
+    u_p = p_sorted[order].contiguous()
+    u_v = v_sorted[order].contiguous()
+    u_len = scene_sorted.length[order].contiguous()
+    u_th = cu(synth.plain_init(N))[:, order].contiguous()
+    u_Y = Y_sorted[:, order].contiguous()
+    del traj, Y_sorted
+    torch.cuda.empty_cache()
+
+    # ---- preallocated step buffers ---------------------------------------
+    perm = torch.empty(N, dtype=torch.int32, device=dev)
+    lane_off = torch.empty(L + 1, dtype=torch.int32, device=dev)
+    mx = torch.zeros(1, dtype=torch.int32, device=dev)
+    s_p = torch.empty(N, device=dev)
+    s_v = torch.empty(N, device=dev)
+    s_len = torch.empty(N, device=dev)
+    s_th = torch.empty((6, N), device=dev)
+    s_Y = torch.empty((K, N), device=dev)
+    hist = torch.zeros(a.iters, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = ctx.handle
+    lib.idm_set_profiling(h, 1)
+    scene_c = lib.idm_scene_t(L, N, a.per_lane, lane_off.data_ptr(), s_len.data_ptr())
+    params_c = lib.make_params(s_th)
+    sim_c = lib.make_sim(K, DT, A_MIN)
+
+    def step(in_lane, in_p, in_v, in_len, in_th, in_Y):
+        lib.idm_layout(h, N, L, in_lane, in_p, perm, lane_off, mx, stream)
+        lib.idm_gather(h, N, perm, [in_p, in_v, in_len] + [in_th[q] for q in range(6)],
+                       [s_p, s_v, s_len] + [s_th[q] for q in range(6)], stream)
+        lib.idm_gather_rows(h, N, K, perm, in_Y, s_Y, stream)
+        lib.idm_fit(h, scene_c, params_c, s_p, s_v, sim_c, s_Y, 1, a.iters, 0.1, 0.01, synth.BOX_LO, synth.BOX_HI,
+                    hist, stream)
+
+    launches_per_step = 4 + 1 + 1 + 3 + 3 * a.iters  # layout 4, gather 1, rows 1, prep 3, 3 per iteration
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up -----------------------------------------------------------
+    for _ in range(a.warmup):
+        step(u_lane, u_p, u_v, u_len, u_th, u_Y)
+    torch.cuda.synchronize()
+    rc, flags = ctx.status()
+    if rc != 0:
+        raise RuntimeError("device status %d flags %d: %s" % (rc, flags, lib.idm_last_error(h)))
+
+    # ---- timed: device-resident inputs --------------------------------------
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fwd_ms = bwd_ms = 0.0
+    n_fit_iters = 0
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(u_lane, u_p, u_v, u_len, u_th, u_Y)
+        f, b, n = lib.idm_phase_times(h, stream)  # syncs the stream: per-launch event times of this step
+        fwd_ms += f
+        bwd_ms += b
+        n_fit_iters += n
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms)
+    final_loss = float(hist[-1].item()) / N
+    first_loss = None
+
+    # ---- timed: end to end from pinned host memory --------------------------
+    e2e_steps = a.e2e_steps if a.e2e_steps is not None else a.steps
+    h_lane = u_lane.cpu().pin_memory()
+    h_p, h_v, h_len = u_p.cpu().pin_memory(), u_v.cpu().pin_memory(), u_len.cpu().pin_memory()
+    h_th = u_th.cpu().pin_memory()
+    h_Y = u_Y.cpu().pin_memory()
+    d_lane, d_p, d_v, d_len = torch.empty_like(u_lane), torch.empty_like(u_p), torch.empty_like(u_v), \
+        torch.empty_like(u_len)
+    d_th, d_Y = torch.empty_like(u_th), torch.empty_like(u_Y)
+    out_th = torch.empty((6, N)).pin_memory()
+    out_hist = torch.empty(a.iters, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_lane, h_p, h_v, h_len, h_th, h_Y))
+    d2h = out_th.numel() * 4 + out_hist.numel() * 8
+    lib.idm_set_profiling(h, 0)
+    barrier()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(e2e_steps):
+        for dst, src in ((d_lane, h_lane), (d_p, h_p), (d_v, h_v), (d_len, h_len), (d_th, h_th), (d_Y, h_Y)):
+            dst.copy_(src, non_blocking=True)
+        step(d_lane, d_p, d_v, d_len, d_th, d_Y)
+        out_th.copy_(s_th, non_blocking=True)
+        out_hist.copy_(hist, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3))
+    rc, flags = ctx.status()
+    if rc != 0:
+        raise RuntimeError("device status %d flags %d after e2e" % (rc, flags))
+    del h_Y, d_Y
+
+    units_per_step = a.iters * N * K
+    value = world * units_per_step * a.steps / (ms * 1e-3)
+    e2e_value = world * units_per_step * e2e_steps / (ms_e2e * 1e-3)
+
+    # ---- roofline of the adjoint launch ----------------------------------------
+    peaks, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    bwd_avg_ms = bwd_ms / max(n_fit_iters, 1)
+    fwd_avg_ms = fwd_ms / max(n_fit_iters, 1)
+    units_launch = N * K
+    achieved_ginst = ADJ_OPS_PER_VS * units_launch / (bwd_avg_ms * 1e-3) / 1e9
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_ginst = alu_peak_ginst(sm_mhz, n_sm)
+    tr_vs = adjoint_traffic_per_vs()
+    roofline = {
+        "kernel": "backward_kernel (adjoint with checkpoint recompute + fused Adam)",
+        "bound": "alu", "achieved": achieved_ginst, "peak": peak_ginst, "unit": "Ginstr/s (FP32 pipe)",
+        "frac": achieved_ginst / peak_ginst,
+        "traffic": (tr_vs * units_launch) if tr_vs else None,
+        "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, %s)" % (n_sm, sm_mhz, peak_kind),
+        "ops_per_vehicle_step": ADJ_OPS_PER_VS,
+        "avg_launch_ms": bwd_avg_ms,
+        "hbm_achieved_gbs": (4.0 + 16.0 / a.ckpt) * units_launch / (bwd_avg_ms * 1e-3) / 1e9,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "vehicles_per_gpu": N, "K": K, "iters_per_step": a.iters,
+                   "ckpt_interval": a.ckpt, "vpt": a.vpt, "warps_per_segment": a.G, "warps_per_block": a.wpb,
+                   "l2": "inputs larger than L2 (targets %.1f GB per GPU)" % (K * N * 4 / 1e9),
+                   "parallelism": "dp%d (independent batches)" % world,
+                   "fwd_ms_per_timestep": fwd_avg_ms / K, "bwd_ms_per_timestep": bwd_avg_ms / K,
+                   "paper_context": "paper Fig. 1: < 30 ms per timestep forward and backward each at 2M vehicles "
+                                    "(RTX A5000 or 16-thread Xeon W-2255)",
+                   "final_mse_m2": final_loss},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": ms_e2e / e2e_steps},
+        "gpu_launches": launches_per_step * a.steps,
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, secs, desc = oracle_sample(iters=30)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank)
+    return run_gpu(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -112,12 +112,16 @@ const char *idm_last_error(const idm_ctx_t *ctx);
  * when the matching bits are set, IDM_OK otherwise. */
 int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
 
-/* Tuning knobs.  vpt: vehicles per thread (1, 2, 4 or 8; 0 = choose from
- * max_lane); ckpt_interval: steps between stored checkpoints of the adjoint
- * (1..64; default 16); warps_per_block: 1..8 (default 8). */
-int idm_set_tuning(idm_ctx_t *ctx, int vpt, int ckpt_interval, int warps_per_block);
+/* Kernel shape.  Whole lanes are packed into segments of at most
+ * 32 * vpt * warps_per_segment vehicles, each simulated by warps_per_segment
+ * warps of one block.  vpt: vehicles per thread (1, 2, 4 or 8; 0 = choose);
+ * warps_per_segment: 1, 2, 4 or 8 (0 = choose; default 4 with vpt 4);
+ * ckpt_interval: steps between stored checkpoints of the adjoint (1..64,
+ * default 8); warps_per_block: 1..16 (default 8; rounded to a multiple of
+ * warps_per_segment, and the adjoint caps it by its shared-memory tape). */
+int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block);
 
-/* Longest lane the library can simulate (vehicles). */
+/* Longest lane the library can simulate (vehicles): 32 * 8 * 8 = 2048. */
 int idm_max_lane_supported(void);
 
 /* Bytes of workspace a loss/gradient call on this scene would hold. */

@@ -36,7 +36,8 @@ struct idm_ctx {
     size_t held = 0;
     char err[512] = {0};
     int vpt_req = 0;
-    int C = 16;
+    int G_req = 0;
+    int C = 8;
     int wpb = 8;
     Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
     cudaStream_t cap_stream = nullptr;
@@ -99,16 +100,29 @@ int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
     return IDM_OK;
 }
 
-int pick_vpt(idm_ctx *c, int max_lane, int *vpt)
+// Kernel shape: VPT vehicles per thread, G warps per segment (capacity
+// 32*VPT*G vehicles).  The default packs several 100-vehicle lanes into one
+// 512-slot segment (VPT 4, G 4).
+int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
 {
-    int v = c->vpt_req;
-    if (v == 0) {
+    int v = c->vpt_req, g = c->G_req;
+    if (v == 0 && g == 0) {
+        v = 4;
+        g = 4;
+        while (32 * v * g < max_lane && g < 8) g <<= 1;
+        while (32 * v * g < max_lane && v < 8) v <<= 1;
+    } else if (v == 0) {
         v = 1;
-        while (32 * v < max_lane && v < 8) v <<= 1;
+        while (32 * v * g < max_lane && v < 8) v <<= 1;
+    } else if (g == 0) {
+        g = 1;
+        while (32 * v * g < max_lane && g < 8) g <<= 1;
     }
-    if (32 * v < max_lane)
-        return fail(c, IDM_ERR_ARG, "max_lane %d exceeds %d vehicles per warp segment (vpt %d)", max_lane, 32 * v, v);
+    if (32 * v * g < max_lane)
+        return fail(c, IDM_ERR_ARG, "max_lane %d exceeds %d vehicles per segment (vpt %d, %d warps)", max_lane,
+                    32 * v * g, v, g);
     *vpt = v;
+    *G = g;
     return IDM_OK;
 }
 
@@ -144,6 +158,8 @@ int check_sim(idm_ctx *c, const idm_sim_t *s)
 // Common preparation: buffers, initial gaps and warp segments.
 struct Prep {
     int vpt = 1;
+    int G = 1;
+    int wpb_f = 1;  // warps per block of the forward (a multiple of G)
     int grid_f = 1, grid_b = 1;
     int wpb_b = 1;  // warps per block of the adjoint (bounded by its shared-memory tape)
     SimArgs a;
@@ -153,13 +169,14 @@ int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const flo
             const idm_sim_t *sim, bool need_ckpt, bool need_loss, int obs_stride, Prep *P, cudaStream_t st)
 {
     int rc;
-    if ((rc = pick_vpt(c, sc->max_lane, &P->vpt))) return rc;
+    if ((rc = pick_shape(c, sc->max_lane, &P->vpt, &P->G))) return rc;
     const int N = sc->n_vehicles, L = sc->n_lanes;
+    const int G = P->G;
     if ((rc = ensure(c, c->seg, sizeof(Seg) * (size_t)L, "segments"))) return rc;
     if ((rc = ensure(c, c->ctl, sizeof(int) * CTL_N, "control"))) return rc;
     if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
     if ((rc = ensure(c, c->g0, sizeof(float) * (size_t)N, "initial gaps"))) return rc;
-    if ((rc = ensure(c, c->loss_part, sizeof(double) * (size_t)L, "loss partials"))) return rc;
+    if ((rc = ensure(c, c->loss_part, sizeof(double) * (size_t)L * G, "loss partials"))) return rc;
     if ((rc = ensure(c, c->loss_tmp, sizeof(double) * 2, "loss scalar"))) return rc;
     const int n_ck = (sim->K + c->C - 1) / c->C;
     if (need_ckpt && (rc = ensure(c, c->ckpt, sizeof(float) * 4 * (size_t)n_ck * N, "checkpoints"))) return rc;
@@ -189,15 +206,17 @@ int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const flo
     a.C = c->C;
     a.status = (unsigned *)c->status.p;
     a.N_total = N;
+    a.G = G;
     (void)need_loss;
 
     CK(cudaMemsetAsync(c->ctl.p, 0, sizeof(int) * 3, st));
     CK(idm::launch_prep_gap(sc->lane_off, L, p_init, sc->length, N, (float *)c->g0.p, a.status, st));
-    CK(idm::launch_build_segments(sc->lane_off, L, nullptr, 0, 32 * P->vpt, N, (Seg *)c->seg.p,
+    CK(idm::launch_build_segments(sc->lane_off, L, nullptr, 0, 32 * P->vpt * G, N, (Seg *)c->seg.p,
                                   (int *)c->ctl.p + CTL_NSEG, a.status, st));
-    const int warps_needed = L;
-    const int blocks_needed = (warps_needed + c->wpb - 1) / c->wpb;
-    int occ_f = idm::occupancy_blocks(P->vpt, false, false, false, false, c->wpb, 0);
+    P->wpb_f = std::max(G, (c->wpb / G) * G);
+    const int warps_needed = L * G;  // segments <= lanes
+    const int blocks_needed = (warps_needed + P->wpb_f - 1) / P->wpb_f;
+    int occ_f = idm::occupancy_blocks(P->vpt, G, false, false, false, false, P->wpb_f, 0);
     P->grid_f = std::min(blocks_needed, c->n_sm * occ_f);
     P->grid_f = P->grid_f < 1 ? 1 : P->grid_f;
     return IDM_OK;
@@ -206,14 +225,17 @@ int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const flo
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L)
 {
     const size_t smem_max = 227 * 1024;
-    const size_t per_warp = idm::backward_smem_bytes(P->vpt, dense, c->C, 1);
-    if (per_warp > smem_max)
-        return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per warp exceeds shared memory; lower "
-                                    "ckpt_interval", per_warp);
-    P->wpb_b = std::min<int>(c->wpb, (int)(smem_max / per_warp));
-    size_t smem = per_warp * P->wpb_b;
-    int occ_b = idm::occupancy_blocks(P->vpt, true, dense, adam, want_delta, P->wpb_b, smem);
-    int blocks_needed = (L + P->wpb_b - 1) / P->wpb_b;
+    const int G = P->G;
+    const size_t per_group = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G);
+    if (per_group > smem_max)
+        return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per segment exceeds shared memory; lower "
+                                    "ckpt_interval", per_group);
+    int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
+    if (G * 32 * groups > 256) groups = std::max(1, 256 / (32 * G));
+    P->wpb_b = groups * G;
+    size_t smem = per_group * groups;
+    int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem);
+    int blocks_needed = (L * G + P->wpb_b - 1) / P->wpb_b;
     P->grid_b = std::min(blocks_needed, c->n_sm * occ_b);
     P->grid_b = P->grid_b < 1 ? 1 : P->grid_b;
     return IDM_OK;
@@ -223,7 +245,7 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
 
 extern "C" {
 
-int idm_max_lane_supported(void) { return 256; }
+int idm_max_lane_supported(void) { return 2048; }
 
 int idm_ctx_create(idm_ctx_t **ctx, size_t workspace_cap_bytes)
 {
@@ -260,14 +282,18 @@ int idm_ctx_destroy(idm_ctx_t *c)
 
 const char *idm_last_error(const idm_ctx_t *c) { return c ? c->err : "no context"; }
 
-int idm_set_tuning(idm_ctx_t *c, int vpt, int ckpt_interval, int warps_per_block)
+int idm_set_tuning(idm_ctx_t *c, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block)
 {
     if (!c) return IDM_ERR_ARG;
     if (!(vpt == 0 || vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8))
         return fail(c, IDM_ERR_ARG, "vpt must be 0, 1, 2, 4 or 8");
+    if (!(warps_per_segment == 0 || warps_per_segment == 1 || warps_per_segment == 2 || warps_per_segment == 4 ||
+          warps_per_segment == 8))
+        return fail(c, IDM_ERR_ARG, "warps_per_segment must be 0, 1, 2, 4 or 8");
     if (ckpt_interval < 1 || ckpt_interval > 64) return fail(c, IDM_ERR_ARG, "ckpt_interval must be in [1, 64]");
-    if (warps_per_block < 1 || warps_per_block > 8) return fail(c, IDM_ERR_ARG, "warps_per_block must be in [1, 8]");
+    if (warps_per_block < 1 || warps_per_block > 16) return fail(c, IDM_ERR_ARG, "warps_per_block must be in [1, 16]");
     c->vpt_req = vpt;
+    c->G_req = warps_per_segment;
     c->C = ckpt_interval;
     c->wpb = warps_per_block;
     return IDM_OK;
@@ -278,7 +304,7 @@ size_t idm_workspace_bytes(const idm_ctx_t *c, const idm_scene_t *s, const idm_s
     if (!c || !s || !sim || sim->K < 1) return 0;
     size_t N = (size_t)s->n_vehicles, L = (size_t)s->n_lanes;
     size_t n_ck = (size_t)((sim->K + c->C - 1) / c->C);
-    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * L + 16 + 16 * n_ck * N;
+    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + 16 * n_ck * N;
 }
 
 int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
@@ -340,7 +366,7 @@ int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *para
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
     P.a.vtraj = vtraj;
-    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, false, P.a, P.grid_f, c->wpb, st));
+    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }
 
@@ -358,7 +384,7 @@ int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *par
     if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, false, 1, &P, st))) return rc;
     if ((rc = backward_grid(c, &P, true, false, grad && grad->delta, scene->n_lanes))) return rc;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, false, true, P.a, P.grid_f, c->wpb, st));
+    CK(idm::launch_forward(P.vpt, false, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     P.a.gP = gP;
     P.a.gV = gV;
@@ -390,8 +416,8 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     if ((rc = backward_grid(c, &P, false, false, want_delta, scene->n_lanes))) return rc;
     P.a.targets = targets;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, true, true, P.a, P.grid_f, c->wpb, st));
-    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
+    CK(idm::launch_forward(P.vpt, false, false, true, true, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.G, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     if (grad) {
         P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
@@ -445,7 +471,7 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
     } key;
     memset(&key, 0, sizeof key);
     key.a = a;
-    key.vpt = P.vpt; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = c->wpb; key.wpb_b = P.wpb_b;
+    key.vpt = P.vpt; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f; key.wpb_b = P.wpb_b;
     key.n_iter = n_iter; key.profiling = c->profiling; key.hist = loss_hist;
     static_assert(sizeof(Key) <= sizeof(((idm_ctx *)0)->fit_key), "fit key too large");
     const bool cached = c->fit_exec && c->fit_key_len == sizeof key && memcmp(c->fit_key, &key, sizeof key) == 0;
@@ -470,11 +496,11 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_F;
-                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, c->wpb, cs);
+                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, P.wpb_f, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
             if (e == cudaSuccess)
-                e = idm::launch_loss_finalize(a.loss_part, a.n_seg, loss_hist ? loss_hist + it : nullptr, cs);
+                e = idm::launch_loss_finalize(a.loss_part, a.n_seg, P.G, loss_hist ? loss_hist + it : nullptr, cs);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_B;

@@ -143,33 +143,35 @@ __device__ __forceinline__ float position(float p_init, const State &s)
     return __fadd_rn(t, __fadd_rn(err, s.xl));
 }
 
-// Leader values in the strided slot mapping: slot q = lane + 32 j; the
-// leader of slot q is q-1 (thread lane-1, same j; for lane 0, thread 31 of
-// j-1).  Slot 0 has no leader in the segment (it is a lane head) and gets 0.
+// Leader values in the strided slot mapping: slot q = lane + 32 j of the
+// warp; the leader of slot q is q-1 (thread lane-1, same j; for lane 0,
+// thread 31 of j-1).  The warp's first slot receives lead_in (the previous
+// warp's last slot, or 0 at the start of a segment, which is a lane head).
 template <int VPT>
-__device__ __forceinline__ void leader_vals(const float (&x)[VPT], float (&out)[VPT], int lane)
+__device__ __forceinline__ void leader_vals(const float (&x)[VPT], float (&out)[VPT], int lane, float lead_in)
 {
     float rot[VPT];
 #pragma unroll
     for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 31) & 31);
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
-        float prev = j > 0 ? rot[j - 1] : 0.0f;
+        float prev = j > 0 ? rot[j - 1] : lead_in;
         out[j] = lane == 0 ? prev : rot[j];
     }
 }
 
 // Follower values: slot q receives from slot q+1 (thread lane+1, same j;
-// for lane 31, thread 0 of j+1).  The last slot gets 0.
+// for lane 31, thread 0 of j+1).  The warp's last slot receives fin (the
+// next warp's first slot, or 0 at the end of a segment).
 template <int VPT>
-__device__ __forceinline__ void follower_vals(const float (&x)[VPT], float (&out)[VPT], int lane)
+__device__ __forceinline__ void follower_vals(const float (&x)[VPT], float (&out)[VPT], int lane, float fin)
 {
     float rot[VPT];
 #pragma unroll
     for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 1) & 31);
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
-        float nxt = j + 1 < VPT ? rot[j + 1] : 0.0f;
+        float nxt = j + 1 < VPT ? rot[j + 1] : fin;
         out[j] = lane == 31 ? nxt : rot[j];
     }
 }

@@ -39,11 +39,12 @@ struct SimArgs {
     const ScenDesc *scen_tab;   // NULL: every segment uses scen0
     ScenDesc scen0;
     const float *g0;            // initial raw gap (+inf for lane heads)
+    int G;                      // warps per segment (1, 2, 4 or 8)
     const float *v0, *T, *s0, *am, *b, *delta;
     const float *p_init, *v_init;
     float *traj, *vtraj;
     const float *targets;
-    double *loss_part;          // [n_seg] per-segment loss
+    double *loss_part;          // [n_seg * G] per-warp loss
     float *ckpt;
     int C;                      // checkpoint interval (steps)
     unsigned *status;
@@ -68,10 +69,10 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt,
                            int grid, int wpb, cudaStream_t st);
 cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
-size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb);
-size_t forward_smem_bytes(int vpt, int wpb);
-cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, cudaStream_t st);
-int occupancy_blocks(int vpt, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb);
+size_t forward_smem_bytes(int vpt, int G, int wpb);
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st);
+int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
 
 // Layout (idm_layout.cu).
 cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,

@@ -180,6 +180,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int FWD_RING = 4;
 constexpr int FWD_PD = 3;
 
+// dst/src_row already point at this warp's first slot.
 template <int VPT>
 __device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, int lane, const bool (&valid)[VPT])
 {
@@ -188,13 +189,98 @@ __device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, i
         if (valid[j]) cp_async4(dst + lane + 32 * j, src_row + lane + 32 * j);
 }
 
+// ---------------------------------------------------------------------------
+// Warp groups.  A segment of up to 32*VPT*G vehicles is run by G warps of
+// one block (G = 1: a single warp, no barrier).  Warp w of the group holds
+// slots [w*32*VPT, (w+1)*32*VPT).  Per step, the leader value of each warp's
+// first slot and (in the adjoint) the follower terms of each warp's last
+// slot cross warp boundaries through double-buffered shared cells and one
+// named barrier (bar.sync id, 32*G) per exchange.
+// ---------------------------------------------------------------------------
+struct Grp {
+    int G;       // warps per segment
+    int w;       // warp index in the group
+    int lane;
+    int bar;     // named barrier id (1 + group index in the block)
+    int *cell;   // [2] work-item broadcast
+    float *xl;   // [2][G] leader exchange
+    float *xf;   // [2][2][G] follower exchange
+};
+
+// Shared floats of one group's control area (cells + exchange cells).
+__host__ __device__ __forceinline__ int grp_ctrl_floats(int G) { return ((2 + 6 * G) + 3) & ~3; }
+
+__device__ __forceinline__ void grp_sync(const Grp &g)
+{
+    if (g.G > 1)
+        asm volatile("bar.sync %0, %1;" ::"r"(g.bar), "r"(32 * g.G) : "memory");
+    else
+        __syncwarp();
+}
+
+__device__ __forceinline__ Grp make_grp(int G, float *ctrl)
+{
+    Grp g;
+    g.G = G;
+    const int warp = threadIdx.x >> 5;
+    g.w = warp % G;
+    g.lane = threadIdx.x & 31;
+    g.bar = 1 + warp / G;
+    g.cell = reinterpret_cast<int *>(ctrl);
+    g.xl = ctrl + 2;
+    g.xf = ctrl + 2 + 2 * G;
+    return g;
+}
+
+__device__ __forceinline__ int grp_next(const Grp &g, int *work, int &par)
+{
+    if (g.G == 1) return next_segment(work, g.lane);
+    if (g.w == 0 && g.lane == 0) g.cell[par] = atomicAdd(work, 1);
+    grp_sync(g);
+    const int s = g.cell[par];
+    par ^= 1;
+    return s;
+}
+
+// Leader speed of this warp's first slot (0 for the group's first warp).
 template <int VPT>
-__device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, VehConst (&kc)[VPT],
+__device__ __forceinline__ float grp_lead_in(const Grp &g, const float (&v)[VPT], int &xp)
+{
+    if (g.G == 1) return 0.0f;
+    if (g.lane == 31) g.xl[xp * g.G + g.w] = v[VPT - 1];
+    grp_sync(g);
+    const float r = g.w > 0 ? g.xl[xp * g.G + g.w - 1] : 0.0f;
+    xp ^= 1;
+    return r;
+}
+
+// Follower terms arriving at this warp's last slot (0 for the last warp).
+__device__ __forceinline__ void grp_follow_in(const Grp &g, float p_first, float v_first, float &in_p, float &in_v,
+                                              int &xp)
+{
+    in_p = 0.0f;
+    in_v = 0.0f;
+    if (g.G == 1) return;
+    float *c = g.xf + xp * 2 * g.G;
+    if (g.lane == 0) {
+        c[g.w] = p_first;
+        c[g.G + g.w] = v_first;
+    }
+    grp_sync(g);
+    if (g.w + 1 < g.G) {
+        in_p = c[g.w + 1];
+        in_v = c[g.G + g.w + 1];
+    }
+    xp ^= 1;
+}
+
+template <int VPT>
+__device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, int wb, VehConst (&kc)[VPT],
                                               State (&st)[VPT], float (&pin)[VPT], bool (&valid)[VPT])
 {
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
-        const int q = lane + 32 * j;
+        const int q = wb + lane + 32 * j;
         valid[j] = q < sg.n_veh;
         if (valid[j]) {
             const int gi = sg.veh_begin + q;
@@ -210,8 +296,9 @@ __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, i
 }
 
 
-// True when every occupied slot of the warp segment has delta == 4, so the
-// step body can use the squaring form of (v/v0)^delta with no branch.
+// True when every occupied slot of the warp has delta == 4, so the step body
+// can use the squaring form of (v/v0)^delta with no branch.  (Both variants
+// execute the same sequence of group barriers.)
 template <int VPT>
 __device__ __forceinline__ bool segment_is_d4(const VehConst (&kc)[VPT], const bool (&valid)[VPT])
 {
@@ -231,16 +318,19 @@ struct FwdFlags {
 };
 
 template <int VPT, bool D4>
-__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, int lane,
+__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
                                                 const VehConst (&kc)[VPT], State (&st)[VPT], const float (&pin)[VPT],
                                                 const bool (&valid)[VPT], FwdFlags f, float *ring)
 {
     constexpr int SL = 32 * VPT;
+    const int lane = g.lane;
     const int Ns = sc.n_veh;
+    const int wl = lb + g.w * SL;  // scenario-local index of this warp's first slot
     float lsum = 0.0f, lcomp = 0.0f;
     int next_obs = sc.obs_stride, obs_row = 0;
     int next_ck = 0, ck_idx = 0;
-    const float *ybase = a.targets + sc.tgt_off + lb;
+    int xp = 0;
+    const float *ybase = a.targets + sc.tgt_off + wl;
     if (f.loss) {
 #pragma unroll
         for (int r = 0; r < FWD_PD; ++r) {
@@ -250,7 +340,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     }
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
-            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + lb;
+            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
@@ -264,7 +354,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             ++ck_idx;
         }
         if (f.traj || f.vtraj) {
-            const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+            const size_t row = sc.traj_off + (size_t)k * Ns + wl;
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
@@ -293,7 +383,8 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
         float vcur[VPT], vh[VPT];
 #pragma unroll
         for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-        leader_vals<VPT>(vcur, vh, lane);
+        const float lead_in = grp_lead_in<VPT>(g, vcur, xp);
+        leader_vals<VPT>(vcur, vh, lane, lead_in);
 #pragma unroll
         for (int j = 0; j < VPT; ++j) {
             float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
@@ -308,7 +399,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
     if (f.loss) {
         double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
-        if (lane == 0) a.loss_part[s_idx] = part;
+        if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
     }
 }
 
@@ -317,10 +408,14 @@ __global__ void __launch_bounds__(512)
 forward_kernel(SimArgs a, FwdFlags f)
 {
     extern __shared__ float fsmem[];
-    const int lane = threadIdx.x & 31;
-    float *ring = fsmem + (threadIdx.x >> 5) * FWD_RING * 32 * VPT;
+    const int G = a.G;
+    const int warp = threadIdx.x >> 5;
+    float *ring = fsmem + warp * FWD_RING * 32 * VPT;
+    float *ctrl = fsmem + (blockDim.x >> 5) * FWD_RING * 32 * VPT + (warp / G) * grp_ctrl_floats(G);
+    Grp g = make_grp(G, ctrl);
+    int par = 0;
     for (;;) {
-        const int s_idx = next_segment(a.work, lane);
+        const int s_idx = grp_next(g, a.work, par);
         if (s_idx >= *a.n_seg) break;
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
@@ -329,45 +424,50 @@ forward_kernel(SimArgs a, FwdFlags f)
         State st[VPT];
         float pin[VPT];
         bool valid[VPT];
-        load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
+        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            forward_segment<VPT, true>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f, ring);
+            forward_segment<VPT, true>(a, sc, s_idx, lb, g, kc, st, pin, valid, f, ring);
         else
-            forward_segment<VPT, false>(a, sc, s_idx, lb, lane, kc, st, pin, valid, f, ring);
+            forward_segment<VPT, false>(a, sc, s_idx, lb, g, kc, st, pin, valid, f, ring);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint.  Per segment of C steps (last first): reload the checkpoint,
-// recompute the C steps into a shared-memory tape of (v, raw gap[, seed]),
+// Adjoint.  Per segment of C steps (last first): cp.async the observed
+// targets of the C steps into the seed tape, reload the checkpoint,
+// recompute the C steps into the group's shared tape of (v, raw gap, seed),
 // then run the reverse recurrences
 //   lp_k = seed_k + lp_{k+1} + mu A_p + mu_f A_ph(f)
 //   lv_k = dt lp_{k+1} + lv_{k+1} + mu A_v + mu_f A_vh(f)
-// with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle.
-// Parameter gradients accumulate in float per checkpoint segment and the
-// segment sums are added into the totals (pairwise-style summation).
+// with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle
+// (and across warps through the group's exchange cells).  Gradient
+// increments accumulate in registers per checkpoint segment and are added
+// to per-slot totals in shared memory.
 // ---------------------------------------------------------------------------
-// Per-warp shared memory of the adjoint: tape v[C][SL], gap[C][SL],
-// (MSE) targets-then-seeds[C][SL], and the six gradient totals [6][SL].
-template <int VPT, bool DENSE>
-__device__ __forceinline__ float *tape_base(float *smem, int C)
+// Shared floats of one group: tape v/gap[/seed] [C][G*SL], totals [6][G*SL],
+// control area.
+__host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, int C, int G)
 {
-    const int per_warp = ((DENSE ? 2 : 3) * C + 6) * 32 * VPT;
-    return smem + (threadIdx.x >> 5) * per_warp;
+    return ((dense ? 2 : 3) * C + 6) * 32 * vpt * G + grp_ctrl_floats(G);
 }
 
 template <int VPT, bool DENSE, bool ADAM, bool WD, bool D4>
-__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int lb,
-                                                 int lane, float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
+__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int lb, Grp &g,
+                                                 float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
                                                  const float (&pin)[VPT], const bool (&valid)[VPT])
 {
     constexpr int SL = 32 * VPT;
-    float *tg = tv + a.C * SL;
-    float *tr = tg + a.C * SL;                         // targets, then seeds (MSE only)
-    float *acc = tv + (DENSE ? 2 : 3) * a.C * SL;      // gradient totals [6][SL]
+    const int SLG = SL * g.G;
+    const int lane = g.lane;
+    const int wb = g.w * SL;                      // this warp's first slot in the group
+    float *tg = tv + a.C * SLG;
+    float *tr = tg + a.C * SLG;                   // targets, then seeds (MSE only)
+    float *acc = tv + (DENSE ? 2 : 3) * a.C * SLG;  // gradient totals [6][SLG]
     const int Ns = sc.n_veh;
+    const int wl = lb + wb;                       // scenario-local index of this warp's first slot
     const float dt = sc.dt;
     const float seed_scale = 2.0f * sc.inv_nobs;
+    int xp = 0, fp = 0;
 
     float lp[VPT], lv[VPT];
 #pragma unroll
@@ -375,7 +475,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         lp[j] = 0.0f;
         lv[j] = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q * SL + lane + 32 * j] = 0.0f;
+        for (int q = 0; q < 6; ++q) acc[q * SLG + wb + lane + 32 * j] = 0.0f;
     }
 
     const int n_ck = (sc.K + a.C - 1) / a.C;
@@ -387,12 +487,12 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         if (obs_k == 0) obs_k = sc.obs_stride;
         if (!DENSE) {  // fetch the segment's observed targets into the seed tape
             for (int k = obs_k; k < c0 + n && k / sc.obs_stride <= sc.n_obs; k += sc.obs_stride)
-                prefetch_row<VPT>(tr + (k - c0) * SL, a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb,
-                                  lane, valid);
+                prefetch_row<VPT>(tr + (k - c0) * SLG + wb,
+                                  a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl, lane, valid);
             cp_async_commit();
         }
         {
-            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + lb;
+            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
@@ -404,7 +504,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         // recompute the segment into the tape
         for (int s = 0; s < n; ++s) {
             const int k = c0 + s;
-            float *rv = tv + s * SL, *rg = tg + s * SL;
+            float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 rv[lane + 32 * j] = st[j].v;
@@ -412,7 +512,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             }
             if (!DENSE && k == obs_k) {
                 if (k / sc.obs_stride <= sc.n_obs) {
-                    float *rr = tr + s * SL;
+                    float *rr = tr + s * SLG + wb;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) {
                         float r = valid[j] ? residual(pin[j], st[j], rr[lane + 32 * j]) : 0.0f;
@@ -424,7 +524,8 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             float vcur[VPT], vh[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-            leader_vals<VPT>(vcur, vh, lane);
+            const float lead_in = grp_lead_in<VPT>(g, vcur, xp);
+            leader_vals<VPT>(vcur, vh, lane, lead_in);
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
                 float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
@@ -433,7 +534,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         }
         if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
             if (DENSE) {
-                const size_t row = sc.traj_off + (size_t)sc.K * Ns + lb;
+                const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
 #pragma unroll
                 for (int j = 0; j < VPT; ++j) {
                     if (!valid[j]) continue;
@@ -444,14 +545,14 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 const int k = sc.K;
                 const bool obs = sc.n_obs > 0 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
                 if (obs) {
-                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + lb;
+                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j)
                         if (valid[j]) lp[j] = __fmul_rn(seed_scale, residual(pin[j], st[j], __ldg(y + lane + 32 * j)));
                 }
             }
         }
-        __syncwarp();
+        grp_sync(g);  // the whole group's tape is written
 
         float sacc[6][VPT];
 #pragma unroll
@@ -463,11 +564,11 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         int obs_hi = ((c0 + n - 1) / sc.obs_stride) * sc.obs_stride;
         for (int s = n - 1; s >= 0; --s) {
             const int k = c0 + s;
-            const float *rv = tv + s * SL, *rg = tg + s * SL;
+            const float *rv = tv + s * SLG, *rg = tg + s * SLG;
             float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
-                const int q = lane + 32 * j;
+                const int q = wb + lane + 32 * j;
                 const float v = rv[q];
                 const float gap = rg[q];
                 const float vh = q > 0 ? rv[q - 1] : 0.0f;
@@ -484,14 +585,16 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 sacc[4][j] += t.f_rd;
                 if (WD) sacc[5][j] += t.f_rdlnr;
             }
+            float in_p, in_v;
+            grp_follow_in(g, to_lp[0], to_lv[0], in_p, in_v, fp);
             float from_p[VPT], from_v[VPT];
-            follower_vals<VPT>(to_lp, from_p, lane);
-            follower_vals<VPT>(to_lv, from_v, lane);
+            follower_vals<VPT>(to_lp, from_p, lane, in_p);
+            follower_vals<VPT>(to_lv, from_v, lane, in_v);
             float seed_p[VPT], seed_v[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j) { seed_p[j] = 0.0f; seed_v[j] = 0.0f; }
             if (DENSE) {
-                const size_t row = sc.traj_off + (size_t)k * Ns + lb;
+                const size_t row = sc.traj_off + (size_t)k * Ns + wl;
 #pragma unroll
                 for (int j = 0; j < VPT; ++j) {
                     if (!valid[j]) continue;
@@ -500,7 +603,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 }
             } else if (k == obs_hi) {
                 if (k >= 1 && k / sc.obs_stride <= sc.n_obs) {
-                    const float *rr = tr + s * SL;
+                    const float *rr = tr + s * SLG + wb;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
                 }
@@ -517,8 +620,8 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) acc[q * SL + lane + 32 * j] += sacc[q][j];
-        __syncwarp();
+            for (int j = 0; j < VPT; ++j) acc[q * SLG + wb + lane + 32 * j] += sacc[q][j];
+        grp_sync(g);  // the tape may be overwritten by the next segment
     }
 
     // epilogue: parameter gradients from the factored sums
@@ -526,20 +629,20 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
         if (!valid[j]) continue;
-        const int q = lane + 32 * j;
+        const int q = wb + lane + 32 * j;
         const int gi = sg.veh_begin + q;
         const float v0 = a.v0[gi], b = a.b[gi];
         const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
-        const float A0 = acc[0 * SL + q], A1 = acc[1 * SL + q], A2 = acc[2 * SL + q];
-        const float A3 = acc[3 * SL + q], A4 = acc[4 * SL + q], A5 = acc[5 * SL + q];
-        float g[6];
-        g[0] = am * dl * A4 / v0;                 // v0
-        g[1] = A1;                                // T
-        g[2] = A0;                                // s0
-        g[3] = A3 - A2 * c / (2.0f * am);         // a_max
-        g[4] = -A2 * c / (2.0f * b);              // b
-        g[5] = -am * A5;                          // delta
-        for (int p = 0; p < 6; ++p) bad |= !isfinite(g[p]);
+        const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
+        const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+        float gr[6];
+        gr[0] = am * dl * A4 / v0;                 // v0
+        gr[1] = A1;                                // T
+        gr[2] = A0;                                // s0
+        gr[3] = A3 - A2 * c / (2.0f * am);         // a_max
+        gr[4] = -A2 * c / (2.0f * b);              // b
+        gr[5] = -am * A5;                          // delta
+        for (int p = 0; p < 6; ++p) bad |= !isfinite(gr[p]);
         if (ADAM) {
             const int it = a.iter;
             const int t = it + 1;
@@ -550,8 +653,8 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 #pragma unroll
             for (int p = 0; p < 5; ++p) {
                 const size_t mi = (size_t)p * a.N_total + gi;
-                float m = 0.9f * a.adam_m[mi] + 0.1f * g[p];
-                float vv = 0.999f * a.adam_v[mi] + 0.001f * g[p] * g[p];
+                float m = 0.9f * a.adam_m[mi] + 0.1f * gr[p];
+                float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[p] * gr[p];
                 a.adam_m[mi] = m;
                 a.adam_v[mi] = vv;
                 float x = th[p][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
@@ -559,12 +662,12 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 th[p][gi] = x;
             }
         } else {
-            if (a.g_v0) a.g_v0[gi] = g[0];
-            if (a.g_T) a.g_T[gi] = g[1];
-            if (a.g_s0) a.g_s0[gi] = g[2];
-            if (a.g_am) a.g_am[gi] = g[3];
-            if (a.g_b) a.g_b[gi] = g[4];
-            if (a.g_delta) a.g_delta[gi] = WD ? g[5] : 0.0f;
+            if (a.g_v0) a.g_v0[gi] = gr[0];
+            if (a.g_T) a.g_T[gi] = gr[1];
+            if (a.g_s0) a.g_s0[gi] = gr[2];
+            if (a.g_am) a.g_am[gi] = gr[3];
+            if (a.g_b) a.g_b[gi] = gr[4];
+            if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
             if (a.g_p_init) a.g_p_init[gi] = lp[j];
             if (a.g_v_init) a.g_v_init[gi] = lv[j];
         }
@@ -577,10 +680,14 @@ __global__ void __launch_bounds__(256, (VPT <= 4 ? 2 : 1))
 backward_kernel(SimArgs a)
 {
     extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    float *tv = tape_base<VPT, DENSE>(smem, a.C);
+    const int G = a.G;
+    const int warp = threadIdx.x >> 5;
+    float *gbase = smem + (warp / G) * bwd_group_floats(VPT, DENSE, a.C, G);
+    float *ctrl = gbase + bwd_group_floats(VPT, DENSE, a.C, G) - grp_ctrl_floats(G);
+    Grp g = make_grp(G, ctrl);
+    int par = 0;
     for (;;) {
-        const int s_idx = next_segment(a.work, lane);
+        const int s_idx = grp_next(g, a.work, par);
         if (s_idx >= *a.n_seg) break;
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
@@ -589,11 +696,11 @@ backward_kernel(SimArgs a)
         State st[VPT];
         float pin[VPT];
         bool valid[VPT];
-        load_vehicles<VPT>(a, sg, lane, kc, st, pin, valid);
+        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, lb, lane, tv, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, lb, g, gbase, kc, st, pin, valid);
         else
-            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, lb, lane, tv, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, lb, g, gbase, kc, st, pin, valid);
     }
 }
 
@@ -601,10 +708,10 @@ backward_kernel(SimArgs a)
 // Deterministic loss reduction over segments (fixed order).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-loss_finalize_kernel(const double *part, const int *n_seg, double *out)
+loss_finalize_kernel(const double *part, const int *n_seg, int per_seg, double *out)
 {
     __shared__ double sh[1024];
-    const int n = *n_seg;
+    const int n = *n_seg * per_seg;
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     sh[threadIdx.x] = s;
@@ -616,9 +723,9 @@ loss_finalize_kernel(const double *part, const int *n_seg, double *out)
     if (threadIdx.x == 0 && out) *out = sh[0];
 }
 
-cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, double *out, cudaStream_t st)
+cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st)
 {
-    loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, out);
+    loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, per_seg, out);
     return cudaGetLastError();
 }
 
@@ -637,7 +744,7 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt,
     case 8: fn = (void *)forward_kernel<8>; break;
     default: return cudaErrorInvalidValue;
     }
-    const size_t smem = forward_smem_bytes(vpt, wpb);
+    const size_t smem = forward_smem_bytes(vpt, a.G, wpb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SimArgs args = a;
@@ -645,12 +752,15 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt,
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
-size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int wpb)
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb)
 {
-    return (size_t)((dense_seed ? 2 : 3) * C + 6) * 32 * vpt * sizeof(float) * wpb;
+    return (size_t)bwd_group_floats(vpt, dense_seed, C, G) * (wpb / G) * sizeof(float);
 }
 
-size_t forward_smem_bytes(int vpt, int wpb) { return (size_t)FWD_RING * 32 * vpt * sizeof(float) * wpb; }
+size_t forward_smem_bytes(int vpt, int G, int wpb)
+{
+    return ((size_t)FWD_RING * 32 * vpt * wpb + (size_t)grp_ctrl_floats(G) * (wpb / G)) * sizeof(float);
+}
 
 // Kernel variants of the adjoint: seeds from dense gradients or from targets,
 // fused Adam or gradient output, with or without the delta gradient.
@@ -679,7 +789,7 @@ cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta
     if (dense_seed && adam) return cudaErrorInvalidValue;
     void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam);
     if (!fn) return cudaErrorInvalidValue;
-    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, wpb);
+    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, a.G, wpb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SimArgs args = a;
@@ -687,7 +797,7 @@ cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
-int occupancy_blocks(int vpt, bool backward, bool dense, bool adam, bool want_delta, int wpb, size_t smem)
+int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool want_delta, int wpb, size_t smem)
 {
     void *fn = nullptr;
     if (!backward) {
@@ -697,7 +807,7 @@ int occupancy_blocks(int vpt, bool backward, bool dense, bool adam, bool want_de
         case 4: fn = (void *)forward_kernel<4>; break;
         case 8: fn = (void *)forward_kernel<8>; break;
         }
-        smem = forward_smem_bytes(vpt, wpb);
+        smem = forward_smem_bytes(vpt, G, wpb);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
         fn = backward_fn_v(vpt, dense, adam, want_delta && !adam);

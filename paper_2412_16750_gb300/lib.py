@@ -46,7 +46,7 @@ _SIGS = {
     "idm_ctx_destroy": (ctypes.c_int, [_vp]),
     "idm_last_error": (ctypes.c_char_p, [_vp]),
     "idm_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), _vp]),
-    "idm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "idm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "idm_max_lane_supported": (ctypes.c_int, []),
     "idm_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_sim_t)]),
     "idm_layout": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -147,8 +147,8 @@ def idm_status(ctx, stream=None):
     return rc, flags.value
 
 
-def idm_set_tuning(ctx, vpt=0, ckpt_interval=16, warps_per_block=8):
-    return check(ctx, load().idm_set_tuning(ctx, vpt, ckpt_interval, warps_per_block))
+def idm_set_tuning(ctx, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=8):
+    return check(ctx, load().idm_set_tuning(ctx, vpt, warps_per_segment, ckpt_interval, warps_per_block))
 
 
 def idm_max_lane_supported():

@@ -43,7 +43,7 @@ def test_binding_covers_the_header(libpath):
 def test_query_without_device(libpath):
     from paper_2412_16750_gb300 import lib
     lib.load(libpath)
-    assert lib.idm_max_lane_supported() == 256
+    assert lib.idm_max_lane_supported() == 2048
 
 
 def test_null_context_is_rejected(libpath):
@@ -51,7 +51,7 @@ def test_null_context_is_rejected(libpath):
     L = lib.load(libpath)
     assert L.idm_ctx_create(None, 0) == lib.IDM_ERR_ARG
     assert L.idm_ctx_destroy(None) == lib.IDM_OK
-    assert L.idm_set_tuning(None, 0, 16, 8) == lib.IDM_ERR_ARG
+    assert L.idm_set_tuning(None, 0, 0, 16, 8) == lib.IDM_ERR_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path):

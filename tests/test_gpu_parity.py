@@ -149,8 +149,8 @@ def test_autograd_function(api):
 EDGE_COUNTS = [1, 2, 3, 33, 0, 17, 31, 32, 1, 5]
 
 
-@pytest.mark.parametrize("vpt,C", [(2, 1), (2, 7), (4, 16), (8, 5), (0, 64)])
-def test_edge_lanes(api, vpt, C):
+@pytest.mark.parametrize("vpt,G,C", [(2, 1, 1), (2, 2, 7), (4, 4, 16), (1, 8, 5), (0, 0, 64), (4, 1, 8), (8, 2, 3)])
+def test_edge_lanes(api, vpt, G, C):
     rng = np.random.default_rng(104)
     sc = synth.make_scene(EDGE_COUNTS, rng)
     K, s = 37, 3
@@ -158,12 +158,34 @@ def test_edge_lanes(api, vpt, C):
     N = int(sc["lane_off"][-1])
     theta = synth.f32(sc["theta_true"] * rng.uniform(0.8, 1.2, size=(6, N)))
     L, g, gp, gv, _ = oracle_loss_grad(sc, theta, Y, K, s)
-    ctx = api.Context(vpt=vpt, ckpt_interval=C, warps_per_block=4)
+    ctx = api.Context(vpt=vpt, warps_per_segment=G, ckpt_interval=C, warps_per_block=8)
     Lg, gg, gpg, gvg = run_loss_grad(api, sc, theta, Y, K, s, ctx=ctx)
     assert ctx.check_status() == 0
     assert Lg == pytest.approx(L, rel=1e-5)
     grad_close(gg, g)
     grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+
+
+@pytest.mark.parametrize("counts,vpt,G", [([1000, 37, 500], 4, 8), ([2048, 3], 8, 8), ([300, 200, 129], 2, 8)])
+def test_long_lanes_multiwarp(api, counts, vpt, G):
+    """Lanes longer than one warp's slots: leader values and follower terms
+    cross warp boundaries inside a segment every step."""
+    rng = np.random.default_rng(115)
+    sc = synth.make_scene(counts, rng)
+    K, s = 24, 2
+    Y = noisy_targets(sc, K, s, rng)
+    N = int(sc["lane_off"][-1])
+    theta = synth.f32(sc["theta_true"] * rng.uniform(0.9, 1.1, size=(6, N)))
+    L, g, gp, gv, P = oracle_loss_grad(sc, theta, Y, K, s)
+    ctx = api.Context(vpt=vpt, warps_per_segment=G, ckpt_interval=5, warps_per_block=8)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, theta, Y, K, s, ctx=ctx)
+    assert ctx.check_status() == 0
+    assert Lg == pytest.approx(L, rel=1e-5)
+    grad_close(gg, g)
+    grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+    traj = api.simulate(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, A_MIN,
+                        ctx=ctx).double().cpu().numpy()
+    assert np.max(np.abs(traj - P)) <= POS_TOL
 
 
 def test_single_step(api):
@@ -250,7 +272,7 @@ def test_argument_errors(api):
     with pytest.raises(lib.IdmError) as e:
         api.loss_grad(th, p0, v0, scn, 5, DT, cuda(np.zeros((5, 6))), 0)
     assert e.value.code == lib.IDM_ERR_ARG
-    big = api.Scene(scn.lane_off, scn.length, 300)
+    big = api.Scene(scn.lane_off, scn.length, 3000)
     with pytest.raises(lib.IdmError) as e:
         api.simulate(th, p0, v0, big, 5, DT)
     assert e.value.code == lib.IDM_ERR_ARG
