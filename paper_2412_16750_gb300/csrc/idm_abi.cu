@@ -111,6 +111,12 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
         g = 4;
         while (32 * v * g < max_lane && g < 8) g <<= 1;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
+        // shrink the segment while the adjoint tape would not fit shared memory
+        while (idm::backward_smem_bytes(v, false, c->C, g, g) > 227 * 1024) {
+            if (g > 1 && 32 * v * (g / 2) >= max_lane) g /= 2;
+            else if (v > 1 && 32 * (v / 2) * g >= max_lane) v /= 2;
+            else break;
+        }
     } else if (v == 0) {
         v = 1;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
