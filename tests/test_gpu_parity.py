@@ -185,7 +185,9 @@ def test_long_lanes_multiwarp(api, counts, vpt, G):
     grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
     traj = api.simulate(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, A_MIN,
                         ctx=ctx).double().cpu().numpy()
-    assert np.max(np.abs(traj - P)) <= POS_TOL
+    # positions reach tens of km behind a 1,000-vehicle lane head, where one
+    # float32 ulp of the output exceeds 1e-3 m: allow 1e-3 m plus 2 ulp
+    np.testing.assert_allclose(traj, P, rtol=2.4e-7, atol=POS_TOL)
 
 
 def test_single_step(api):
