@@ -213,6 +213,58 @@ int idm_fit(idm_ctx_t *ctx, const idm_scene_t *scene, idm_params_t *params,
             const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
             const float *box_lo, const float *box_hi, double *loss_hist, void *stream);
 
+/* ---- batched uneven scenarios ------------------------------------------ */
+
+/* Many independent scenes in one launch.  Scenario s owns lanes
+ * [scen_lane_off[s], scen_lane_off[s+1]) of the common lane CSR, and is
+ * simulated for K[s] steps of dt[s] with observed steps j*obs_stride[s].
+ * Per-scenario time-major arrays are concatenated in scenario order:
+ *   trajectories: scenario s is a [(K[s]+1)][N_s] block,
+ *   targets:      scenario s is a [floor(K[s]/obs_stride[s])][N_s] block,
+ * where N_s is the scenario's vehicle count (idm_batch_sizes gives the
+ * totals).  The host plans the launch (scenario table, warp segments,
+ * longest-first order) and uploads it to the context's workspace; the
+ * upload synchronises `stream`. */
+typedef struct {
+    int32_t n_scen;
+    const int32_t *scen_lane_off;  /* HOST [n_scen+1], from 0 to n_lanes */
+    const int32_t *K;              /* HOST [n_scen], >= 1 */
+    const float *dt;               /* HOST [n_scen], > 0 */
+    const int32_t *obs_stride;     /* HOST [n_scen], >= 1 (NULL: every step) */
+    float a_min;                   /* shared deceleration bound, < 0 */
+    int32_t n_lanes;
+    int32_t n_vehicles;
+    const int32_t *lane_off_host;  /* HOST [n_lanes+1] lane CSR (head-first lanes) */
+    const int32_t *lane_off;       /* DEVICE [n_lanes+1], the same values */
+    const float *length;           /* DEVICE [n_vehicles] */
+} idm_batch_t;
+
+/* Element counts of the concatenated trajectory, target and checkpoint
+ * arrays of a batch (host only; any output may be NULL). */
+int idm_batch_sizes(const idm_batch_t *batch, int ckpt_interval, int64_t *traj_elems, int64_t *target_elems,
+                    int64_t *ckpt_elems);
+
+/* Positions of every scenario (concatenated [(K_s+1)][N_s] blocks). */
+int idm_batch_forward(idm_ctx_t *ctx, const idm_batch_t *batch, const idm_params_t *params,
+                      const float *p_init, const float *v_init, float *traj, void *stream);
+
+/* Per-scenario squared-error losses L_s (the single-scene definition applied
+ * to each scenario; device double [n_scen], may be NULL), their sum
+ * (device double, may be NULL), and the gradients of the sum. */
+int idm_batch_loss_grad(idm_ctx_t *ctx, const idm_batch_t *batch, const idm_params_t *params,
+                        const float *p_init, const float *v_init, const float *targets, double *scen_loss,
+                        double *loss_total, idm_params_t *grad, float *grad_p_init, float *grad_v_init,
+                        void *stream);
+
+/* idm_fit over a batch: n_iter Adam iterations on the sum of the scenario
+ * losses, the whole fit captured as one CUDA graph.  loss_hist (device
+ * double [n_iter], may be NULL) receives the summed loss before each update,
+ * scen_loss (device double [n_scen], may be NULL) the per-scenario losses of
+ * the last iteration. */
+int idm_batch_fit(idm_ctx_t *ctx, const idm_batch_t *batch, idm_params_t *params, const float *p_init,
+                  const float *v_init, const float *targets, int32_t n_iter, float lr0, float lr1,
+                  const float *box_lo, const float *box_hi, double *loss_hist, double *scen_loss, void *stream);
+
 /* ---- measurement ------------------------------------------------------ */
 
 /* When on, idm_fit records CUDA events around every forward and adjoint

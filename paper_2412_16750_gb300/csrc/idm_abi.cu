@@ -12,44 +12,16 @@
 #include <new>
 
 #include "../../include/idm.h"
+#include "idm_ctx.h"
 #include "idm_internal.h"
 
 using idm::ScenDesc;
 using idm::Seg;
 using idm::SimArgs;
+using namespace idm::abi;
 
-namespace {
-
-struct Buf {
-    void *p = nullptr;
-    size_t n = 0;
-};
-
-enum Ctl { CTL_NSEG = 0, CTL_WORK_F = 1, CTL_WORK_B = 2, CTL_ITER = 3, CTL_N = 8 };
-
-}  // namespace
-
-struct idm_ctx {
-    int device = 0;
-    int n_sm = 1;
-    size_t cap = 0;
-    size_t held = 0;
-    char err[512] = {0};
-    int vpt_req = 0;
-    int G_req = 0;
-    int C = 8;
-    int wpb = 8;
-    Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t fit_exec = nullptr;
-    unsigned char fit_key[512] = {0};  // arguments the cached fit graph was captured with
-    size_t fit_key_len = 0;
-    int profiling = 0;
-    std::vector<cudaEvent_t> ev;       // per fit iteration: fwd begin/end, adjoint begin/end
-    int ev_used = 0;                   // iterations recorded by the cached graph
-};
-
-namespace {
+namespace idm {
+namespace abi {
 
 int fail(idm_ctx *c, int code, const char *fmt, ...)
 {
@@ -67,11 +39,7 @@ int cuda_fail(idm_ctx *c, cudaError_t e, const char *what)
     return fail(c, IDM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call)                                          \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
-    } while (0)
+#define CK(call) IDM_CK(call)
 
 int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
 {
@@ -132,7 +100,7 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
     return IDM_OK;
 }
 
-int check_scene(idm_ctx *c, const idm_scene_t *s)
+static int check_scene(idm_ctx *c, const idm_scene_t *s)
 {
     if (!s) return fail(c, IDM_ERR_ARG, "scene is NULL");
     if (s->n_lanes < 1) return fail(c, IDM_ERR_ARG, "n_lanes must be >= 1 (got %d)", s->n_lanes);
@@ -152,7 +120,7 @@ int check_params(idm_ctx *c, const idm_params_t *p, bool all)
     return IDM_OK;
 }
 
-int check_sim(idm_ctx *c, const idm_sim_t *s)
+static int check_sim(idm_ctx *c, const idm_sim_t *s)
 {
     if (!s) return fail(c, IDM_ERR_ARG, "sim is NULL");
     if (s->K < 1) return fail(c, IDM_ERR_ARG, "K must be >= 1 (got %d)", s->K);
@@ -161,17 +129,9 @@ int check_sim(idm_ctx *c, const idm_sim_t *s)
     return IDM_OK;
 }
 
-// Common preparation: buffers, initial gaps and warp segments.
-struct Prep {
-    int vpt = 1;
-    int G = 1;
-    int wpb_f = 1;  // warps per block of the forward (a multiple of G)
-    int grid_f = 1, grid_b = 1;
-    int wpb_b = 1;  // warps per block of the adjoint (bounded by its shared-memory tape)
-    SimArgs a;
-};
-
-int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const float *p_init, const float *v_init,
+// Common preparation of a single-scene call: buffers, initial gaps and warp
+// segments.
+static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const float *p_init, const float *v_init,
             const idm_sim_t *sim, bool need_ckpt, bool need_loss, int obs_stride, Prep *P, cudaStream_t st)
 {
     int rc;
@@ -219,6 +179,13 @@ int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, const flo
     CK(idm::launch_prep_gap(sc->lane_off, L, p_init, sc->length, N, (float *)c->g0.p, a.status, st));
     CK(idm::launch_build_segments(sc->lane_off, L, nullptr, 0, 32 * P->vpt * G, N, (Seg *)c->seg.p,
                                   (int *)c->ctl.p + CTL_NSEG, a.status, st));
+    P->loss_per_seg = G;
+    return forward_grid(c, P, L);
+}
+
+int forward_grid(idm_ctx *c, Prep *P, int L)
+{
+    const int G = P->G;
     P->wpb_f = std::max(G, (c->wpb / G) * G);
     const int warps_needed = L * G;  // segments <= lanes
     const int blocks_needed = (warps_needed + P->wpb_f - 1) / P->wpb_f;
@@ -245,6 +212,100 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     P->grid_b = std::min(blocks_needed, c->n_sm * occ_b);
     P->grid_b = P->grid_b < 1 ? 1 : P->grid_b;
     return IDM_OK;
+}
+
+int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
+                  float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
+                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t))
+{
+    int rc;
+    if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
+    if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
+
+    SimArgs &a = P.a;
+    a.adam_m = (float *)c->adam_m.p;
+    a.adam_v = (float *)c->adam_v.p;
+    a.n_iter = n_iter;
+    a.lr0 = lr0;
+    a.lr1 = lr1;
+    for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
+
+    // The graph depends on every launch argument; reuse it when they repeat.
+    struct Key {
+        SimArgs a;
+        int vpt, G, grid_f, grid_b, wpb, wpb_b, n_iter, profiling, loss_per_seg;
+        const double *hist;
+        unsigned char extra[64];
+    } key;
+    memset(&key, 0, sizeof key);
+    key.a = a;
+    key.vpt = P.vpt; key.G = P.G; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f;
+    key.wpb_b = P.wpb_b; key.n_iter = n_iter; key.profiling = c->profiling; key.loss_per_seg = P.loss_per_seg;
+    key.hist = loss_hist;
+    if (extra_len > sizeof key.extra) extra_len = sizeof key.extra;
+    if (extra_key) memcpy(key.extra, extra_key, extra_len);
+    static_assert(sizeof(Key) <= sizeof(((idm_ctx *)0)->fit_key), "fit key too large");
+    const bool cached = c->fit_exec && c->fit_key_len == sizeof key && memcmp(c->fit_key, &key, sizeof key) == 0;
+
+    if (!cached) {
+        while (c->profiling && (int)c->ev.size() < 4 * n_iter) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev.push_back(e);
+        }
+        // capture the whole fit (n_iter unrolled iterations) on the context's stream
+        cudaStream_t cs = c->cap_stream;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, cs);
+        for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+            a.iter = it;
+            e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) {
+                a.work = (int *)c->ctl.p + CTL_WORK_F;
+                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, P.wpb_f, cs);
+            }
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = finalize(c, P, it, loss_hist, cs);
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) {
+                a.work = (int *)c->ctl.p + CTL_WORK_B;
+                e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
+            }
+            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit"); }
+        if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+        if (c->fit_exec) {
+            CK(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(c->fit_exec);
+            c->fit_exec = nullptr;
+            c->fit_key_len = 0;
+        }
+        e = cudaGraphInstantiate(&c->fit_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        memcpy(c->fit_key, &key, sizeof key);
+        c->fit_key_len = sizeof key;
+        c->ev_used = c->profiling ? n_iter : 0;
+    }
+    CK(cudaGraphLaunch(c->fit_exec, st));
+    return IDM_OK;
+}
+
+}  // namespace abi
+}  // namespace idm
+
+namespace {
+
+// Loss of a single-scene fit iteration: fixed-order sum of the per-warp partials.
+cudaError_t single_finalize(idm_ctx *c, const Prep &P, int it, double *hist, cudaStream_t st)
+{
+    (void)c;
+    return idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.loss_per_seg, hist ? hist + it : nullptr, st);
 }
 
 }  // namespace
@@ -456,82 +517,9 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
     Prep P;
     if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, true, obs_stride, &P, st))) return rc;
     if ((rc = backward_grid(c, &P, false, true, false, scene->n_lanes))) return rc;
-    const size_t N = (size_t)scene->n_vehicles;
-    if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
-    if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
-
-    SimArgs a = P.a;
-    a.targets = targets;
-    a.adam_m = (float *)c->adam_m.p;
-    a.adam_v = (float *)c->adam_v.p;
-    a.n_iter = n_iter;
-    a.lr0 = lr0;
-    a.lr1 = lr1;
-    for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
-
-    // The graph depends on every launch argument; reuse it when they repeat.
-    struct Key {
-        SimArgs a;
-        int vpt, grid_f, grid_b, wpb, wpb_b, n_iter, profiling;
-        const double *hist;
-    } key;
-    memset(&key, 0, sizeof key);
-    key.a = a;
-    key.vpt = P.vpt; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f; key.wpb_b = P.wpb_b;
-    key.n_iter = n_iter; key.profiling = c->profiling; key.hist = loss_hist;
-    static_assert(sizeof(Key) <= sizeof(((idm_ctx *)0)->fit_key), "fit key too large");
-    const bool cached = c->fit_exec && c->fit_key_len == sizeof key && memcmp(c->fit_key, &key, sizeof key) == 0;
-
-    if (!cached) {
-        if (c->profiling && (int)c->ev.size() < 4 * n_iter) {
-            while ((int)c->ev.size() < 4 * n_iter) {
-                cudaEvent_t e;
-                CK(cudaEventCreate(&e));
-                c->ev.push_back(e);
-            }
-        }
-        // capture the whole fit (n_iter unrolled iterations) on the context's stream
-        cudaStream_t cs = c->cap_stream;
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, cs);
-        for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
-            a.iter = it;
-            e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
-            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
-            if (e == cudaSuccess) {
-                a.work = (int *)c->ctl.p + CTL_WORK_F;
-                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, P.wpb_f, cs);
-            }
-            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
-            if (e == cudaSuccess)
-                e = idm::launch_loss_finalize(a.loss_part, a.n_seg, P.G, loss_hist ? loss_hist + it : nullptr, cs);
-            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
-            if (e == cudaSuccess) {
-                a.work = (int *)c->ctl.p + CTL_WORK_B;
-                e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
-            }
-            if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
-        }
-        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit"); }
-        if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-        if (c->fit_exec) {
-            CK(cudaDeviceSynchronize());
-            cudaGraphExecDestroy(c->fit_exec);
-            c->fit_exec = nullptr;
-            c->fit_key_len = 0;
-        }
-        e = cudaGraphInstantiate(&c->fit_exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-        memcpy(c->fit_key, &key, sizeof key);
-        c->fit_key_len = sizeof key;
-        c->ev_used = c->profiling ? n_iter : 0;
-    }
-    CK(cudaGraphLaunch(c->fit_exec, st));
-    return IDM_OK;
+    P.a.targets = targets;
+    return run_fit_graph(c, P, n_iter, (size_t)scene->n_vehicles, box_lo, box_hi, lr0, lr1, loss_hist, nullptr, 0,
+                         st, single_finalize);
 }
 
 int idm_set_profiling(idm_ctx_t *c, int on)

@@ -1,0 +1,81 @@
+// Internal: the libidm context, its workspace and the launch planning shared
+// by the single-scene entry points (idm_abi.cu) and the batched ones
+// (idm_batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "../../include/idm.h"
+#include "idm_internal.h"
+
+namespace idm {
+namespace abi {
+
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+enum Ctl { CTL_NSEG = 0, CTL_WORK_F = 1, CTL_WORK_B = 2, CTL_ITER = 3, CTL_N = 8 };
+
+// Launch plan of one call.
+struct Prep {
+    int vpt = 1;
+    int G = 1;
+    int wpb_f = 1;  // warps per block of the forward (a multiple of G)
+    int grid_f = 1, grid_b = 1;
+    int wpb_b = 1;  // warps per block of the adjoint (bounded by its shared-memory tape)
+    int loss_per_seg = 1;
+    SimArgs a;
+};
+
+}  // namespace abi
+}  // namespace idm
+
+struct idm_ctx {
+    int device = 0;
+    int n_sm = 1;
+    size_t cap = 0;
+    size_t held = 0;
+    char err[512] = {0};
+    int vpt_req = 0;
+    int G_req = 0;
+    int C = 8;
+    int wpb = 8;
+    idm::abi::Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
+    idm::abi::Buf scen_tab, scen_seg_off, scen_seg_idx, lane_off_dev;  // batched scenarios
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t fit_exec = nullptr;
+    unsigned char fit_key[640] = {0};  // arguments the cached fit graph was captured with
+    size_t fit_key_len = 0;
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;       // per fit iteration: fwd begin/end, adjoint begin/end
+    int ev_used = 0;                   // iterations recorded by the cached graph
+};
+
+namespace idm {
+namespace abi {
+
+int fail(idm_ctx *c, int code, const char *fmt, ...);
+int cuda_fail(idm_ctx *c, cudaError_t e, const char *what);
+int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name);
+int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
+int check_params(idm_ctx *c, const idm_params_t *p, bool all);
+int forward_grid(idm_ctx *c, Prep *P, int L);
+int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L);
+// Capture (or reuse) the n_iter-iteration fit graph for plan P and launch it.
+// finalize(it, stream) enqueues the loss reduction of iteration it.
+int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
+                  float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
+                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t));
+
+}  // namespace abi
+}  // namespace idm
+
+#define IDM_CK(call)                                                     \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return idm::abi::cuda_fail(c, e_, #call); \
+    } while (0)

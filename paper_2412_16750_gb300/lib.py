@@ -40,6 +40,12 @@ class idm_sim_t(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("dt", ctypes.c_float), ("a_min", ctypes.c_float)]
 
 
+class idm_batch_t(ctypes.Structure):
+    _fields_ = [("n_scen", ctypes.c_int32), ("scen_lane_off", _vp), ("K", _vp), ("dt", _vp), ("obs_stride", _vp),
+                ("a_min", ctypes.c_float), ("n_lanes", ctypes.c_int32), ("n_vehicles", ctypes.c_int32),
+                ("lane_off_host", _vp), ("lane_off", _vp), ("length", _vp)]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
     "idm_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_size_t]),
@@ -64,6 +70,15 @@ _SIGS = {
     "idm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "idm_phase_times": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int32)]),
+    "idm_batch_sizes": (ctypes.c_int, [ctypes.POINTER(idm_batch_t), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "idm_batch_forward": (ctypes.c_int, [_vp, ctypes.POINTER(idm_batch_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                         _vp, _vp]),
+    "idm_batch_loss_grad": (ctypes.c_int, [_vp, ctypes.POINTER(idm_batch_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                           _vp, _vp, _vp, ctypes.POINTER(idm_params_t), _vp, _vp, _vp]),
+    "idm_batch_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_batch_t), ctypes.POINTER(idm_params_t), _vp, _vp, _vp,
+                                     ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_float), _vp, _vp, _vp]),
     "idm_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
                                ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -213,6 +228,36 @@ def idm_fit(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter
     return check(ctx, load().idm_fit(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
                                      ctypes.byref(sim), ptr(targets), obs_stride, n_iter, lr0, lr1, lo, hi,
                                      ptr(loss_hist), stream_ptr(stream)))
+
+
+def idm_batch_sizes(batch, ckpt_interval=8):
+    t, y, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = load().idm_batch_sizes(ctypes.byref(batch), ckpt_interval, ctypes.byref(t), ctypes.byref(y), ctypes.byref(c))
+    if rc != IDM_OK:
+        raise IdmError(rc, "idm_batch_sizes: bad batch description")
+    return t.value, y.value, c.value
+
+
+def idm_batch_forward(ctx, batch, params, p_init, v_init, traj, stream=None):
+    return check(ctx, load().idm_batch_forward(ctx, ctypes.byref(batch), ctypes.byref(params), ptr(p_init),
+                                               ptr(v_init), ptr(traj), stream_ptr(stream)))
+
+
+def idm_batch_loss_grad(ctx, batch, params, p_init, v_init, targets, scen_loss=None, loss_total=None, grad=None,
+                        grad_p_init=None, grad_v_init=None, stream=None):
+    return check(ctx, load().idm_batch_loss_grad(ctx, ctypes.byref(batch), ctypes.byref(params), ptr(p_init),
+                                                 ptr(v_init), ptr(targets), ptr(scen_loss), ptr(loss_total),
+                                                 ctypes.byref(grad) if grad is not None else None,
+                                                 ptr(grad_p_init), ptr(grad_v_init), stream_ptr(stream)))
+
+
+def idm_batch_fit(ctx, batch, params, p_init, v_init, targets, n_iter, lr0, lr1, box_lo, box_hi, loss_hist=None,
+                  scen_loss=None, stream=None):
+    lo = (ctypes.c_float * 5)(*box_lo)
+    hi = (ctypes.c_float * 5)(*box_hi)
+    return check(ctx, load().idm_batch_fit(ctx, ctypes.byref(batch), ctypes.byref(params), ptr(p_init), ptr(v_init),
+                                           ptr(targets), n_iter, lr0, lr1, lo, hi, ptr(loss_hist), ptr(scen_loss),
+                                           stream_ptr(stream)))
 
 
 # ---- struct builders ---------------------------------------------------------
