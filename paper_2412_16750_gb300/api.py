@@ -173,6 +173,74 @@ def gather(perm, srcs, ctx=None):
     return dsts
 
 
+class Batch:
+    """Uneven scenarios for the idm_batch_* calls.  Host arrays (numpy or
+    lists) describe the scenarios; the lane CSR and lengths are copied to the
+    device once."""
+
+    def __init__(self, scen_lane_off, K, dt, obs_stride, lane_off, length, a_min=-10.0):
+        import numpy as np
+        self.scen_lane_off = np.ascontiguousarray(scen_lane_off, dtype=np.int32)
+        self.K = np.ascontiguousarray(K, dtype=np.int32)
+        self.dt = np.ascontiguousarray(dt, dtype=np.float32)
+        self.obs_stride = np.ascontiguousarray(obs_stride, dtype=np.int32)
+        self.lane_off_host = np.ascontiguousarray(lane_off, dtype=np.int32)
+        self.lane_off = torch.as_tensor(self.lane_off_host, device="cuda")
+        self.length = _f32(torch.as_tensor(length))
+        self.a_min = a_min
+        self.n_scen = len(self.K)
+        self.veh_off = self.lane_off_host[self.scen_lane_off]
+        self.n_obs = self.K // self.obs_stride
+        nv = np.diff(self.veh_off)
+        self.traj_off = np.concatenate([[0], np.cumsum((self.K.astype(np.int64) + 1) * nv)])
+        self.tgt_off = np.concatenate([[0], np.cumsum(self.n_obs.astype(np.int64) * nv)])
+
+    def c(self):
+        return lib.idm_batch_t(self.n_scen, self.scen_lane_off.ctypes.data, self.K.ctypes.data, self.dt.ctypes.data,
+                               self.obs_stride.ctypes.data, self.a_min, len(self.lane_off_host) - 1,
+                               int(self.lane_off_host[-1]), self.lane_off_host.ctypes.data, self.lane_off.data_ptr(),
+                               self.length.data_ptr())
+
+    @property
+    def n_vehicles(self):
+        return int(self.lane_off_host[-1])
+
+
+def batch_forward(theta, p_init, v_init, batch, ctx=None):
+    """Concatenated per-scenario trajectories (flat float32 tensor)."""
+    ctx = ctx or default_context()
+    traj = torch.empty(int(batch.traj_off[-1]), device="cuda", dtype=torch.float32)
+    lib.idm_batch_forward(ctx.handle, batch.c(), lib.make_params(_f32(theta)), _f32(p_init), _f32(v_init), traj,
+                          _stream())
+    return traj
+
+
+def batch_loss_grad(theta, p_init, v_init, batch, targets, ctx=None):
+    """(per-scenario losses [S] float64, total, g_theta (6,N), g_p_init, g_v_init)."""
+    ctx = ctx or default_context()
+    N = batch.n_vehicles
+    sl = torch.zeros(batch.n_scen, device="cuda", dtype=torch.float64)
+    tot = torch.zeros((), device="cuda", dtype=torch.float64)
+    g = torch.empty((6, N), device="cuda", dtype=torch.float32)
+    gp = torch.empty(N, device="cuda", dtype=torch.float32)
+    gv = torch.empty(N, device="cuda", dtype=torch.float32)
+    lib.idm_batch_loss_grad(ctx.handle, batch.c(), lib.make_params(_f32(theta)), _f32(p_init), _f32(v_init),
+                            _f32(targets), sl, tot, lib.make_params(g), gp, gv, _stream())
+    return sl, tot, g, gp, gv
+
+
+def batch_fit(theta, p_init, v_init, batch, targets, n_iter, lr0=0.1, lr1=0.01, box_lo=(20.0, 0.1, 1.0, 0.5, 0.1),
+              box_hi=(60.0, 5.0, 10.0, 10.0, 5.0), ctx=None):
+    """In-place Adam fit over a batch; returns (loss history (n_iter,), per-scenario losses of the last iteration)."""
+    ctx = ctx or default_context()
+    assert theta.is_cuda and theta.dtype == torch.float32 and theta.is_contiguous()
+    hist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
+    sl = torch.zeros(batch.n_scen, device="cuda", dtype=torch.float64)
+    lib.idm_batch_fit(ctx.handle, batch.c(), lib.make_params(theta), _f32(p_init), _f32(v_init), _f32(targets), n_iter,
+                      lr0, lr1, box_lo, box_hi, hist, sl, _stream())
+    return hist[:n_iter], sl
+
+
 class IdmFunction(torch.autograd.Function):
     """Differentiable simulation: forward = idm_forward, backward = idm_backward."""
 

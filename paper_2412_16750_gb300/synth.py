@@ -129,6 +129,32 @@ def config2_tables(n_scen=4096, rng=None):
     return n_lanes, K, counts
 
 
+def make_batch(lanes_per_scen, counts_per_scen, K, obs_stride, rng, dt=0.1):
+    """Uneven scenarios laid out one after another: scenario s owns
+    lanes_per_scen[s] lanes with the vehicle counts counts_per_scen[s], its
+    own horizon K[s] and observation stride obs_stride[s]."""
+    counts = np.concatenate([np.asarray(c, dtype=np.int64) for c in counts_per_scen])
+    sc = make_scene(counts, rng)
+    scen_lane_off = lane_offsets(lanes_per_scen)
+    n_scen = len(lanes_per_scen)
+    sc.update(scen_lane_off=scen_lane_off, K=np.asarray(K, dtype=np.int32),
+              dt=np.full(n_scen, dt, dtype=np.float32), obs_stride=np.asarray(obs_stride, dtype=np.int32))
+    lo = sc["lane_off"]
+    sc["veh_off"] = lo[scen_lane_off]
+    return sc
+
+
+def config2(n_scen=4096):
+    """4,096 scenarios: lanes U[1,64], vehicles per lane U[2,200], horizons
+    U[50,500], dt 0.1 s, targets observed every 10th step."""
+    rng = rng_for(2)
+    n_lanes, K, counts = config2_tables(n_scen, rng)
+    sc = make_batch(n_lanes, counts, K, np.full(n_scen, 10), rng)
+    sc["name"] = "%d scenarios (%d lanes, %d vehicles), K U[50,500], obs every 10th step" % (
+        n_scen, int(sc["scen_lane_off"][-1]), int(sc["lane_off"][-1]))
+    return sc
+
+
 def unsorted_view(sc, rng):
     """The same vehicles in a random order, with lane ids, as a layout step
     would receive them."""
