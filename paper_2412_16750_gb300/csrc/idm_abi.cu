@@ -71,6 +71,19 @@ int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
 // Kernel shape: VPT vehicles per thread, G warps per segment (capacity
 // 32*VPT*G vehicles).  The default packs several 100-vehicle lanes into one
 // 512-slot segment (VPT 4, G 4).
+// The device status word accumulates across calls until idm_status reads
+// and clears it, so it must start at zero when first allocated.
+int ensure_status(idm_ctx *c)
+{
+    if (c->status.p) return IDM_OK;
+    int rc = ensure(c, c->status, sizeof(unsigned) * 4, "status");
+    if (rc) return rc;
+    cudaError_t e = cudaMemset(c->status.p, 0, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();  // before any stream of the caller uses it
+    if (e != cudaSuccess) return cuda_fail(c, e, "clearing the status word");
+    return IDM_OK;
+}
+
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
 {
     int v = c->vpt_req, g = c->G_req;
@@ -140,7 +153,7 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     const int G = P->G;
     if ((rc = ensure(c, c->seg, sizeof(Seg) * (size_t)L, "segments"))) return rc;
     if ((rc = ensure(c, c->ctl, sizeof(int) * CTL_N, "control"))) return rc;
-    if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
+    if ((rc = ensure_status(c))) return rc;
     if ((rc = ensure(c, c->g0, sizeof(float) * (size_t)N, "initial gaps"))) return rc;
     if ((rc = ensure(c, c->loss_part, sizeof(double) * (size_t)L * G, "loss partials"))) return rc;
     if ((rc = ensure(c, c->loss_tmp, sizeof(double) * 2, "loss scalar"))) return rc;
@@ -399,7 +412,7 @@ int idm_layout(idm_ctx_t *c, int32_t N, int32_t n_lanes, const int32_t *lane_id,
     if (N > 0 && (!lane_id || !pos || !perm)) return fail(c, IDM_ERR_ARG, "lane_id, pos and perm are required");
     if (!lane_off) return fail(c, IDM_ERR_ARG, "lane_off is required");
     int rc;
-    if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
+    if ((rc = ensure_status(c))) return rc;
     if ((rc = ensure(c, c->lay_counts, sizeof(int) * (size_t)n_lanes, "layout counts"))) return rc;
     if ((rc = ensure(c, c->lay_cursor, sizeof(int) * (size_t)n_lanes, "layout cursor"))) return rc;
     cudaStream_t st = (cudaStream_t)stream;

@@ -147,7 +147,7 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
     const size_t n_seg = BP.seg.size();
     if ((rc = ensure(c, c->seg, sizeof(Seg) * std::max<size_t>(n_seg, 1), "segments"))) return rc;
     if ((rc = ensure(c, c->ctl, sizeof(int) * CTL_N, "control"))) return rc;
-    if ((rc = ensure(c, c->status, sizeof(unsigned) * 4, "status"))) return rc;
+    if ((rc = ensure_status(c))) return rc;
     if ((rc = ensure(c, c->g0, sizeof(float) * (size_t)N, "initial gaps"))) return rc;
     if ((rc = ensure(c, c->loss_part, sizeof(double) * std::max<size_t>(n_seg, 1) * G, "loss partials"))) return rc;
     if ((rc = ensure(c, c->loss_tmp, sizeof(double) * 2, "loss scalar"))) return rc;

@@ -61,6 +61,7 @@ namespace abi {
 int fail(idm_ctx *c, int code, const char *fmt, ...);
 int cuda_fail(idm_ctx *c, cudaError_t e, const char *what);
 int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name);
+int ensure_status(idm_ctx *c);
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
 int check_params(idm_ctx *c, const idm_params_t *p, bool all);
 int forward_grid(idm_ctx *c, Prep *P, int L);
