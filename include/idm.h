@@ -265,6 +265,38 @@ int idm_batch_fit(idm_ctx_t *ctx, const idm_batch_t *batch, idm_params_t *params
                   const float *v_init, const float *targets, int32_t n_iter, float lr0, float lr1,
                   const float *box_lo, const float *box_hi, double *loss_hist, double *scen_loss, void *stream);
 
+/* ---- loss and gradient without allocation ------------------------------ */
+
+/* Size of the library's built-in device scratch array (16 MiB). */
+#define IDM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* idm_loss_grad for callers that cannot allocate device memory: code whose
+ * memory is owned by a custom allocator or a fixed budget, or that runs
+ * where cudaMalloc is not allowed (for instance between the begin and end of
+ * a stream capture).  The paper has no counterpart; this is a deployment
+ * convenience.  No context is needed and nothing is allocated: the scratch
+ * (segments, counters, status, initial gaps, loss partials, checkpoints)
+ * lives in one IDM_NOALLOC_SCRATCH_BYTES static device array that every GPU
+ * loading the library holds until the process exits.
+ *   Arguments and results are those of idm_loss_grad; the kernel shape is
+ *   the default (checkpoint interval 8).
+ *   status_out (device uint32, may be NULL): receives the device status word
+ *   (IDM_STATUS_* bits) of this call, since there is no context to query.
+ * Limit: the scratch must hold about 16*n_lanes + 4*N + 64*n_lanes +
+ * 16*N*ceil(K/8) bytes (plus 256-byte alignment of each piece), i.e. about
+ * N * ceil(K/8) <= 1,000,000 vehicle-checkpoints; larger problems return
+ * IDM_ERR_WORKSPACE before anything is launched.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and overwrites it: calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Returns IDM_OK, IDM_ERR_ARG, IDM_ERR_WORKSPACE
+ * or IDM_ERR_CUDA (no message string is kept). */
+int idm_loss_grad_noalloc(const idm_scene_t *scene, const idm_params_t *params, const float *p_init,
+                          const float *v_init, const idm_sim_t *sim, const float *targets, int32_t obs_stride,
+                          double *loss_out, idm_params_t *grad, float *grad_p_init, float *grad_v_init,
+                          uint32_t *status_out, void *stream);
+
 /* ---- measurement ------------------------------------------------------ */
 
 /* When on, idm_fit records CUDA events around every forward and adjoint

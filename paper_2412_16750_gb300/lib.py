@@ -79,6 +79,9 @@ _SIGS = {
     "idm_batch_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_batch_t), ctypes.POINTER(idm_params_t), _vp, _vp, _vp,
                                      ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float), _vp, _vp, _vp]),
+    "idm_loss_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                             ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, _vp,
+                                             ctypes.POINTER(idm_params_t), _vp, _vp, _vp, _vp]),
     "idm_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
                                ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -219,6 +222,15 @@ def idm_loss_grad(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, 
                                            ptr(v_init), ctypes.byref(sim), ptr(targets), obs_stride,
                                            ptr(loss_out), ctypes.byref(grad) if grad is not None else None,
                                            ptr(grad_p_init), ptr(grad_v_init), stream_ptr(stream)))
+
+
+def idm_loss_grad_noalloc(scene, params, p_init, v_init, sim, targets, obs_stride, loss_out=None, grad=None,
+                          grad_p_init=None, grad_v_init=None, status_out=None, stream=None):
+    """Returns the raw status code (there is no context to hold a message)."""
+    return load().idm_loss_grad_noalloc(ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
+                                        ctypes.byref(sim), ptr(targets), obs_stride, ptr(loss_out),
+                                        ctypes.byref(grad) if grad is not None else None, ptr(grad_p_init),
+                                        ptr(grad_v_init), ptr(status_out), stream_ptr(stream))
 
 
 def idm_fit(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi,
