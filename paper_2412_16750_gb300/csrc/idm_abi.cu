@@ -278,16 +278,16 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_F;
-                e = idm::launch_forward(P.vpt, false, false, true, true, a, P.grid_f, P.wpb_f, cs);
+                e = idm::launch_forward(P.vpt, false, false, true, a, P.grid_f, P.wpb_f, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
-            if (e == cudaSuccess) e = finalize(c, P, it, loss_hist, cs);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_B;
                 e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = finalize(c, P, it, loss_hist, cs);  // loss of the parameters before update it
         }
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit"); }
@@ -446,7 +446,7 @@ int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *para
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
     P.a.vtraj = vtraj;
-    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, false, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }
 
@@ -464,7 +464,7 @@ int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *par
     if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, false, 1, &P, st))) return rc;
     if ((rc = backward_grid(c, &P, true, false, grad && grad->delta, scene->n_lanes))) return rc;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, false, true, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     P.a.gP = gP;
     P.a.gV = gV;
@@ -496,8 +496,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     if ((rc = backward_grid(c, &P, false, false, want_delta, scene->n_lanes))) return rc;
     P.a.targets = targets;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, true, true, P.a, P.grid_f, P.wpb_f, st));
-    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.G, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
+    CK(idm::launch_forward(P.vpt, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     if (grad) {
         P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
@@ -506,6 +505,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     P.a.g_p_init = grad_p_init;
     P.a.g_v_init = grad_v_init;
     CK(idm::launch_backward(P.vpt, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
+    CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.G, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
     return IDM_OK;
 }
 

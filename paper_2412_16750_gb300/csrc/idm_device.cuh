@@ -180,73 +180,71 @@ __device__ __forceinline__ void follower_vals(const float (&x)[VPT], float (&out
 
 namespace idm {
 
-// Terms of one reverse step for one vehicle (the adjoint of accel_star and
-// euler).  mu = dt * (adjoint of the vehicle's step-(k+1) speed).  With
-// sigma2 = d a* / d a, sigma1 = d s* / d s_opt, S = d a / d s*,
-// G = d a / d gap and W = mu sigma2 S sigma1:
-//   own_p  = mu d a*/d p          = -mu sigma2 G
-//   own_v  = mu d a*/d v          (own speed, incl. the a_lb branch)
-//   lead_p = mu d a*/d p_leader   = +mu sigma2 G       (sent to the leader)
-//   lead_v = mu d a*/d v_leader   = W (-c v)           (sent to the leader)
-// and the parameter-gradient increments, factored so that per-vehicle
-// constants multiply once at the end:
-//   w = W, w_v = W v, w_vdv = W v dv, f_a = mu sigma2 (1 - r^delta - z^2),
-//   f_rd = mu sigma2 r^delta, f_rdlnr = mu sigma2 r^delta ln r.
-struct AdjTerms {
-    float own_p, own_v, lead_p, lead_v;
-    float w, w_v, w_vdv, f_a, f_rd, f_rdlnr;
+// Coefficients of one reverse step for one vehicle (the adjoint of
+// accel_star and euler), independent of the incoming adjoint.  With
+// sigma2 = d a*/d a, sigma1 = d s*/d s_opt, S = d a/d s*, G = d a/d gap:
+//   Ap  = d a*/d p         = -sigma2 G     (the leader's d a*/d p_h is -Ap)
+//   Av  = d a*/d v         (own speed, incl. the a_lb branch)
+//   Avh = d a*/d v_leader  = w0 (-c v),  w0 = sigma2 S sigma1
+// and the parameter-gradient factors (per-vehicle constants multiply the
+// sums once at the end): w0, w0 v, w0 v dv, sigma2 (1 - r^delta - z^2),
+// sigma2 r^delta, sigma2 r^delta ln r.  The reverse step multiplies all of
+// them by mu = dt * (adjoint of the step-(k+1) speed), so this part can be
+// evaluated ahead of the dependent adjoint chain.
+struct AdjJac {
+    float Ap, Av, Avh;
+    float w0, w0v, w0vdv, fa, frd, frdl;
 };
 
 template <bool WANT_DELTA, bool D4>
-__device__ __forceinline__ AdjTerms adjoint_terms(float mu, float v, float gap_raw, float vh,
-                                                  const VehConst &k, float inv_dt, float a_min)
+__device__ __forceinline__ AdjJac adjoint_jac(float v, float gap_raw, float vh, const VehConst &k, float inv_dt,
+                                              float a_min)
 {
-    AdjTerms t;
+    AdjJac J;
     const bool floored = gap_raw < IDM_GAP_FLOOR;
-    float gap = floored ? IDM_GAP_FLOOR : gap_raw;
-    float dv = __fsub_rn(v, vh);
-    float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);
-    Soft s1 = softplus(s_opt);
-    float sig1 = sigmoid_from(s_opt, s1.e);
-    float inv_gap = rcp_approx(gap);
-    float z = __fmul_rn(s1.sp, inv_gap);
-    float r = __fmul_rn(v, k.inv_v0);
+    const float gap = floored ? IDM_GAP_FLOOR : gap_raw;
+    const float dv = __fsub_rn(v, vh);
+    const float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);
+    const Soft s1 = softplus(s_opt);
+    const float sig1 = sigmoid_from(s_opt, s1.e);
+    const float inv_gap = rcp_approx(gap);
+    const float z = __fmul_rn(s1.sp, inv_gap);
+    const float r = __fmul_rn(v, k.inv_v0);
     float rd, rdm1;
     if (D4) {
-        float r2 = __fmul_rn(r, r);
+        const float r2 = __fmul_rn(r, r);
         rd = __fmul_rn(r2, r2);
         rdm1 = __fmul_rn(r2, r);
     } else {
         rd = r > 0.0f ? __powf(r, k.delta) : 0.0f;
         rdm1 = r > 0.0f ? __powf(r, k.delta - 1.0f) : (k.delta > 1.0f ? 0.0f : (k.delta == 1.0f ? 1.0f : INFINITY));
     }
-    float free_and_int = __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z));
-    float a = __fmul_rn(k.am, free_and_int);
-    float lbv = -__fmul_rn(v, inv_dt);
+    const float free_and_int = __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z));
+    const float a = __fmul_rn(k.am, free_and_int);
+    const float lbv = -__fmul_rn(v, inv_dt);
     const bool beta = lbv > a_min;
-    float a_lb = beta ? lbv : a_min;
-    float x2 = __fsub_rn(a, a_lb);
-    float e2 = __expf(-fabsf(x2));
-    float d2 = rcp_approx(__fadd_rn(1.0f, e2));
-    float sig2 = x2 >= 0.0f ? d2 : __fmul_rn(e2, d2);       // sigma(x2)
-    float one_m_sig2 = x2 >= 0.0f ? __fmul_rn(e2, d2) : d2; // sigma(-x2)
+    const float a_lb = beta ? lbv : a_min;
+    const float x2 = __fsub_rn(a, a_lb);
+    const float e2 = __expf(-fabsf(x2));
+    const float d2 = rcp_approx(__fadd_rn(1.0f, e2));
+    const float ed2 = __fmul_rn(e2, d2);
+    const float sig2 = x2 >= 0.0f ? d2 : ed2;        // sigma(x2)
+    const float one_m_sig2 = x2 >= 0.0f ? ed2 : d2;  // sigma(-x2)
 
-    float S = -2.0f * k.am * z * inv_gap;     // d a / d s*
-    float G = floored ? 0.0f : -S * z;        // d a / d gap = 2 a_max z^2 / gap
-    float ms2 = mu * sig2;
-    float W = ms2 * S * sig1;
-    t.own_p = -ms2 * G;
-    t.lead_p = ms2 * G;
-    t.lead_v = -W * k.c * v;
-    float dfree_dv = -k.am * k.delta * rdm1 * k.inv_v0;
-    t.own_v = ms2 * dfree_dv + W * (k.T + k.c * (v + dv)) - (beta ? mu * one_m_sig2 * inv_dt : 0.0f);
-    t.w = W;
-    t.w_v = W * v;
-    t.w_vdv = W * v * dv;
-    t.f_a = ms2 * free_and_int;
-    t.f_rd = ms2 * rd;
-    t.f_rdlnr = (WANT_DELTA && rd > 0.0f) ? ms2 * rd * __logf(r) : 0.0f;
-    return t;
+    const float S = -2.0f * k.am * z * inv_gap;  // d a / d s*
+    const float G = floored ? 0.0f : -S * z;     // d a / d gap = 2 a_max z^2 / gap
+    const float w0 = sig2 * S * sig1;
+    const float dfree_dv = -k.am * (D4 ? 4.0f : k.delta) * rdm1 * k.inv_v0;
+    J.Ap = -sig2 * G;
+    J.Av = sig2 * dfree_dv + w0 * (k.T + k.c * (v + dv)) - (beta ? one_m_sig2 * inv_dt : 0.0f);
+    J.Avh = -w0 * k.c * v;
+    J.w0 = w0;
+    J.w0v = w0 * v;
+    J.w0vdv = J.w0v * dv;
+    J.fa = sig2 * free_and_int;
+    J.frd = sig2 * rd;
+    J.frdl = (WANT_DELTA && rd > 0.0f) ? J.frd * __logf(r) : 0.0f;
+    return J;
 }
 
 }  // namespace idm

@@ -65,8 +65,8 @@ cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_ini
                             int N, float *g0, unsigned *status, cudaStream_t st);
 cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *scen_lane_off, int n_scen,
                                   int cap, int N, Seg *seg, int *n_seg, unsigned *status, cudaStream_t st);
-cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt, const SimArgs &a,
-                           int grid, int wpb, cudaStream_t st);
+cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
+                           cudaStream_t st);
 cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
 size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb);

@@ -175,11 +175,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Observed-target rows are prefetched FWD_PD rows ahead into a ring of
-// FWD_RING rows per warp; the slot written is never the one just read.
-constexpr int FWD_RING = 4;
-constexpr int FWD_PD = 3;
-
 // dst/src_row already point at this warp's first slot.
 template <int VPT>
 __device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, int lane, const bool (&valid)[VPT])
@@ -310,34 +305,24 @@ __device__ __forceinline__ bool segment_is_d4(const VehConst (&kc)[VPT], const b
 }
 
 // ---------------------------------------------------------------------------
-// Forward: K steps per segment, optional trajectory / speed output, fused
-// squared-error loss, checkpoints every C steps.
+// Forward: K steps per segment, optional trajectory / speed output,
+// checkpoints every C steps.  (The squared-error loss is accumulated by the
+// adjoint's recompute, which evaluates the residuals anyway.)
 // ---------------------------------------------------------------------------
 struct FwdFlags {
-    bool traj, vtraj, loss, ckpt;
+    bool traj, vtraj, ckpt;
 };
 
 template <int VPT, bool D4>
-__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
+__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int lb, Grp &g,
                                                 const VehConst (&kc)[VPT], State (&st)[VPT], const float (&pin)[VPT],
-                                                const bool (&valid)[VPT], FwdFlags f, float *ring)
+                                                const bool (&valid)[VPT], FwdFlags f)
 {
-    constexpr int SL = 32 * VPT;
     const int lane = g.lane;
     const int Ns = sc.n_veh;
-    const int wl = lb + g.w * SL;  // scenario-local index of this warp's first slot
-    float lsum = 0.0f, lcomp = 0.0f;
-    int next_obs = sc.obs_stride, obs_row = 0;
+    const int wl = lb + g.w * 32 * VPT;  // scenario-local index of this warp's first slot
     int next_ck = 0, ck_idx = 0;
     int xp = 0;
-    const float *ybase = a.targets + sc.tgt_off + wl;
-    if (f.loss) {
-#pragma unroll
-        for (int r = 0; r < FWD_PD; ++r) {
-            if (r < sc.n_obs) prefetch_row<VPT>(ring + r * SL, ybase + (size_t)r * Ns, lane, valid);
-            cp_async_commit();
-        }
-    }
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
             float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
@@ -363,21 +348,6 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
                 if (f.vtraj) a.vtraj[row + q] = st[j].v;
             }
         }
-        if (f.loss && k == next_obs && obs_row < sc.n_obs) {
-            cp_async_wait<FWD_PD - 1>();
-            const float *y = ring + (obs_row % FWD_RING) * SL;
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                if (!valid[j]) continue;
-                float r = residual(pin[j], st[j], y[lane + 32 * j]);
-                kahan_add(lsum, lcomp, __fmul_rn(r, r));
-            }
-            const int nr = obs_row + FWD_PD;
-            if (nr < sc.n_obs) prefetch_row<VPT>(ring + (nr % FWD_RING) * SL, ybase + (size_t)nr * Ns, lane, valid);
-            cp_async_commit();
-            next_obs += sc.obs_stride;
-            ++obs_row;
-        }
         if (k == sc.K) break;
 
         float vcur[VPT], vh[VPT];
@@ -391,16 +361,11 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             euler(st[j], as, vh[j], sc.dt);
         }
     }
-    if (f.loss) cp_async_wait<0>();
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < VPT; ++j)
         if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].xh))) bad = true;
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
-    if (f.loss) {
-        double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
-        if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
-    }
 }
 
 template <int VPT>
@@ -410,8 +375,7 @@ forward_kernel(SimArgs a, FwdFlags f)
     extern __shared__ float fsmem[];
     const int G = a.G;
     const int warp = threadIdx.x >> 5;
-    float *ring = fsmem + warp * FWD_RING * 32 * VPT;
-    float *ctrl = fsmem + (blockDim.x >> 5) * FWD_RING * 32 * VPT + (warp / G) * grp_ctrl_floats(G);
+    float *ctrl = fsmem + (warp / G) * grp_ctrl_floats(G);
     Grp g = make_grp(G, ctrl);
     int par = 0;
     for (;;) {
@@ -426,9 +390,9 @@ forward_kernel(SimArgs a, FwdFlags f)
         bool valid[VPT];
         load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            forward_segment<VPT, true>(a, sc, s_idx, lb, g, kc, st, pin, valid, f, ring);
+            forward_segment<VPT, true>(a, sc, lb, g, kc, st, pin, valid, f);
         else
-            forward_segment<VPT, false>(a, sc, s_idx, lb, g, kc, st, pin, valid, f, ring);
+            forward_segment<VPT, false>(a, sc, lb, g, kc, st, pin, valid, f);
     }
 }
 
@@ -452,8 +416,8 @@ __host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, in
 }
 
 template <int VPT, bool DENSE, bool ADAM, bool WD, bool D4>
-__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int lb, Grp &g,
-                                                 float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
+__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
+                                                 Grp &g, float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
                                                  const float (&pin)[VPT], const bool (&valid)[VPT])
 {
     constexpr int SL = 32 * VPT;
@@ -468,6 +432,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     const float dt = sc.dt;
     const float seed_scale = 2.0f * sc.inv_nobs;
     int xp = 0, fp = 0;
+    float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE), Kahan
 
     float lp[VPT], lv[VPT];
 #pragma unroll
@@ -517,6 +482,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     for (int j = 0; j < VPT; ++j) {
                         float r = valid[j] ? residual(pin[j], st[j], rr[lane + 32 * j]) : 0.0f;
                         rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
+                        kahan_add(lsum, lcomp, __fmul_rn(r, r));
                     }
                 }
                 obs_k += sc.obs_stride;
@@ -548,7 +514,11 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j)
-                        if (valid[j]) lp[j] = __fmul_rn(seed_scale, residual(pin[j], st[j], __ldg(y + lane + 32 * j)));
+                        if (valid[j]) {
+                            const float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
+                            lp[j] = __fmul_rn(seed_scale, r);
+                            kahan_add(lsum, lcomp, __fmul_rn(r, r));
+                        }
                 }
             }
         }
@@ -562,28 +532,39 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 
         // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
         int obs_hi = ((c0 + n - 1) / sc.obs_stride) * sc.obs_stride;
+        // The step-k coefficients do not depend on the adjoint, so those of
+        // step k-1 are evaluated while the dependent chain of step k runs.
+        AdjJac J[VPT];
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const int q = wb + lane + 32 * j;
+            const float *rv = tv + (n - 1) * SLG, *rg = tg + (n - 1) * SLG;
+            J[j] = adjoint_jac<WD, D4>(rv[q], rg[q], q > 0 ? rv[q - 1] : 0.0f, kc[j], sc.inv_dt, sc.a_min);
+        }
         for (int s = n - 1; s >= 0; --s) {
             const int k = c0 + s;
-            const float *rv = tv + s * SLG, *rg = tg + s * SLG;
             float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
-                const int q = wb + lane + 32 * j;
-                const float v = rv[q];
-                const float gap = rg[q];
-                const float vh = q > 0 ? rv[q - 1] : 0.0f;
                 const float mu = __fmul_rn(dt, lv[j]);
-                AdjTerms t = adjoint_terms<WD, D4>(mu, v, gap, vh, kc[j], sc.inv_dt, sc.a_min);
-                own_p[j] = t.own_p;
-                own_v[j] = t.own_v;
-                to_lp[j] = t.lead_p;
-                to_lv[j] = t.lead_v;
-                sacc[0][j] += t.w;
-                sacc[1][j] += t.w_v;
-                sacc[2][j] += t.w_vdv;
-                sacc[3][j] += t.f_a;
-                sacc[4][j] += t.f_rd;
-                if (WD) sacc[5][j] += t.f_rdlnr;
+                own_p[j] = mu * J[j].Ap;
+                own_v[j] = mu * J[j].Av;
+                to_lp[j] = -own_p[j];
+                to_lv[j] = mu * J[j].Avh;
+                sacc[0][j] += mu * J[j].w0;
+                sacc[1][j] += mu * J[j].w0v;
+                sacc[2][j] += mu * J[j].w0vdv;
+                sacc[3][j] += mu * J[j].fa;
+                sacc[4][j] += mu * J[j].frd;
+                if (WD) sacc[5][j] += mu * J[j].frdl;
+            }
+            if (s > 0) {
+                const float *rv = tv + (s - 1) * SLG, *rg = tg + (s - 1) * SLG;
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    const int q = wb + lane + 32 * j;
+                    J[j] = adjoint_jac<WD, D4>(rv[q], rg[q], q > 0 ? rv[q - 1] : 0.0f, kc[j], sc.inv_dt, sc.a_min);
+                }
             }
             float in_p, in_v;
             grp_follow_in(g, to_lp[0], to_lv[0], in_p, in_v, fp);
@@ -673,6 +654,10 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (!DENSE) {
+        const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
+    }
 }
 
 template <int VPT, bool DENSE, bool ADAM, bool WD>
@@ -698,9 +683,9 @@ backward_kernel(SimArgs a)
         bool valid[VPT];
         load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, lb, g, gbase, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, pin, valid);
         else
-            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, lb, g, gbase, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, pin, valid);
     }
 }
 
@@ -732,10 +717,10 @@ cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int 
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
-cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool loss, bool ckpt, const SimArgs &a, int grid,
-                           int wpb, cudaStream_t st)
+cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
+                           cudaStream_t st)
 {
-    FwdFlags f{traj, vtraj, loss, ckpt};
+    FwdFlags f{traj, vtraj, ckpt};
     void *fn = nullptr;
     switch (vpt) {
     case 1: fn = (void *)forward_kernel<1>; break;
@@ -759,7 +744,8 @@ size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb)
 
 size_t forward_smem_bytes(int vpt, int G, int wpb)
 {
-    return ((size_t)FWD_RING * 32 * vpt * wpb + (size_t)grp_ctrl_floats(G) * (wpb / G)) * sizeof(float);
+    (void)vpt;
+    return (size_t)grp_ctrl_floats(G) * (wpb / G) * sizeof(float);
 }
 
 // Kernel variants of the adjoint: seeds from dense gradients or from targets,
