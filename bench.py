@@ -58,9 +58,9 @@ def parse():
     p.add_argument("--iters", type=int, default=100, help="Adam iterations per step")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--vpt", type=int, default=4)
-    p.add_argument("--G", type=int, default=4, help="warps per segment")
-    p.add_argument("--ckpt", type=int, default=6)
+    p.add_argument("--vpt", type=int, default=2)
+    p.add_argument("--G", type=int, default=8, help="warps per segment")
+    p.add_argument("--ckpt", type=int, default=8)
     p.add_argument("--wpb", type=int, default=8)
     return p.parse_args()
 

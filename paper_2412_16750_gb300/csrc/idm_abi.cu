@@ -88,9 +88,8 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
 {
     int v = c->vpt_req, g = c->G_req;
     if (v == 0 && g == 0) {
-        v = 4;
-        g = 4;
-        while (32 * v * g < max_lane && g < 8) g <<= 1;
+        v = 2;
+        g = 8;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
         // shrink the segment while the adjoint tape would not fit shared memory
         while (idm::backward_smem_bytes(v, false, c->C, g, g) > 227 * 1024) {
@@ -196,13 +195,28 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     return forward_grid(c, P, L);
 }
 
+void forward_shape(int vpt, int G, int *vpt_f, int *G_f)
+{
+    // the forward carries fewer live values per vehicle, so it prefers 4
+    // vehicles per thread for the same segment capacity
+    const int cap = 32 * vpt * G;
+    if (cap % 128 == 0 && cap / 128 >= 1 && cap / 128 <= 8) {
+        *vpt_f = 4;
+        *G_f = cap / 128;
+    } else {
+        *vpt_f = vpt;
+        *G_f = G;
+    }
+}
+
 int forward_grid(idm_ctx *c, Prep *P, int L)
 {
-    const int G = P->G;
+    forward_shape(P->vpt, P->G, &P->vpt_f, &P->G_f);
+    const int G = P->G_f;
     P->wpb_f = std::max(G, (c->wpb / G) * G);
     const int warps_needed = L * G;  // segments <= lanes
     const int blocks_needed = (warps_needed + P->wpb_f - 1) / P->wpb_f;
-    int occ_f = idm::occupancy_blocks(P->vpt, G, false, false, false, false, P->wpb_f, 0);
+    int occ_f = idm::occupancy_blocks(P->vpt_f, G, false, false, false, false, P->wpb_f, 0);
     P->grid_f = std::min(blocks_needed, c->n_sm * occ_f);
     P->grid_f = P->grid_f < 1 ? 1 : P->grid_f;
     return IDM_OK;
@@ -252,7 +266,7 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     } key;
     memset(&key, 0, sizeof key);
     key.a = a;
-    key.vpt = P.vpt; key.G = P.G; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f;
+    key.vpt = P.vpt * 16 + P.vpt_f; key.G = P.G * 16 + P.G_f; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f;
     key.wpb_b = P.wpb_b; key.n_iter = n_iter; key.profiling = c->profiling; key.loss_per_seg = P.loss_per_seg;
     key.hist = loss_hist;
     if (extra_len > sizeof key.extra) extra_len = sizeof key.extra;
@@ -278,13 +292,13 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_F;
-                e = idm::launch_forward(P.vpt, false, false, true, a, P.grid_f, P.wpb_f, cs);
+                e = idm::launch_forward(P.vpt_f, P.G_f, false, false, true, a, P.grid_f, P.wpb_f, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
                 a.work = (int *)c->ctl.p + CTL_WORK_B;
-                e = idm::launch_backward(P.vpt, false, true, false, a, P.grid_b, P.wpb_b, cs);
+                e = idm::launch_backward(P.vpt, P.G, false, true, false, a, P.grid_b, P.wpb_b, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) e = finalize(c, P, it, loss_hist, cs);  // loss of the parameters before update it
@@ -446,7 +460,7 @@ int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *para
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
     P.a.vtraj = vtraj;
-    CK(idm::launch_forward(P.vpt, traj != nullptr, vtraj != nullptr, false, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt_f, P.G_f, traj != nullptr, vtraj != nullptr, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }
 
@@ -464,7 +478,7 @@ int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *par
     if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, false, 1, &P, st))) return rc;
     if ((rc = backward_grid(c, &P, true, false, grad && grad->delta, scene->n_lanes))) return rc;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, true, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt_f, P.G_f, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     P.a.gP = gP;
     P.a.gV = gV;
@@ -474,7 +488,7 @@ int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *par
     }
     P.a.g_p_init = grad_p_init;
     P.a.g_v_init = grad_v_init;
-    CK(idm::launch_backward(P.vpt, true, false, grad && grad->delta, P.a, P.grid_b, P.wpb_b, st));
+    CK(idm::launch_backward(P.vpt, P.G, true, false, grad && grad->delta, P.a, P.grid_b, P.wpb_b, st));
     return IDM_OK;
 }
 
@@ -496,7 +510,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     if ((rc = backward_grid(c, &P, false, false, want_delta, scene->n_lanes))) return rc;
     P.a.targets = targets;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, true, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt_f, P.G_f, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     if (grad) {
         P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
@@ -504,7 +518,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
     }
     P.a.g_p_init = grad_p_init;
     P.a.g_v_init = grad_v_init;
-    CK(idm::launch_backward(P.vpt, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
+    CK(idm::launch_backward(P.vpt, P.G, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
     CK(idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.G, loss_out ? loss_out : (double *)c->loss_tmp.p, st));
     return IDM_OK;
 }

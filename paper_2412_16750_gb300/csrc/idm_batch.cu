@@ -263,7 +263,7 @@ int idm_batch_forward(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *pa
     if ((rc = prepare_batch(c, b, params, p_init, v_init, false, &P, BP, st))) return rc;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
-    CK(idm::launch_forward(P.vpt, true, false, false, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt_f, P.G_f, true, false, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }
 
@@ -284,7 +284,7 @@ int idm_batch_loss_grad(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *
     if ((rc = backward_grid(c, &P, false, false, want_delta, (int)std::max<size_t>(BP.seg.size(), 1)))) return rc;
     P.a.targets = targets;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
-    CK(idm::launch_forward(P.vpt, false, false, true, P.a, P.grid_f, P.wpb_f, st));
+    CK(idm::launch_forward(P.vpt_f, P.G_f, false, false, true, P.a, P.grid_f, P.wpb_f, st));
     P.a.work = (int *)c->ctl.p + CTL_WORK_B;
     if (grad) {
         P.a.g_v0 = grad->v0; P.a.g_T = grad->T; P.a.g_s0 = grad->s0;
@@ -292,7 +292,7 @@ int idm_batch_loss_grad(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *
     }
     P.a.g_p_init = grad_p_init;
     P.a.g_v_init = grad_v_init;
-    CK(idm::launch_backward(P.vpt, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
+    CK(idm::launch_backward(P.vpt, P.G, false, false, want_delta, P.a, P.grid_b, P.wpb_b, st));
     g_bfin = BatchFinalize{b->n_scen, scen_loss};
     CK(batch_finalize(c, P, 0, loss_total, st));
     return IDM_OK;

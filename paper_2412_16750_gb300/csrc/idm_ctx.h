@@ -22,9 +22,11 @@ enum Ctl { CTL_NSEG = 0, CTL_WORK_F = 1, CTL_WORK_B = 2, CTL_ITER = 3, CTL_N = 8
 
 // Launch plan of one call.
 struct Prep {
-    int vpt = 1;
-    int G = 1;
-    int wpb_f = 1;  // warps per block of the forward (a multiple of G)
+    int vpt = 1;    // adjoint shape: vehicles per thread
+    int G = 1;      //               warps per segment
+    int vpt_f = 1;  // forward shape (same segment capacity 32 * vpt * G)
+    int G_f = 1;
+    int wpb_f = 1;  // warps per block of the forward (a multiple of G_f)
     int grid_f = 1, grid_b = 1;
     int wpb_b = 1;  // warps per block of the adjoint (bounded by its shared-memory tape)
     int loss_per_seg = 1;
@@ -63,6 +65,8 @@ int cuda_fail(idm_ctx *c, cudaError_t e, const char *what);
 int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name);
 int ensure_status(idm_ctx *c);
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
+// Forward shape for the segment capacity of the adjoint shape (vpt, G).
+void forward_shape(int vpt, int G, int *vpt_f, int *G_f);
 int check_params(idm_ctx *c, const idm_params_t *p, bool all);
 int forward_grid(idm_ctx *c, Prep *P, int L);
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L);

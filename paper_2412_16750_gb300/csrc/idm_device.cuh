@@ -103,45 +103,39 @@ __device__ __forceinline__ float accel_star(float v, float gap_raw, float vh, co
     return __fadd_rn(a_lb, s2.sp);
 }
 
-// Vehicle state: displacement since step 0 as an unevaluated float pair
-// (xh + xl), speed, and raw gap to the leader.
+// Vehicle state: absolute position as an unevaluated float pair (ph + pl,
+// ph the float32 position, pl the accumulated rounding error), speed, and
+// raw gap to the leader.
 struct State {
-    float xh, xl, v, gap;
+    float ph, pl, v, gap;
 };
 
 // Explicit Euler step (Eq. 3): positions use the old speeds, so the gap
-// moves by dt (vh - v); the displacement is accumulated with TwoSum plus the
-// exact rounding error of dt*v, so xh + xl stays within ~1e-10 relative.
+// moves by dt (vh - v); the position is accumulated with TwoSum plus the
+// exact rounding error of dt*v, so ph + pl stays within ~1e-10 relative of
+// the exact sum.
 __device__ __forceinline__ void euler(State &s, float a_star, float vh, float dt)
 {
     float d = __fmul_rn(dt, s.v);
     float d_err = __fmaf_rn(dt, s.v, -d);
-    float t = __fadd_rn(s.xh, d);
-    float bb = __fsub_rn(t, s.xh);
-    float err = __fadd_rn(__fsub_rn(s.xh, __fsub_rn(t, bb)), __fsub_rn(d, bb));
-    s.xh = t;
-    s.xl = __fadd_rn(s.xl, __fadd_rn(err, d_err));
+    float t = __fadd_rn(s.ph, d);
+    float bb = __fsub_rn(t, s.ph);
+    float err = __fadd_rn(__fsub_rn(s.ph, __fsub_rn(t, bb)), __fsub_rn(d, bb));
+    s.ph = t;
+    s.pl = __fadd_rn(s.pl, __fadd_rn(err, d_err));
     s.gap = __fmaf_rn(dt, __fsub_rn(vh, s.v), s.gap);
     s.v = __fmaf_rn(dt, a_star, s.v);
 }
 
-// p_init + xh + xl - y, evaluated with TwoSum so the residual keeps the
-// precision of the pair even when p_init is kilometres from zero.
-__device__ __forceinline__ float residual(float p_init, const State &s, float y)
+// ph + pl - y.  ph - y is exact when the target is within a factor two of the
+// position (Sterbenz) and otherwise rounds at the scale of the residual, so the
+// residual keeps the pair's precision even kilometres from the origin.
+__device__ __forceinline__ float residual(const State &s, float y)
 {
-    float t = __fadd_rn(p_init, s.xh);
-    float bb = __fsub_rn(t, p_init);
-    float err = __fadd_rn(__fsub_rn(p_init, __fsub_rn(t, bb)), __fsub_rn(s.xh, bb));
-    return __fadd_rn(__fsub_rn(t, y), __fadd_rn(err, s.xl));
+    return __fadd_rn(__fsub_rn(s.ph, y), s.pl);
 }
 
-__device__ __forceinline__ float position(float p_init, const State &s)
-{
-    float t = __fadd_rn(p_init, s.xh);
-    float bb = __fsub_rn(t, p_init);
-    float err = __fadd_rn(__fsub_rn(p_init, __fsub_rn(t, bb)), __fsub_rn(s.xh, bb));
-    return __fadd_rn(t, __fadd_rn(err, s.xl));
-}
+__device__ __forceinline__ float position(const State &s) { return __fadd_rn(s.ph, s.pl); }
 
 // Leader values in the strided slot mapping: slot q = lane + 32 j of the
 // warp; the leader of slot q is q-1 (thread lane-1, same j; for lane 0,

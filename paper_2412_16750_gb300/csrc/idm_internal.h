@@ -65,9 +65,12 @@ cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_ini
                             int N, float *g0, unsigned *status, cudaStream_t st);
 cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *scen_lane_off, int n_scen,
                                   int cap, int N, Seg *seg, int *n_seg, unsigned *status, cudaStream_t st);
-cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
+// The kernel shape (vehicles per thread, warps per segment) of each launch is
+// passed explicitly; the forward and the adjoint may differ as long as
+// 32 * vpt * G (the segment capacity the segments were packed for) agrees.
+cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
                            cudaStream_t st);
-cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
+cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
 size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb);
 size_t forward_smem_bytes(int vpt, int G, int wpb);

@@ -143,7 +143,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
                                        ctl + CTL_NSEG, status, st);
     if (e == cudaSuccess) {
         a.work = ctl + CTL_WORK_F;
-        e = idm::launch_forward(P.vpt, false, false, true, a, P.grid_f, P.wpb_f, st);
+        e = idm::launch_forward(P.vpt_f, P.G_f, false, false, true, a, P.grid_f, P.wpb_f, st);
     }
     if (e == cudaSuccess) {
         a.work = ctl + CTL_WORK_B;
@@ -153,7 +153,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
         }
         a.g_p_init = grad_p_init;
         a.g_v_init = grad_v_init;
-        e = idm::launch_backward(P.vpt, false, false, want_delta, a, P.grid_b, P.wpb_b, st);
+        e = idm::launch_backward(P.vpt, P.G, false, false, want_delta, a, P.grid_b, P.wpb_b, st);
     }
     if (e == cudaSuccess)
         e = idm::launch_loss_finalize(a.loss_part, a.n_seg, G, loss_out ? loss_out : (double *)(base + o_loss), st);

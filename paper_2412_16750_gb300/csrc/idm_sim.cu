@@ -271,7 +271,7 @@ __device__ __forceinline__ void grp_follow_in(const Grp &g, float p_first, float
 
 template <int VPT>
 __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, int wb, VehConst (&kc)[VPT],
-                                              State (&st)[VPT], float (&pin)[VPT], bool (&valid)[VPT])
+                                              State (&st)[VPT], bool (&valid)[VPT])
 {
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
@@ -280,12 +280,10 @@ __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, i
         if (valid[j]) {
             const int gi = sg.veh_begin + q;
             kc[j] = make_const(a.v0[gi], a.T[gi], a.s0[gi], a.am[gi], a.b[gi], a.delta[gi]);
-            st[j] = State{0.0f, 0.0f, a.v_init[gi], a.g0[gi]};
-            pin[j] = a.p_init[gi];
+            st[j] = State{a.p_init[gi], 0.0f, a.v_init[gi], a.g0[gi]};
         } else {
             kc[j] = ghost_const();
             st[j] = State{0.0f, 0.0f, 0.0f, INFINITY};
-            pin[j] = 0.0f;
         }
     }
 }
@@ -315,7 +313,7 @@ struct FwdFlags {
 
 template <int VPT, bool D4>
 __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int lb, Grp &g,
-                                                const VehConst (&kc)[VPT], State (&st)[VPT], const float (&pin)[VPT],
+                                                const VehConst (&kc)[VPT], State (&st)[VPT],
                                                 const bool (&valid)[VPT], FwdFlags f)
 {
     const int lane = g.lane;
@@ -330,8 +328,8 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
                 const int q = lane + 32 * j;
-                base[q] = st[j].xh;
-                base[(size_t)Ns + q] = st[j].xl;
+                base[q] = st[j].ph;
+                base[(size_t)Ns + q] = st[j].pl;
                 base[2 * (size_t)Ns + q] = st[j].v;
                 base[3 * (size_t)Ns + q] = st[j].gap;
             }
@@ -344,7 +342,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             for (int j = 0; j < VPT; ++j) {
                 if (!valid[j]) continue;
                 const int q = lane + 32 * j;
-                if (f.traj) a.traj[row + q] = position(pin[j], st[j]);
+                if (f.traj) a.traj[row + q] = position(st[j]);
                 if (f.vtraj) a.vtraj[row + q] = st[j].v;
             }
         }
@@ -364,7 +362,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < VPT; ++j)
-        if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].xh))) bad = true;
+        if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].ph))) bad = true;
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
 }
 
@@ -386,13 +384,12 @@ forward_kernel(SimArgs a, FwdFlags f)
         const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
         VehConst kc[VPT];
         State st[VPT];
-        float pin[VPT];
         bool valid[VPT];
-        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
+        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            forward_segment<VPT, true>(a, sc, lb, g, kc, st, pin, valid, f);
+            forward_segment<VPT, true>(a, sc, lb, g, kc, st, valid, f);
         else
-            forward_segment<VPT, false>(a, sc, lb, g, kc, st, pin, valid, f);
+            forward_segment<VPT, false>(a, sc, lb, g, kc, st, valid, f);
     }
 }
 
@@ -418,7 +415,7 @@ __host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, in
 template <int VPT, bool DENSE, bool ADAM, bool WD, bool D4>
 __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
                                                  Grp &g, float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
-                                                 const float (&pin)[VPT], const bool (&valid)[VPT])
+                                                 const bool (&valid)[VPT])
 {
     constexpr int SL = 32 * VPT;
     const int SLG = SL * g.G;
@@ -432,7 +429,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     const float dt = sc.dt;
     const float seed_scale = 2.0f * sc.inv_nobs;
     int xp = 0, fp = 0;
-    float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE), Kahan
+    float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
 
     float lp[VPT], lv[VPT];
 #pragma unroll
@@ -466,6 +463,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             }
         }
         if (!DENSE) cp_async_wait<0>();
+        float lseg = 0.0f;
         // recompute the segment into the tape
         for (int s = 0; s < n; ++s) {
             const int k = c0 + s;
@@ -480,9 +478,9 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     float *rr = tr + s * SLG + wb;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) {
-                        float r = valid[j] ? residual(pin[j], st[j], rr[lane + 32 * j]) : 0.0f;
+                        float r = valid[j] ? residual(st[j], rr[lane + 32 * j]) : 0.0f;
                         rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
-                        kahan_add(lsum, lcomp, __fmul_rn(r, r));
+                        lseg = __fmaf_rn(r, r, lseg);
                     }
                 }
                 obs_k += sc.obs_stride;
@@ -515,13 +513,14 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 #pragma unroll
                     for (int j = 0; j < VPT; ++j)
                         if (valid[j]) {
-                            const float r = residual(pin[j], st[j], __ldg(y + lane + 32 * j));
+                            const float r = residual(st[j], __ldg(y + lane + 32 * j));
                             lp[j] = __fmul_rn(seed_scale, r);
                             kahan_add(lsum, lcomp, __fmul_rn(r, r));
                         }
                 }
             }
         }
+        kahan_add(lsum, lcomp, lseg);
         grp_sync(g);  // the whole group's tape is written
 
         float sacc[6][VPT];
@@ -679,13 +678,12 @@ backward_kernel(SimArgs a)
         const int lb = sg.veh_begin - sc.veh_begin;
         VehConst kc[VPT];
         State st[VPT];
-        float pin[VPT];
         bool valid[VPT];
-        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, pin, valid);
+        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, valid);
         if (segment_is_d4<VPT>(kc, valid))
-            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, valid);
         else
-            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, pin, valid);
+            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, valid);
     }
 }
 
@@ -717,7 +715,7 @@ cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int 
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
-cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
+cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
                            cudaStream_t st)
 {
     FwdFlags f{traj, vtraj, ckpt};
@@ -729,10 +727,11 @@ cudaError_t launch_forward(int vpt, bool traj, bool vtraj, bool ckpt, const SimA
     case 8: fn = (void *)forward_kernel<8>; break;
     default: return cudaErrorInvalidValue;
     }
-    const size_t smem = forward_smem_bytes(vpt, a.G, wpb);
+    const size_t smem = forward_smem_bytes(vpt, G, wpb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SimArgs args = a;
+    args.G = G;
     void *params[] = {&args, &f};
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
@@ -769,16 +768,17 @@ static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd)
     return nullptr;
 }
 
-cudaError_t launch_backward(int vpt, bool dense_seed, bool adam, bool want_delta, const SimArgs &a, int grid,
+cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool want_delta, const SimArgs &a, int grid,
                             int wpb, cudaStream_t st)
 {
     if (dense_seed && adam) return cudaErrorInvalidValue;
     void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam);
     if (!fn) return cudaErrorInvalidValue;
-    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, a.G, wpb);
+    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, G, wpb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SimArgs args = a;
+    args.G = G;
     void *params[] = {&args};
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }

@@ -1,0 +1,87 @@
+"""Multi-rank path on CPU (gloo, world size 2): lane sharding and the two
+host-side collectives.  The sharded loss equals the unsharded one and every
+rank's gradients equal its slice of the full adjoint (FP64 oracle)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2412_16750_gb300 import dist as idm_dist
+from paper_2412_16750_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+
+def test_lane_shards_balanced_and_complete():
+    lane_off = synth.lane_offsets([5, 100, 3, 40, 40, 7, 90, 1])
+    for world in (1, 2, 3, 4, 8):
+        sh = idm_dist.lane_shards(lane_off, world)
+        assert sh[0][0] == 0 and sh[-1][1] == 8
+        assert all(sh[r][1] == sh[r + 1][0] for r in range(world - 1))
+    sh = idm_dist.lane_shards(synth.lane_offsets([100] * 20), 4)
+    assert [b - a for a, b in sh] == [5, 5, 5, 5]
+    assert idm_dist.weak_scaling_value(1e9, 4, 1000.0) == pytest.approx(4e9)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sc = synth.make_scene([7, 12, 3, 9, 15, 4], np.random.default_rng(40))
+    K, dt = 25, float(np.float32(0.1))
+    N = int(sc["lane_off"][-1])
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, dt)
+    Y = P[1:] + np.random.default_rng(41).normal(0, 0.5, size=(K, N))
+    theta = synth.plain_init(N)
+    l0, l1 = idm_dist.lane_shards(sc["lane_off"], world)[rank]
+    a, e, lo = idm_dist.shard_arrays(sc["lane_off"], l0, l1)
+    Ps, Vs = oracle.forward(lo, sc["length"][a:e], theta[:, a:e], sc["p_init"][a:e], sc["v_init"][a:e], K, dt)
+    L, gP = oracle.mse_seed(Ps, Y[:, a:e], 1)
+    g, _, _ = oracle.adjoint(lo, sc["length"][a:e], theta[:, a:e], K, dt, Ps, Vs, gP)
+    total = idm_dist.all_reduce_scalar(L, "sum")
+    slowest = idm_dist.all_reduce_scalar(float(rank + 1), "max")
+    out.put((rank, a, e, L, total, slowest, g))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_loss_and_gradients_match_unsharded():
+    import multiprocessing as mp
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sc = synth.make_scene([7, 12, 3, 9, 15, 4], np.random.default_rng(40))
+    K, dt = 25, float(np.float32(0.1))
+    N = int(sc["lane_off"][-1])
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, dt)
+    Y = P[1:] + np.random.default_rng(41).normal(0, 0.5, size=(K, N))
+    theta = synth.plain_init(N)
+    Pf, Vf = oracle.forward(sc["lane_off"], sc["length"], theta, sc["p_init"], sc["v_init"], K, dt)
+    Lf, gPf = oracle.mse_seed(Pf, Y, 1)
+    gf, _, _ = oracle.adjoint(sc["lane_off"], sc["length"], theta, K, dt, Pf, Vf, gPf)
+    covered = np.zeros(N, dtype=bool)
+    for rank, a, e, L, total, slowest, g in res:
+        assert total == pytest.approx(Lf, rel=1e-12)
+        assert slowest == 2.0
+        np.testing.assert_allclose(g, gf[:, a:e], rtol=1e-12, atol=1e-15)
+        covered[a:e] = True
+    assert covered.all()
