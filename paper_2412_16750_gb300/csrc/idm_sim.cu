@@ -444,13 +444,16 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     for (int cs = n_ck - 1; cs >= 0; --cs) {
         const int c0 = cs * a.C;
         const int n = min(a.C, sc.K - c0);
-        // first observed step >= max(c0, 1)
-        int obs_k = ((c0 + sc.obs_stride - 1) / sc.obs_stride) * sc.obs_stride;
-        if (obs_k == 0) obs_k = sc.obs_stride;
+        // first observed step >= max(c0, 1) and its target row (one division
+        // per checkpoint segment; the step loops count instead of dividing)
+        int obs_row = (c0 + sc.obs_stride - 1) / sc.obs_stride;
+        if (obs_row == 0) obs_row = 1;
+        int obs_k = obs_row * sc.obs_stride;
+        obs_row -= 1;
         if (!DENSE) {  // fetch the segment's observed targets into the seed tape
-            for (int k = obs_k; k < c0 + n && k / sc.obs_stride <= sc.n_obs; k += sc.obs_stride)
-                prefetch_row<VPT>(tr + (k - c0) * SLG + wb,
-                                  a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl, lane, valid);
+            const float *yrow = a.targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
+            for (int k = obs_k, r = obs_row; k < c0 + n && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
+                prefetch_row<VPT>(tr + (k - c0) * SLG + wb, yrow, lane, valid);
             cp_async_commit();
         }
         {
@@ -474,7 +477,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 rg[lane + 32 * j] = st[j].gap;
             }
             if (!DENSE && k == obs_k) {
-                if (k / sc.obs_stride <= sc.n_obs) {
+                if (obs_row < sc.n_obs) {
                     float *rr = tr + s * SLG + wb;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) {
@@ -484,6 +487,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     }
                 }
                 obs_k += sc.obs_stride;
+                ++obs_row;
             }
             float vcur[VPT], vh[VPT];
 #pragma unroll
@@ -530,7 +534,8 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             for (int j = 0; j < VPT; ++j) sacc[q][j] = 0.0f;
 
         // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
-        int obs_hi = ((c0 + n - 1) / sc.obs_stride) * sc.obs_stride;
+        int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
+        int obs_hi = row_hi * sc.obs_stride;
         // The step-k coefficients do not depend on the adjoint, so those of
         // step k-1 are evaluated while the dependent chain of step k runs.
         AdjJac J[VPT];
@@ -582,12 +587,13 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     if (a.gV) seed_v[j] = a.gV[row + lane + 32 * j];
                 }
             } else if (k == obs_hi) {
-                if (k >= 1 && k / sc.obs_stride <= sc.n_obs) {
+                if (k >= 1 && row_hi <= sc.n_obs) {
                     const float *rr = tr + s * SLG + wb;
 #pragma unroll
                     for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
                 }
                 obs_hi -= sc.obs_stride;
+                --row_hi;
             }
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
