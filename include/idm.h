@@ -114,8 +114,8 @@ int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
 
 /* Kernel shape.  Whole lanes are packed into segments of at most
  * 32 * vpt * warps_per_segment vehicles, each simulated by warps_per_segment
- * warps of one block.  vpt: vehicles per thread (1, 2, 4 or 8; 0 = choose);
- * warps_per_segment: 1, 2, 4 or 8 (0 = choose; default 4 with vpt 4);
+ * warps of one block.  vpt: vehicles per thread (2, 4 or 8; 0 = choose);
+ * warps_per_segment: 1, 2, 4 or 8 (0 = choose; default 8 with vpt 2);
  * ckpt_interval: steps between stored checkpoints of the adjoint (1..64,
  * default 8); warps_per_block: 1..16 (default 8; rounded to a multiple of
  * warps_per_segment, and the adjoint caps it by its shared-memory tape). */

@@ -98,7 +98,7 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
             else break;
         }
     } else if (v == 0) {
-        v = 1;
+        v = 2;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
     } else if (g == 0) {
         g = 1;
@@ -379,8 +379,8 @@ const char *idm_last_error(const idm_ctx_t *c) { return c ? c->err : "no context
 int idm_set_tuning(idm_ctx_t *c, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block)
 {
     if (!c) return IDM_ERR_ARG;
-    if (!(vpt == 0 || vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8))
-        return fail(c, IDM_ERR_ARG, "vpt must be 0, 1, 2, 4 or 8");
+    if (!(vpt == 0 || vpt == 2 || vpt == 4 || vpt == 8))
+        return fail(c, IDM_ERR_ARG, "vpt must be 0, 2, 4 or 8");
     if (!(warps_per_segment == 0 || warps_per_segment == 1 || warps_per_segment == 2 || warps_per_segment == 4 ||
           warps_per_segment == 8))
         return fail(c, IDM_ERR_ARG, "warps_per_segment must be 0, 1, 2, 4 or 8");

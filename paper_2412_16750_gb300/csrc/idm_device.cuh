@@ -1,9 +1,13 @@
 // Device arithmetic of the modified IDM step (Eq. 1-3 and the softplus
 // bounds of Sec. III-C, arXiv 2412.16750) and of its partial derivatives.
 //
-// Every rounding in the state update is written with explicit _rn
-// intrinsics so that the forward kernel and the recompute inside the adjoint
-// kernel produce bit-identical trajectories (no contraction freedom).
+// Two vehicles are processed per instruction: every value is a float2 pair
+// and the FP32 arithmetic uses the packed sm_100+ forms (FADD2 / FMUL2 /
+// FFMA2) with round-to-nearest, so each component is rounded exactly as a
+// scalar op would round it.  Special functions (exp2, log2, reciprocal) are
+// per component on the SFU.  Every rounding in the state update is explicit,
+// so the forward kernel and the recompute inside the adjoint kernel produce
+// bit-identical trajectories.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -13,7 +17,22 @@
 namespace idm {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr float LOG2E = 1.44269504088896340736f;
+constexpr float LN2 = 0.69314718055994530942f;
 
+// ---- special-function unit (PTX approximate ops) ---------------------------
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float r;
@@ -21,223 +40,244 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// Softplus pieces: e = exp(-|x|) and sp(x) = max(x,0) + log(1 + e).
-struct Soft {
-    float e;   // exp(-|x|)
-    float sp;  // softplus(x)
+// ---- packed pairs ------------------------------------------------------------
+using f2 = float2;
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one fused op: b * (-1) + a is exact before its single rounding,
+// so the result equals the correctly rounded difference.
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }
+__device__ __forceinline__ f2 ex2(f2 x) { return make_float2(ex2_approx(x.x), ex2_approx(x.y)); }
+__device__ __forceinline__ f2 lg2(f2 x) { return make_float2(lg2_approx(x.x), lg2_approx(x.y)); }
+__device__ __forceinline__ f2 rcp2(f2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
+__device__ __forceinline__ f2 vmax(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 vabs(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+
+// Softplus pieces: e = exp(-|x|) = 2^(-|x| log2 e) and
+// sp(x) = max(x, 0) + ln(1 + e) = log2(1 + e) * ln 2 + max(x, 0).
+struct Soft2 {
+    f2 e;
+    f2 sp;
 };
 
-__device__ __forceinline__ Soft softplus(float x)
+__device__ __forceinline__ Soft2 softplus2(f2 x)
 {
-    Soft s;
-    s.e = __expf(-fabsf(x));
-    s.sp = __fadd_rn(fmaxf(x, 0.0f), __logf(__fadd_rn(1.0f, s.e)));
+    Soft2 s;
+    s.e = ex2(mul2(vabs(x), F2(-LOG2E)));
+    s.sp = fma2(lg2(add2(F2(1.0f), s.e)), F2(LN2), vmax(x, F2(0.0f)));
     return s;
 }
 
-// Logistic sigmoid from the e = exp(-|x|) already computed for softplus.
-__device__ __forceinline__ float sigmoid_from(float x, float e)
+// Logistic sigmoid from the e = exp(-|x|) of softplus2: sigma(x) and
+// sigma(-x) = 1 - sigma(x) without cancellation.
+__device__ __forceinline__ void sigmoid2(f2 x, f2 e, f2 &sig, f2 &sig_neg)
 {
-    float d = rcp_approx(__fadd_rn(1.0f, e));
-    return x >= 0.0f ? d : __fmul_rn(e, d);
+    const f2 d = rcp2(add2(F2(1.0f), e));
+    const f2 ed = mul2(e, d);
+    sig = make_float2(x.x >= 0.0f ? d.x : ed.x, x.y >= 0.0f ? d.y : ed.y);
+    sig_neg = make_float2(x.x >= 0.0f ? ed.x : d.x, x.y >= 0.0f ? ed.y : d.y);
 }
 
-// Per-vehicle constants of one call.
-struct VehConst {
-    float inv_v0;  // 1 / v0
-    float T, s0, am, c;  // c = 1 / (2 sqrt(a_max b)), Eq. 1
-    float delta;
+// Per-vehicle constants of one call, for a pair of vehicles.
+struct VehConst2 {
+    f2 inv_v0;          // 1 / v0
+    f2 T, s0, am, c;    // c = 1 / (2 sqrt(a_max b)), Eq. 1
+    f2 delta;
 };
 
-__device__ __forceinline__ VehConst make_const(float v0, float T, float s0, float am, float b, float delta)
-{
-    VehConst k;
-    k.inv_v0 = __frcp_rn(v0);
-    k.T = T;
-    k.s0 = s0;
-    k.am = am;
-    k.c = __fmul_rn(0.5f, rsqrtf(__fmul_rn(am, b)));
-    k.delta = delta;
-    return k;
-}
+__device__ __forceinline__ float c_of(float am, float b) { return __fmul_rn(0.5f, rsqrtf(__fmul_rn(am, b))); }
 
-// Ghost slots (padding at the end of a warp segment) and lane heads never
-// feed a real vehicle; these constants keep their arithmetic finite.
-__device__ __forceinline__ VehConst ghost_const()
-{
-    VehConst k;
-    k.inv_v0 = 1.0f; k.T = 0.0f; k.s0 = 0.0f; k.am = 1.0f; k.c = 0.5f; k.delta = 4.0f;
-    return k;
-}
-
-// (v / v0)^delta.  D4: every vehicle of the warp has delta == 4 (decided
-// once per segment), so the power is two squarings and the step body has no
-// per-vehicle branch.
+// (v / v0)^delta.  D4: every vehicle of the warp has delta == 4 (decided once
+// per segment), so the power is two squarings.
 template <bool D4>
-__device__ __forceinline__ float pow_delta(float r, float delta)
+__device__ __forceinline__ f2 pow_delta2(f2 r, f2 delta)
 {
     if (D4) {
-        float r2 = __fmul_rn(r, r);
-        return __fmul_rn(r2, r2);
+        const f2 r2 = mul2(r, r);
+        return mul2(r2, r2);
     }
-    return r > 0.0f ? __powf(r, delta) : 0.0f;
+    return make_float2(r.x > 0.0f ? __powf(r.x, delta.x) : 0.0f, r.y > 0.0f ? __powf(r.y, delta.y) : 0.0f);
 }
 
-// Bounded acceleration a* of one vehicle from its speed v, its raw gap
-// (p_h - p - length_h; +inf for a lane head) and its leader's speed vh.
-template <bool D4>
-__device__ __forceinline__ float accel_star(float v, float gap_raw, float vh, const VehConst &k,
-                                            float inv_dt, float a_min)
+__device__ __forceinline__ f2 floor_gap(f2 g)
 {
-    float gap = gap_raw < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : gap_raw;
-    float dv = __fsub_rn(v, vh);                                   // Sec. III-A
-    float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);    // Eq. 1
-    Soft s1 = softplus(s_opt);                                     // Sec. III-C
-    float z = __fmul_rn(s1.sp, rcp_approx(gap));                   // 0 for a head
-    float r = __fmul_rn(v, k.inv_v0);
-    float rd = pow_delta<D4>(r, k.delta);
-    float a = __fmul_rn(k.am, __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z)));  // Eq. 2
-    float lbv = -__fmul_rn(v, inv_dt);
-    float a_lb = lbv > a_min ? lbv : a_min;                        // Sec. III-C
-    Soft s2 = softplus(__fsub_rn(a, a_lb));
-    return __fadd_rn(a_lb, s2.sp);
+    return make_float2(g.x < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : g.x, g.y < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : g.y);
 }
 
-// Vehicle state: absolute position as an unevaluated float pair (ph + pl,
-// ph the float32 position, pl the accumulated rounding error), speed, and
-// raw gap to the leader.
-struct State {
-    float ph, pl, v, gap;
+// a_lb = max(-v/dt, a_min) with the strict-inequality tie rule (Sec. III-C).
+__device__ __forceinline__ f2 lower_bound(f2 lbv, float a_min, bool &bx, bool &by)
+{
+    bx = lbv.x > a_min;
+    by = lbv.y > a_min;
+    return make_float2(bx ? lbv.x : a_min, by ? lbv.y : a_min);
+}
+
+// Bounded acceleration a* of two vehicles from their speeds v, raw gaps
+// (p_h - p - length_h; +inf for a lane head) and leaders' speeds vh.
+template <bool D4>
+__device__ __forceinline__ f2 accel_star2(f2 v, f2 gap_raw, f2 vh, const VehConst2 &k, float inv_dt, float a_min)
+{
+    const f2 gap = floor_gap(gap_raw);
+    const f2 dv = sub2(v, vh);                                  // Sec. III-A
+    const f2 s_opt = fma2(v, fma2(dv, k.c, k.T), k.s0);         // Eq. 1
+    const Soft2 s1 = softplus2(s_opt);                          // Sec. III-C
+    const f2 z = mul2(s1.sp, rcp2(gap));                        // 0 for a head
+    const f2 r = mul2(v, k.inv_v0);
+    const f2 rd = pow_delta2<D4>(r, k.delta);
+    const f2 a = mul2(k.am, sub2(sub2(F2(1.0f), rd), mul2(z, z)));  // Eq. 2
+    bool bx, by;
+    const f2 a_lb = lower_bound(mul2(v, F2(-inv_dt)), a_min, bx, by);  // Sec. III-C
+    const Soft2 s2 = softplus2(sub2(a, a_lb));
+    return add2(a_lb, s2.sp);
+}
+
+// Vehicle-pair state: absolute position as an unevaluated float pair
+// (ph + pl, ph the float32 position, pl the accumulated rounding error),
+// speed, and raw gap to the leader.
+struct State2 {
+    f2 ph, pl, v, gap;
 };
 
-// Explicit Euler step (Eq. 3): positions use the old speeds, so the gap
-// moves by dt (vh - v); the position is accumulated with TwoSum plus the
-// exact rounding error of dt*v, so ph + pl stays within ~1e-10 relative of
-// the exact sum.
-__device__ __forceinline__ void euler(State &s, float a_star, float vh, float dt)
+// Explicit Euler step (Eq. 3): positions use the old speeds, so the gap moves
+// by dt (vh - v).  The position is accumulated with TwoSum plus the exact
+// rounding error of dt*v (en = d - dt*v, so the error is -en), keeping
+// ph + pl within ~1e-10 relative of the exact sum.
+__device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, float dt)
 {
-    float d = __fmul_rn(dt, s.v);
-    float d_err = __fmaf_rn(dt, s.v, -d);
-    float t = __fadd_rn(s.ph, d);
-    float bb = __fsub_rn(t, s.ph);
-    float err = __fadd_rn(__fsub_rn(s.ph, __fsub_rn(t, bb)), __fsub_rn(d, bb));
+    const f2 d = mul2(F2(dt), s.v);
+    const f2 en = fma2(F2(-dt), s.v, d);
+    const f2 t = add2(s.ph, d);
+    const f2 bb = sub2(t, s.ph);
+    const f2 err = add2(sub2(s.ph, sub2(t, bb)), sub2(d, bb));
     s.ph = t;
-    s.pl = __fadd_rn(s.pl, __fadd_rn(err, d_err));
-    s.gap = __fmaf_rn(dt, __fsub_rn(vh, s.v), s.gap);
-    s.v = __fmaf_rn(dt, a_star, s.v);
+    s.pl = add2(s.pl, sub2(err, en));
+    s.gap = fma2(F2(dt), sub2(vh, s.v), s.gap);
+    s.v = fma2(F2(dt), a_star, s.v);
 }
 
 // ph + pl - y.  ph - y is exact when the target is within a factor two of the
-// position (Sterbenz) and otherwise rounds at the scale of the residual, so the
-// residual keeps the pair's precision even kilometres from the origin.
-__device__ __forceinline__ float residual(const State &s, float y)
-{
-    return __fadd_rn(__fsub_rn(s.ph, y), s.pl);
-}
+// position (Sterbenz) and otherwise rounds at the scale of the residual.
+__device__ __forceinline__ f2 residual2(const State2 &s, f2 y) { return add2(sub2(s.ph, y), s.pl); }
 
-__device__ __forceinline__ float position(const State &s) { return __fadd_rn(s.ph, s.pl); }
+__device__ __forceinline__ f2 position2(const State2 &s) { return add2(s.ph, s.pl); }
 
-// Leader values in the strided slot mapping: slot q = lane + 32 j of the
-// warp; the leader of slot q is q-1 (thread lane-1, same j; for lane 0,
-// thread 31 of j-1).  The warp's first slot receives lead_in (the previous
-// warp's last slot, or 0 at the start of a segment, which is a lane head).
-template <int VPT>
-__device__ __forceinline__ void leader_vals(const float (&x)[VPT], float (&out)[VPT], int lane, float lead_in)
+// ---- neighbours in the warp's slot mapping -----------------------------------
+// Pair p of lane l holds the consecutive slots 64p + 2l (.x) and 64p + 2l + 1
+// (.y).  The leader of .y is the same thread's .x; the leader of .x is lane
+// l-1's .y (for lane 0: lane 31's .y of pair p-1, or lead_in for p = 0, the
+// previous warp's last slot or 0 at a segment start).
+template <int NP>
+__device__ __forceinline__ void leader_vals2(const f2 (&x)[NP], f2 (&out)[NP], int lane, float lead_in)
 {
-    float rot[VPT];
+    float ry[NP];
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 31) & 31);
+    for (int p = 0; p < NP; ++p) ry[p] = __shfl_sync(FULL, x[p].y, (lane + 31) & 31);
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-        float prev = j > 0 ? rot[j - 1] : lead_in;
-        out[j] = lane == 0 ? prev : rot[j];
+    for (int p = 0; p < NP; ++p) {
+        const float prev = p > 0 ? ry[p - 1] : lead_in;
+        out[p].x = lane == 0 ? prev : ry[p];
+        out[p].y = x[p].x;
     }
 }
 
-// Follower values: slot q receives from slot q+1 (thread lane+1, same j;
-// for lane 31, thread 0 of j+1).  The warp's last slot receives fin (the
-// next warp's first slot, or 0 at the end of a segment).
-template <int VPT>
-__device__ __forceinline__ void follower_vals(const float (&x)[VPT], float (&out)[VPT], int lane, float fin)
+// Follower values: the follower of .x is the same thread's .y; the follower
+// of .y is lane l+1's .x (for lane 31: lane 0's .x of pair p+1, or fin for the
+// warp's last slot).
+template <int NP>
+__device__ __forceinline__ void follower_vals2(const f2 (&x)[NP], f2 (&out)[NP], int lane, float fin)
 {
-    float rot[VPT];
+    float rx[NP];
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) rot[j] = __shfl_sync(FULL, x[j], (lane + 1) & 31);
+    for (int p = 0; p < NP; ++p) rx[p] = __shfl_sync(FULL, x[p].x, (lane + 1) & 31);
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-        float nxt = j + 1 < VPT ? rot[j + 1] : fin;
-        out[j] = lane == 31 ? nxt : rot[j];
+    for (int p = 0; p < NP; ++p) {
+        const float nxt = p + 1 < NP ? rx[p + 1] : fin;
+        out[p].x = x[p].y;
+        out[p].y = lane == 31 ? nxt : rx[p];
     }
 }
 
-}  // namespace idm
-
-namespace idm {
-
-// Coefficients of one reverse step for one vehicle (the adjoint of
-// accel_star and euler), independent of the incoming adjoint.  With
-// sigma2 = d a*/d a, sigma1 = d s*/d s_opt, S = d a/d s*, G = d a/d gap:
-//   Ap  = d a*/d p         = -sigma2 G     (the leader's d a*/d p_h is -Ap)
+// ---- adjoint coefficients ------------------------------------------------------
+// Coefficients of one reverse step for a vehicle pair (the adjoint of
+// accel_star2 and euler2), independent of the incoming adjoint.  With
+// sigma2 = d a*/d a, sigma1 = d s*/d s_opt, Sn = -d a/d s* = 2 a_max z / gap
+// and G = d a/d gap = Sn z (0 below the gap floor):
+//   Aph = d a*/d p_leader  =  sigma2 G  (own d a*/d p is -Aph)
 //   Av  = d a*/d v         (own speed, incl. the a_lb branch)
-//   Avh = d a*/d v_leader  = w0 (-c v),  w0 = sigma2 S sigma1
-// and the parameter-gradient factors (per-vehicle constants multiply the
-// sums once at the end): w0, w0 v, w0 v dv, sigma2 (1 - r^delta - z^2),
-// sigma2 r^delta, sigma2 r^delta ln r.  The reverse step multiplies all of
-// them by mu = dt * (adjoint of the step-(k+1) speed), so this part can be
-// evaluated ahead of the dependent adjoint chain.
-struct AdjJac {
-    float Ap, Av, Avh;
-    float w0, w0v, w0vdv, fa, frd, frdl;
+//   Avh = d a*/d v_leader  =  w0n c v,  w0n = sigma2 Sn sigma1
+// and the parameter-gradient factors, all sign-positive forms (per-vehicle
+// constants and signs are applied once at the end): w0n, w0n v, w0n v dv,
+// sigma2 (1 - r^delta - z^2), sigma2 r^delta, sigma2 r^delta ln r.  The
+// reverse step multiplies all of them by mu = dt * (adjoint of the
+// step-(k+1) speed).
+struct AdjJac2 {
+    f2 Aph, Av, Avh;
+    f2 w0n, w0nv, w0nvdv, fa, frd, frdl;
 };
 
 template <bool WANT_DELTA, bool D4>
-__device__ __forceinline__ AdjJac adjoint_jac(float v, float gap_raw, float vh, const VehConst &k, float inv_dt,
-                                              float a_min)
+__device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const VehConst2 &k, float inv_dt,
+                                                float a_min)
 {
-    AdjJac J;
-    const bool floored = gap_raw < IDM_GAP_FLOOR;
-    const float gap = floored ? IDM_GAP_FLOOR : gap_raw;
-    const float dv = __fsub_rn(v, vh);
-    const float s_opt = __fmaf_rn(v, __fmaf_rn(dv, k.c, k.T), k.s0);
-    const Soft s1 = softplus(s_opt);
-    const float sig1 = sigmoid_from(s_opt, s1.e);
-    const float inv_gap = rcp_approx(gap);
-    const float z = __fmul_rn(s1.sp, inv_gap);
-    const float r = __fmul_rn(v, k.inv_v0);
-    float rd, rdm1;
+    AdjJac2 J;
+    const bool fx = gap_raw.x < IDM_GAP_FLOOR, fy = gap_raw.y < IDM_GAP_FLOOR;
+    const f2 gap = floor_gap(gap_raw);
+    const f2 dv = sub2(v, vh);
+    const f2 s_opt = fma2(v, fma2(dv, k.c, k.T), k.s0);
+    const Soft2 s1 = softplus2(s_opt);
+    f2 sig1, sig1n;
+    sigmoid2(s_opt, s1.e, sig1, sig1n);
+    const f2 inv_gap = rcp2(gap);
+    const f2 z = mul2(s1.sp, inv_gap);
+    const f2 r = mul2(v, k.inv_v0);
+    f2 rd, rdm1;
     if (D4) {
-        const float r2 = __fmul_rn(r, r);
-        rd = __fmul_rn(r2, r2);
-        rdm1 = __fmul_rn(r2, r);
+        const f2 r2 = mul2(r, r);
+        rd = mul2(r2, r2);
+        rdm1 = mul2(r2, r);
     } else {
-        rd = r > 0.0f ? __powf(r, k.delta) : 0.0f;
-        rdm1 = r > 0.0f ? __powf(r, k.delta - 1.0f) : (k.delta > 1.0f ? 0.0f : (k.delta == 1.0f ? 1.0f : INFINITY));
+        rd = pow_delta2<false>(r, k.delta);
+        rdm1 = make_float2(
+            r.x > 0.0f ? __powf(r.x, k.delta.x - 1.0f) : (k.delta.x > 1.0f ? 0.0f : (k.delta.x == 1.0f ? 1.0f : INFINITY)),
+            r.y > 0.0f ? __powf(r.y, k.delta.y - 1.0f) : (k.delta.y > 1.0f ? 0.0f : (k.delta.y == 1.0f ? 1.0f : INFINITY)));
     }
-    const float free_and_int = __fsub_rn(__fsub_rn(1.0f, rd), __fmul_rn(z, z));
-    const float a = __fmul_rn(k.am, free_and_int);
-    const float lbv = -__fmul_rn(v, inv_dt);
-    const bool beta = lbv > a_min;
-    const float a_lb = beta ? lbv : a_min;
-    const float x2 = __fsub_rn(a, a_lb);
-    const float e2 = __expf(-fabsf(x2));
-    const float d2 = rcp_approx(__fadd_rn(1.0f, e2));
-    const float ed2 = __fmul_rn(e2, d2);
-    const float sig2 = x2 >= 0.0f ? d2 : ed2;        // sigma(x2)
-    const float one_m_sig2 = x2 >= 0.0f ? ed2 : d2;  // sigma(-x2)
+    const f2 free_and_int = sub2(sub2(F2(1.0f), rd), mul2(z, z));
+    const f2 a = mul2(k.am, free_and_int);
+    bool bx, by;
+    const f2 a_lb = lower_bound(mul2(v, F2(-inv_dt)), a_min, bx, by);
+    const f2 x2 = sub2(a, a_lb);
+    const f2 e2 = ex2(mul2(vabs(x2), F2(-LOG2E)));
+    f2 sig2, one_m_sig2;
+    sigmoid2(x2, e2, sig2, one_m_sig2);
 
-    const float S = -2.0f * k.am * z * inv_gap;  // d a / d s*
-    const float G = floored ? 0.0f : -S * z;     // d a / d gap = 2 a_max z^2 / gap
-    const float w0 = sig2 * S * sig1;
-    const float dfree_dv = -k.am * (D4 ? 4.0f : k.delta) * rdm1 * k.inv_v0;
-    J.Ap = -sig2 * G;
-    J.Av = sig2 * dfree_dv + w0 * (k.T + k.c * (v + dv)) - (beta ? one_m_sig2 * inv_dt : 0.0f);
-    J.Avh = -w0 * k.c * v;
-    J.w0 = w0;
-    J.w0v = w0 * v;
-    J.w0vdv = J.w0v * dv;
-    J.fa = sig2 * free_and_int;
-    J.frd = sig2 * rd;
-    J.frdl = (WANT_DELTA && rd > 0.0f) ? J.frd * __logf(r) : 0.0f;
+    const f2 Sn = mul2(mul2(add2(k.am, k.am), z), inv_gap);   // -d a / d s* = 2 a_max z / gap
+    f2 G = mul2(Sn, z);                                          // d a / d gap = 2 a_max z^2 / gap
+    G.x = fx ? 0.0f : G.x;
+    G.y = fy ? 0.0f : G.y;
+    const f2 w0n = mul2(mul2(sig2, Sn), sig1);
+    const f2 dl = D4 ? F2(4.0f) : k.delta;
+    const f2 q = mul2(mul2(k.am, dl), mul2(rdm1, k.inv_v0));    // -d(free term)/dv
+    f2 beta_term = mul2(one_m_sig2, F2(inv_dt));
+    beta_term.x = bx ? beta_term.x : 0.0f;
+    beta_term.y = by ? beta_term.y : 0.0f;
+    J.Aph = mul2(sig2, G);
+    const f2 u = fma2(k.c, add2(v, dv), k.T);                    // d s_opt / d v
+    J.Av = mul2(fma2(sig2, q, fma2(w0n, u, beta_term)), F2(-1.0f));
+    J.Avh = mul2(mul2(w0n, k.c), v);
+    J.w0n = w0n;
+    J.w0nv = mul2(w0n, v);
+    J.w0nvdv = mul2(J.w0nv, dv);
+    J.fa = mul2(sig2, free_and_int);
+    J.frd = mul2(sig2, rd);
+    if (WANT_DELTA) {
+        const f2 lnr = mul2(lg2(r), F2(LN2));
+        const f2 t = mul2(J.frd, lnr);
+        J.frdl = make_float2(rd.x > 0.0f ? t.x : 0.0f, rd.y > 0.0f ? t.y : 0.0f);
+    } else {
+        J.frdl = F2(0.0f);
+    }
     return J;
 }
 

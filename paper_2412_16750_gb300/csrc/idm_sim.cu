@@ -175,13 +175,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Slots of a warp: pair p of lane l holds slots 64p + 2l and 64p + 2l + 1.
 // dst/src_row already point at this warp's first slot.
-template <int VPT>
-__device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, int lane, const bool (&valid)[VPT])
+template <int NP>
+__device__ __forceinline__ void prefetch_row(float *dst, const float *src_row, int lane, const bool (&vx)[NP],
+                                             const bool (&vy)[NP])
 {
 #pragma unroll
-    for (int j = 0; j < VPT; ++j)
-        if (valid[j]) cp_async4(dst + lane + 32 * j, src_row + lane + 32 * j);
+    for (int p = 0; p < NP; ++p) {
+        const int q = 64 * p + 2 * lane;
+        if (vx[p]) cp_async4(dst + q, src_row + q);
+        if (vy[p]) cp_async4(dst + q + 1, src_row + q + 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -237,12 +242,12 @@ __device__ __forceinline__ int grp_next(const Grp &g, int *work, int &par)
     return s;
 }
 
-// Leader speed of this warp's first slot (0 for the group's first warp).
-template <int VPT>
-__device__ __forceinline__ float grp_lead_in(const Grp &g, const float (&v)[VPT], int &xp)
+// Leader speed of this warp's first slot (0 for the group's first warp);
+// last_v is this lane's value of the warp's last slot (used by lane 31).
+__device__ __forceinline__ float grp_lead_in(const Grp &g, float last_v, int &xp)
 {
     if (g.G == 1) return 0.0f;
-    if (g.lane == 31) g.xl[xp * g.G + g.w] = v[VPT - 1];
+    if (g.lane == 31) g.xl[xp * g.G + g.w] = last_v;
     grp_sync(g);
     const float r = g.w > 0 ? g.xl[xp * g.G + g.w - 1] : 0.0f;
     xp ^= 1;
@@ -269,37 +274,71 @@ __device__ __forceinline__ void grp_follow_in(const Grp &g, float p_first, float
     xp ^= 1;
 }
 
-template <int VPT>
-__device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, int wb, VehConst (&kc)[VPT],
-                                              State (&st)[VPT], bool (&valid)[VPT])
+template <int NP>
+__device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, int lane, int wb, VehConst2 (&kc)[NP],
+                                              State2 (&st)[NP], bool (&vx)[NP], bool (&vy)[NP])
 {
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-        const int q = wb + lane + 32 * j;
-        valid[j] = q < sg.n_veh;
-        if (valid[j]) {
-            const int gi = sg.veh_begin + q;
-            kc[j] = make_const(a.v0[gi], a.T[gi], a.s0[gi], a.am[gi], a.b[gi], a.delta[gi]);
-            st[j] = State{a.p_init[gi], 0.0f, a.v_init[gi], a.g0[gi]};
-        } else {
-            kc[j] = ghost_const();
-            st[j] = State{0.0f, 0.0f, 0.0f, INFINITY};
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int q = wb + 64 * p + 2 * lane + c;
+            const bool ok = q < sg.n_veh;
+            float inv_v0 = 1.0f, T = 0.0f, s0 = 0.0f, am = 1.0f, cc = 0.5f, dl = 4.0f;  // ghost slot
+            float ph = 0.0f, v = 0.0f, gap = INFINITY;
+            if (ok) {
+                const int gi = sg.veh_begin + q;
+                inv_v0 = __frcp_rn(a.v0[gi]);
+                T = a.T[gi];
+                s0 = a.s0[gi];
+                am = a.am[gi];
+                cc = c_of(am, a.b[gi]);
+                dl = a.delta[gi];
+                ph = a.p_init[gi];
+                v = a.v_init[gi];
+                gap = a.g0[gi];
+            }
+            if (c == 0) {
+                vx[p] = ok;
+                kc[p].inv_v0.x = inv_v0; kc[p].T.x = T; kc[p].s0.x = s0; kc[p].am.x = am; kc[p].c.x = cc;
+                kc[p].delta.x = dl;
+                st[p].ph.x = ph; st[p].pl.x = 0.0f; st[p].v.x = v; st[p].gap.x = gap;
+            } else {
+                vy[p] = ok;
+                kc[p].inv_v0.y = inv_v0; kc[p].T.y = T; kc[p].s0.y = s0; kc[p].am.y = am; kc[p].c.y = cc;
+                kc[p].delta.y = dl;
+                st[p].ph.y = ph; st[p].pl.y = 0.0f; st[p].v.y = v; st[p].gap.y = gap;
+            }
         }
     }
 }
 
-
 // True when every occupied slot of the warp has delta == 4, so the step body
 // can use the squaring form of (v/v0)^delta with no branch.  (Both variants
 // execute the same sequence of group barriers.)
-template <int VPT>
-__device__ __forceinline__ bool segment_is_d4(const VehConst (&kc)[VPT], const bool (&valid)[VPT])
+template <int NP>
+__device__ __forceinline__ bool segment_is_d4(const VehConst2 (&kc)[NP], const bool (&vx)[NP], const bool (&vy)[NP])
 {
     bool ok = true;
 #pragma unroll
-    for (int j = 0; j < VPT; ++j)
-        if (valid[j] && kc[j].delta != 4.0f) ok = false;
+    for (int p = 0; p < NP; ++p) {
+        if (vx[p] && kc[p].delta.x != 4.0f) ok = false;
+        if (vy[p] && kc[p].delta.y != 4.0f) ok = false;
+    }
     return __all_sync(FULL, ok);
+}
+
+// Store one pair to a scalar array at slot offset q (two 4-byte stores:
+// the pair's global index need not be 8-byte aligned).
+__device__ __forceinline__ void store_pair(float *base, int q, f2 x, bool vx, bool vy)
+{
+    if (vx) base[q] = x.x;
+    if (vy) base[q + 1] = x.y;
+}
+
+__device__ __forceinline__ f2 load_pair(const float *base, int q, bool vx, bool vy)
+{
+    return make_float2(vx ? base[q] : 0.0f, vy ? base[q + 1] : 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,27 +350,26 @@ struct FwdFlags {
     bool traj, vtraj, ckpt;
 };
 
-template <int VPT, bool D4>
+template <int NP, bool D4>
 __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int lb, Grp &g,
-                                                const VehConst (&kc)[VPT], State (&st)[VPT],
-                                                const bool (&valid)[VPT], FwdFlags f)
+                                                const VehConst2 (&kc)[NP], State2 (&st)[NP], const bool (&vx)[NP],
+                                                const bool (&vy)[NP], FwdFlags f)
 {
     const int lane = g.lane;
     const int Ns = sc.n_veh;
-    const int wl = lb + g.w * 32 * VPT;  // scenario-local index of this warp's first slot
+    const int wl = lb + g.w * 64 * NP;  // scenario-local index of this warp's first slot
     int next_ck = 0, ck_idx = 0;
     int xp = 0;
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
             float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                if (!valid[j]) continue;
-                const int q = lane + 32 * j;
-                base[q] = st[j].ph;
-                base[(size_t)Ns + q] = st[j].pl;
-                base[2 * (size_t)Ns + q] = st[j].v;
-                base[3 * (size_t)Ns + q] = st[j].gap;
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                store_pair(base, q, st[p].ph, vx[p], vy[p]);
+                store_pair(base + (size_t)Ns, q, st[p].pl, vx[p], vy[p]);
+                store_pair(base + 2 * (size_t)Ns, q, st[p].v, vx[p], vy[p]);
+                store_pair(base + 3 * (size_t)Ns, q, st[p].gap, vx[p], vy[p]);
             }
             next_ck += a.C;
             ++ck_idx;
@@ -339,30 +377,31 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
         if (f.traj || f.vtraj) {
             const size_t row = sc.traj_off + (size_t)k * Ns + wl;
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                if (!valid[j]) continue;
-                const int q = lane + 32 * j;
-                if (f.traj) a.traj[row + q] = position(st[j]);
-                if (f.vtraj) a.vtraj[row + q] = st[j].v;
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                if (f.traj) store_pair(a.traj + row, q, position2(st[p]), vx[p], vy[p]);
+                if (f.vtraj) store_pair(a.vtraj + row, q, st[p].v, vx[p], vy[p]);
             }
         }
         if (k == sc.K) break;
 
-        float vcur[VPT], vh[VPT];
+        f2 vcur[NP], vh[NP];
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-        const float lead_in = grp_lead_in<VPT>(g, vcur, xp);
-        leader_vals<VPT>(vcur, vh, lane, lead_in);
+        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+        leader_vals2<NP>(vcur, vh, lane, lead_in);
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
-            euler(st[j], as, vh[j], sc.dt);
+        for (int p = 0; p < NP; ++p) {
+            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+            euler2(st[p], as, vh[p], sc.dt);
         }
     }
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < VPT; ++j)
-        if (valid[j] && !(isfinite(st[j].v) && isfinite(st[j].ph))) bad = true;
+    for (int p = 0; p < NP; ++p) {
+        if (vx[p] && !(isfinite(st[p].v.x) && isfinite(st[p].ph.x))) bad = true;
+        if (vy[p] && !(isfinite(st[p].v.y) && isfinite(st[p].ph.y))) bad = true;
+    }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
 }
 
@@ -370,6 +409,7 @@ template <int VPT>
 __global__ void __launch_bounds__(512)
 forward_kernel(SimArgs a, FwdFlags f)
 {
+    constexpr int NP = VPT / 2;
     extern __shared__ float fsmem[];
     const int G = a.G;
     const int warp = threadIdx.x >> 5;
@@ -382,14 +422,14 @@ forward_kernel(SimArgs a, FwdFlags f)
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
         const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
-        VehConst kc[VPT];
-        State st[VPT];
-        bool valid[VPT];
-        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, valid);
-        if (segment_is_d4<VPT>(kc, valid))
-            forward_segment<VPT, true>(a, sc, lb, g, kc, st, valid, f);
+        VehConst2 kc[NP];
+        State2 st[NP];
+        bool vx[NP], vy[NP];
+        load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
+        if (segment_is_d4<NP>(kc, vx, vy))
+            forward_segment<NP, true>(a, sc, lb, g, kc, st, vx, vy, f);
         else
-            forward_segment<VPT, false>(a, sc, lb, g, kc, st, valid, f);
+            forward_segment<NP, false>(a, sc, lb, g, kc, st, vx, vy, f);
     }
 }
 
@@ -401,9 +441,10 @@ forward_kernel(SimArgs a, FwdFlags f)
 //   lp_k = seed_k + lp_{k+1} + mu A_p + mu_f A_ph(f)
 //   lv_k = dt lp_{k+1} + lv_{k+1} + mu A_v + mu_f A_vh(f)
 // with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle
-// (and across warps through the group's exchange cells).  Gradient
-// increments accumulate in registers per checkpoint segment and are added
-// to per-slot totals in shared memory.
+// (and across warps through the group's exchange cells).  The coefficients
+// of step k-1 are evaluated while the dependent chain of step k runs.
+// Gradient increments accumulate in registers per checkpoint segment and
+// are added to per-slot totals in shared memory.
 // ---------------------------------------------------------------------------
 // Shared floats of one group: tape v/gap[/seed] [C][G*SL], totals [6][G*SL],
 // control area.
@@ -412,32 +453,35 @@ __host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, in
     return ((dense ? 2 : 3) * C + 6) * 32 * vpt * G + grp_ctrl_floats(G);
 }
 
-template <int VPT, bool DENSE, bool ADAM, bool WD, bool D4>
+__device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
+__device__ __forceinline__ void sts2(float *p, f2 x) { *reinterpret_cast<f2 *>(p) = x; }
+
+template <int NP, bool DENSE, bool ADAM, bool WD, bool D4>
 __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
-                                                 Grp &g, float *tv, const VehConst (&kc)[VPT], State (&st)[VPT],
-                                                 const bool (&valid)[VPT])
+                                                 Grp &g, float *tv, const VehConst2 (&kc)[NP], State2 (&st)[NP],
+                                                 const bool (&vx)[NP], const bool (&vy)[NP])
 {
-    constexpr int SL = 32 * VPT;
+    constexpr int SL = 64 * NP;
     const int SLG = SL * g.G;
     const int lane = g.lane;
-    const int wb = g.w * SL;                      // this warp's first slot in the group
+    const int wb = g.w * SL;                        // this warp's first slot in the group
     float *tg = tv + a.C * SLG;
-    float *tr = tg + a.C * SLG;                   // targets, then seeds (MSE only)
+    float *tr = tg + a.C * SLG;                     // targets, then seeds (MSE only)
     float *acc = tv + (DENSE ? 2 : 3) * a.C * SLG;  // gradient totals [6][SLG]
     const int Ns = sc.n_veh;
-    const int wl = lb + wb;                       // scenario-local index of this warp's first slot
+    const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
-    const float seed_scale = 2.0f * sc.inv_nobs;
+    const f2 seed_scale = F2(2.0f * sc.inv_nobs);
     int xp = 0, fp = 0;
     float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
 
-    float lp[VPT], lv[VPT];
+    f2 lp[NP], lv[NP];
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-        lp[j] = 0.0f;
-        lv[j] = 0.0f;
+    for (int p = 0; p < NP; ++p) {
+        lp[p] = F2(0.0f);
+        lv[p] = F2(0.0f);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q * SLG + wb + lane + 32 * j] = 0.0f;
+        for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
     }
 
     const int n_ck = (sc.K + a.C - 1) / a.C;
@@ -453,61 +497,69 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         if (!DENSE) {  // fetch the segment's observed targets into the seed tape
             const float *yrow = a.targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
             for (int k = obs_k, r = obs_row; k < c0 + n && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
-                prefetch_row<VPT>(tr + (k - c0) * SLG + wb, yrow, lane, valid);
+                prefetch_row<NP>(tr + (k - c0) * SLG + wb, yrow, lane, vx, vy);
             cp_async_commit();
         }
         {
             const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                if (!valid[j]) continue;
-                const int q = lane + 32 * j;
-                st[j] = State{base[q], base[(size_t)Ns + q], base[2 * (size_t)Ns + q], base[3 * (size_t)Ns + q]};
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                st[p].ph = load_pair(base, q, vx[p], vy[p]);
+                st[p].pl = load_pair(base + (size_t)Ns, q, vx[p], vy[p]);
+                const f2 v = load_pair(base + 2 * (size_t)Ns, q, vx[p], vy[p]);
+                const f2 gp = load_pair(base + 3 * (size_t)Ns, q, vx[p], vy[p]);
+                st[p].v = v;
+                st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
             }
         }
         if (!DENSE) cp_async_wait<0>();
-        float lseg = 0.0f;
+        f2 lseg = F2(0.0f);
         // recompute the segment into the tape
         for (int s = 0; s < n; ++s) {
             const int k = c0 + s;
             float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                rv[lane + 32 * j] = st[j].v;
-                rg[lane + 32 * j] = st[j].gap;
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                sts2(rv + q, st[p].v);
+                sts2(rg + q, st[p].gap);
             }
             if (!DENSE && k == obs_k) {
                 if (obs_row < sc.n_obs) {
                     float *rr = tr + s * SLG + wb;
 #pragma unroll
-                    for (int j = 0; j < VPT; ++j) {
-                        float r = valid[j] ? residual(st[j], rr[lane + 32 * j]) : 0.0f;
-                        rr[lane + 32 * j] = __fmul_rn(seed_scale, r);
-                        lseg = __fmaf_rn(r, r, lseg);
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], lds2(rr + q));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        sts2(rr + q, mul2(seed_scale, r));
+                        lseg = fma2(r, r, lseg);
                     }
                 }
                 obs_k += sc.obs_stride;
                 ++obs_row;
             }
-            float vcur[VPT], vh[VPT];
+            f2 vcur[NP], vh[NP];
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) vcur[j] = st[j].v;
-            const float lead_in = grp_lead_in<VPT>(g, vcur, xp);
-            leader_vals<VPT>(vcur, vh, lane, lead_in);
+            for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+            const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+            leader_vals2<NP>(vcur, vh, lane, lead_in);
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                float as = accel_star<D4>(st[j].v, st[j].gap, vh[j], kc[j], sc.inv_dt, sc.a_min);
-                euler(st[j], as, vh[j], dt);
+            for (int p = 0; p < NP; ++p) {
+                const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+                euler2(st[p], as, vh[p], dt);
             }
         }
         if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
             if (DENSE) {
                 const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
 #pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    lp[j] = a.gP[row + lane + 32 * j];
-                    lv[j] = a.gV ? a.gV[row + lane + 32 * j] : 0.0f;
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = load_pair(a.gP + row, q, vx[p], vy[p]);
+                    lv[p] = a.gV ? load_pair(a.gV + row, q, vx[p], vy[p]) : F2(0.0f);
                 }
             } else {
                 const int k = sc.K;
@@ -515,147 +567,160 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 if (obs) {
                     const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl;
 #pragma unroll
-                    for (int j = 0; j < VPT; ++j)
-                        if (valid[j]) {
-                            const float r = residual(st[j], __ldg(y + lane + 32 * j));
-                            lp[j] = __fmul_rn(seed_scale, r);
-                            kahan_add(lsum, lcomp, __fmul_rn(r, r));
-                        }
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], load_pair(y, q, vx[p], vy[p]));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        lp[p] = mul2(seed_scale, r);
+                        lseg = fma2(r, r, lseg);
+                    }
                 }
             }
         }
-        kahan_add(lsum, lcomp, lseg);
+        kahan_add(lsum, lcomp, __fadd_rn(lseg.x, lseg.y));
         grp_sync(g);  // the whole group's tape is written
 
-        float sacc[6][VPT];
+        f2 sacc[6][NP];
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) sacc[q][j] = 0.0f;
+            for (int p = 0; p < NP; ++p) sacc[q][p] = F2(0.0f);
 
         // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
         int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
         int obs_hi = row_hi * sc.obs_stride;
-        // The step-k coefficients do not depend on the adjoint, so those of
-        // step k-1 are evaluated while the dependent chain of step k runs.
-        AdjJac J[VPT];
+        AdjJac2 J[NP];
+        {
+            const float *rv = tv + (n - 1) * SLG + wb, *rg = tg + (n - 1) * SLG + wb;
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            const int q = wb + lane + 32 * j;
-            const float *rv = tv + (n - 1) * SLG, *rg = tg + (n - 1) * SLG;
-            J[j] = adjoint_jac<WD, D4>(rv[q], rg[q], q > 0 ? rv[q - 1] : 0.0f, kc[j], sc.inv_dt, sc.a_min);
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                const f2 v = lds2(rv + q);
+                const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+            }
         }
         for (int s = n - 1; s >= 0; --s) {
             const int k = c0 + s;
-            float own_p[VPT], own_v[VPT], to_lp[VPT], to_lv[VPT];
+            f2 to_lp[NP], to_lv[NP], t1[NP], nlv[NP];
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                const float mu = __fmul_rn(dt, lv[j]);
-                own_p[j] = mu * J[j].Ap;
-                own_v[j] = mu * J[j].Av;
-                to_lp[j] = -own_p[j];
-                to_lv[j] = mu * J[j].Avh;
-                sacc[0][j] += mu * J[j].w0;
-                sacc[1][j] += mu * J[j].w0v;
-                sacc[2][j] += mu * J[j].w0vdv;
-                sacc[3][j] += mu * J[j].fa;
-                sacc[4][j] += mu * J[j].frd;
-                if (WD) sacc[5][j] += mu * J[j].frdl;
+            for (int p = 0; p < NP; ++p) {
+                const f2 mu = mul2(F2(dt), lv[p]);
+                to_lp[p] = mul2(mu, J[p].Aph);
+                to_lv[p] = mul2(mu, J[p].Avh);
+                t1[p] = sub2(lp[p], to_lp[p]);                          // lp + mu A_p
+                nlv[p] = fma2(mu, J[p].Av, fma2(F2(dt), lp[p], lv[p]));  // dt lp + lv + mu A_v
+                sacc[0][p] = fma2(mu, J[p].w0n, sacc[0][p]);
+                sacc[1][p] = fma2(mu, J[p].w0nv, sacc[1][p]);
+                sacc[2][p] = fma2(mu, J[p].w0nvdv, sacc[2][p]);
+                sacc[3][p] = fma2(mu, J[p].fa, sacc[3][p]);
+                sacc[4][p] = fma2(mu, J[p].frd, sacc[4][p]);
+                if (WD) sacc[5][p] = fma2(mu, J[p].frdl, sacc[5][p]);
             }
             if (s > 0) {
-                const float *rv = tv + (s - 1) * SLG, *rg = tg + (s - 1) * SLG;
+                const float *rv = tv + (s - 1) * SLG + wb, *rg = tg + (s - 1) * SLG + wb;
 #pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    const int q = wb + lane + 32 * j;
-                    J[j] = adjoint_jac<WD, D4>(rv[q], rg[q], q > 0 ? rv[q - 1] : 0.0f, kc[j], sc.inv_dt, sc.a_min);
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    const f2 v = lds2(rv + q);
+                    const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
                 }
             }
             float in_p, in_v;
-            grp_follow_in(g, to_lp[0], to_lv[0], in_p, in_v, fp);
-            float from_p[VPT], from_v[VPT];
-            follower_vals<VPT>(to_lp, from_p, lane, in_p);
-            follower_vals<VPT>(to_lv, from_v, lane, in_v);
-            float seed_p[VPT], seed_v[VPT];
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) { seed_p[j] = 0.0f; seed_v[j] = 0.0f; }
+            grp_follow_in(g, to_lp[0].x, to_lv[0].x, in_p, in_v, fp);
+            f2 from_p[NP], from_v[NP];
+            follower_vals2<NP>(to_lp, from_p, lane, in_p);
+            follower_vals2<NP>(to_lv, from_v, lane, in_v);
             if (DENSE) {
                 const size_t row = sc.traj_off + (size_t)k * Ns + wl;
 #pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    if (!valid[j]) continue;
-                    seed_p[j] = a.gP[row + lane + 32 * j];
-                    if (a.gV) seed_v[j] = a.gV[row + lane + 32 * j];
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = add2(add2(t1[p], from_p[p]), load_pair(a.gP + row, q, vx[p], vy[p]));
+                    lv[p] = add2(nlv[p], from_v[p]);
+                    if (a.gV) lv[p] = add2(lv[p], load_pair(a.gV + row, q, vx[p], vy[p]));
                 }
-            } else if (k == obs_hi) {
-                if (k >= 1 && row_hi <= sc.n_obs) {
-                    const float *rr = tr + s * SLG + wb;
+            } else if (k == obs_hi && k >= 1 && row_hi <= sc.n_obs) {
+                const float *rr = tr + s * SLG + wb;
 #pragma unroll
-                    for (int j = 0; j < VPT; ++j) seed_p[j] = rr[lane + 32 * j];
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(add2(t1[p], from_p[p]), lds2(rr + 64 * p + 2 * lane));
+                    lv[p] = add2(nlv[p], from_v[p]);
                 }
+            } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(t1[p], from_p[p]);
+                    lv[p] = add2(nlv[p], from_v[p]);
+                }
+            }
+            if (!DENSE && k == obs_hi) {
                 obs_hi -= sc.obs_stride;
                 --row_hi;
-            }
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                float nlp = lp[j] + own_p[j] + from_p[j] + seed_p[j];
-                float nlv = dt * lp[j] + lv[j] + own_v[j] + from_v[j] + seed_v[j];
-                lp[j] = nlp;
-                lv[j] = nlv;
             }
         }
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
-            for (int j = 0; j < VPT; ++j) acc[q * SLG + wb + lane + 32 * j] += sacc[q][j];
+            for (int p = 0; p < NP; ++p) {
+                float *ap = acc + q * SLG + wb + 64 * p + 2 * lane;
+                sts2(ap, add2(lds2(ap), sacc[q][p]));
+            }
         grp_sync(g);  // the tape may be overwritten by the next segment
     }
 
     // epilogue: parameter gradients from the factored sums
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < VPT; ++j) {
-        if (!valid[j]) continue;
-        const int q = wb + lane + 32 * j;
-        const int gi = sg.veh_begin + q;
-        const float v0 = a.v0[gi], b = a.b[gi];
-        const float am = kc[j].am, c = kc[j].c, dl = kc[j].delta;
-        const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
-        const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
-        float gr[6];
-        gr[0] = am * dl * A4 / v0;                 // v0
-        gr[1] = A1;                                // T
-        gr[2] = A0;                                // s0
-        gr[3] = A3 - A2 * c / (2.0f * am);         // a_max
-        gr[4] = -A2 * c / (2.0f * b);              // b
-        gr[5] = -am * A5;                          // delta
-        for (int p = 0; p < 6; ++p) bad |= !isfinite(gr[p]);
-        if (ADAM) {
-            const int it = a.iter;
-            const int t = it + 1;
-            const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
-            const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
-            float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
-                            const_cast<float *>(a.am), const_cast<float *>(a.b)};
+    for (int p = 0; p < NP; ++p) {
 #pragma unroll
-            for (int p = 0; p < 5; ++p) {
-                const size_t mi = (size_t)p * a.N_total + gi;
-                float m = 0.9f * a.adam_m[mi] + 0.1f * gr[p];
-                float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[p] * gr[p];
-                a.adam_m[mi] = m;
-                a.adam_v[mi] = vv;
-                float x = th[p][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
-                x = fminf(fmaxf(x, a.lo[p]), a.hi[p]);
-                th[p][gi] = x;
+        for (int c = 0; c < 2; ++c) {
+            if (!(c ? vy[p] : vx[p])) continue;
+            const int q = wb + 64 * p + 2 * lane + c;
+            const int gi = sg.veh_begin + q;
+            const float v0 = a.v0[gi], b = a.b[gi];
+            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
+            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
+            const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
+            const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+            float gr[6];
+            gr[0] = am * dl * A4 / v0;                 // v0
+            gr[1] = -A1;                               // T
+            gr[2] = -A0;                               // s0
+            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
+            gr[4] = A2 * cc / (2.0f * b);              // b
+            gr[5] = -am * A5;                          // delta
+            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
+            if (ADAM) {
+                const int it = a.iter;
+                const int t = it + 1;
+                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
+                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const size_t mi = (size_t)r * a.N_total + gi;
+                    float m = 0.9f * a.adam_m[mi] + 0.1f * gr[r];
+                    float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[r] * gr[r];
+                    a.adam_m[mi] = m;
+                    a.adam_v[mi] = vv;
+                    float x = th[r][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+                    x = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
+                    th[r][gi] = x;
+                }
+            } else {
+                if (a.g_v0) a.g_v0[gi] = gr[0];
+                if (a.g_T) a.g_T[gi] = gr[1];
+                if (a.g_s0) a.g_s0[gi] = gr[2];
+                if (a.g_am) a.g_am[gi] = gr[3];
+                if (a.g_b) a.g_b[gi] = gr[4];
+                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
+                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
+                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
             }
-        } else {
-            if (a.g_v0) a.g_v0[gi] = gr[0];
-            if (a.g_T) a.g_T[gi] = gr[1];
-            if (a.g_s0) a.g_s0[gi] = gr[2];
-            if (a.g_am) a.g_am[gi] = gr[3];
-            if (a.g_b) a.g_b[gi] = gr[4];
-            if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
-            if (a.g_p_init) a.g_p_init[gi] = lp[j];
-            if (a.g_v_init) a.g_v_init[gi] = lv[j];
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
@@ -669,6 +734,7 @@ template <int VPT, bool DENSE, bool ADAM, bool WD>
 __global__ void __launch_bounds__(256, (VPT <= 4 ? 2 : 1))
 backward_kernel(SimArgs a)
 {
+    constexpr int NP = VPT / 2;
     extern __shared__ float smem[];
     const int G = a.G;
     const int warp = threadIdx.x >> 5;
@@ -682,14 +748,14 @@ backward_kernel(SimArgs a)
         const Seg sg = a.seg[s_idx];
         const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
         const int lb = sg.veh_begin - sc.veh_begin;
-        VehConst kc[VPT];
-        State st[VPT];
-        bool valid[VPT];
-        load_vehicles<VPT>(a, sg, g.lane, g.w * 32 * VPT, kc, st, valid);
-        if (segment_is_d4<VPT>(kc, valid))
-            backward_segment<VPT, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, valid);
+        VehConst2 kc[NP];
+        State2 st[NP];
+        bool vx[NP], vy[NP];
+        load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
+        if (segment_is_d4<NP>(kc, vx, vy))
+            backward_segment<NP, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
         else
-            backward_segment<VPT, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, valid);
+            backward_segment<NP, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
     }
 }
 
@@ -727,7 +793,6 @@ cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, con
     FwdFlags f{traj, vtraj, ckpt};
     void *fn = nullptr;
     switch (vpt) {
-    case 1: fn = (void *)forward_kernel<1>; break;
     case 2: fn = (void *)forward_kernel<2>; break;
     case 4: fn = (void *)forward_kernel<4>; break;
     case 8: fn = (void *)forward_kernel<8>; break;
@@ -766,7 +831,6 @@ static void *backward_fn(bool dense, bool adam, bool wd)
 static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd)
 {
     switch (vpt) {
-    case 1: return backward_fn<1>(dense, adam, wd);
     case 2: return backward_fn<2>(dense, adam, wd);
     case 4: return backward_fn<4>(dense, adam, wd);
     case 8: return backward_fn<8>(dense, adam, wd);
@@ -794,7 +858,6 @@ int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool 
     void *fn = nullptr;
     if (!backward) {
         switch (vpt) {
-        case 1: fn = (void *)forward_kernel<1>; break;
         case 2: fn = (void *)forward_kernel<2>; break;
         case 4: fn = (void *)forward_kernel<4>; break;
         case 8: fn = (void *)forward_kernel<8>; break;

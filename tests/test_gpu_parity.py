@@ -149,7 +149,7 @@ def test_autograd_function(api):
 EDGE_COUNTS = [1, 2, 3, 33, 0, 17, 31, 32, 1, 5]
 
 
-@pytest.mark.parametrize("vpt,G,C", [(2, 1, 1), (2, 2, 7), (4, 4, 16), (1, 8, 5), (0, 0, 64), (4, 1, 8), (8, 2, 3)])
+@pytest.mark.parametrize("vpt,G,C", [(2, 1, 1), (2, 2, 7), (4, 4, 16), (2, 4, 5), (0, 0, 64), (4, 1, 8), (8, 2, 3)])
 def test_edge_lanes(api, vpt, G, C):
     rng = np.random.default_rng(104)
     sc = synth.make_scene(EDGE_COUNTS, rng)
@@ -286,15 +286,15 @@ def test_argument_errors(api):
 
 def test_device_status_lane_too_long(api):
     from paper_2412_16750_gb300 import lib
-    sc = synth.make_scene([40, 3], np.random.default_rng(111))
-    ctx = api.Context(vpt=1)
+    sc = synth.make_scene([70, 3], np.random.default_rng(111))
+    ctx = api.Context(vpt=2, warps_per_segment=1)
     scn = api.Scene(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]), 32)  # understated max_lane
     traj = api.simulate(cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 5, DT, ctx=ctx)
     rc, flags = ctx.status()
     assert rc == lib.IDM_ERR_LANE and flags & lib.IDM_STATUS_LANE_TOO_LONG
     # the short lane is still simulated
     P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], 5, DT, A_MIN)
-    np.testing.assert_allclose(traj[:, 40:].double().cpu().numpy(), P[:, 40:], atol=POS_TOL)
+    np.testing.assert_allclose(traj[:, 70:].double().cpu().numpy(), P[:, 70:], atol=POS_TOL)
     assert ctx.status()[0] == lib.IDM_OK  # cleared
 
 
