@@ -46,9 +46,9 @@ __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-// a - b as one fused op: b * (-1) + a is exact before its single rounding,
-// so the result equals the correctly rounded difference.
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }
+// a - b: the negation is exact, so each component is the correctly rounded
+// difference.
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ f2 ex2(f2 x) { return make_float2(ex2_approx(x.x), ex2_approx(x.y)); }
 __device__ __forceinline__ f2 lg2(f2 x) { return make_float2(lg2_approx(x.x), lg2_approx(x.y)); }
 __device__ __forceinline__ f2 rcp2(f2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
@@ -65,7 +65,7 @@ struct Soft2 {
 __device__ __forceinline__ Soft2 softplus2(f2 x)
 {
     Soft2 s;
-    s.e = ex2(mul2(vabs(x), F2(-LOG2E)));
+    s.e = make_float2(ex2_approx(fabsf(x.x) * -LOG2E), ex2_approx(fabsf(x.y) * -LOG2E));
     s.sp = fma2(lg2(add2(F2(1.0f), s.e)), F2(LN2), vmax(x, F2(0.0f)));
     return s;
 }
@@ -248,7 +248,7 @@ __device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const V
     bool bx, by;
     const f2 a_lb = lower_bound(mul2(v, F2(-inv_dt)), a_min, bx, by);
     const f2 x2 = sub2(a, a_lb);
-    const f2 e2 = ex2(mul2(vabs(x2), F2(-LOG2E)));
+    const f2 e2 = make_float2(ex2_approx(fabsf(x2.x) * -LOG2E), ex2_approx(fabsf(x2.y) * -LOG2E));
     f2 sig2, one_m_sig2;
     sigmoid2(x2, e2, sig2, one_m_sig2);
 
