@@ -193,23 +193,28 @@ def alu_peak_ginst(sm_mhz, n_sm):
 ADJ_OPS_PER_VS = 118.0
 
 
-def adjoint_traffic_per_vs():
-    """DRAM bytes per vehicle-step of the adjoint from the committed ncu
-    summary, or None if absent / taken on a different kernel source."""
+def adjoint_traffic(n_vehicles, K, ckpt):
+    """DRAM bytes of one adjoint launch from the committed ncu summary
+    (N K a + N b, captured at checkpoint interval 8), or None if absent,
+    taken on a different kernel source or for another interval."""
     path = os.path.join(ROOT, "profiles", "adjoint_kernel_2M.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or ckpt != 8:
         return None
     import hashlib
     src = open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_sim.cu"), "rb").read()
     src += open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_device.cuh"), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
-    got_sha, bytes_vs = None, None
+    got_sha, per_vs, per_v = None, None, 0.0
     for line in open(path):
         if line.startswith("kernel_source_sha256_16:"):
             got_sha = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_vehicle_step:"):
-            bytes_vs = float(line.split(":", 1)[1].strip())
-    return bytes_vs if (got_sha == sha and bytes_vs) else None
+            per_vs = float(line.split(":", 1)[1].strip())
+        if line.startswith("dram_bytes_per_vehicle:"):
+            per_v = float(line.split(":", 1)[1].strip())
+    if got_sha != sha or not per_vs:
+        return None
+    return n_vehicles * K * per_vs + n_vehicles * per_v
 
 
 def run_e2e(a, e2e_steps, step, barrier, max_over_ranks, stream, dev, u_lane, u_p, u_v, u_len, u_th, u_Y, s_th,
@@ -383,12 +388,12 @@ def run_gpu(a, rank, world, local_rank):
     achieved_ginst = ADJ_OPS_PER_VS * units_launch / (bwd_avg_ms * 1e-3) / 1e9
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_ginst = alu_peak_ginst(sm_mhz, n_sm)
-    tr_vs = adjoint_traffic_per_vs()
+    traffic = adjoint_traffic(N, K, a.ckpt)
     roofline = {
         "kernel": "backward_kernel (adjoint with checkpoint recompute + fused Adam)",
         "bound": "alu", "achieved": achieved_ginst, "peak": peak_ginst, "unit": "Ginstr/s (FP32 pipe)",
         "frac": achieved_ginst / peak_ginst,
-        "traffic": (tr_vs * units_launch) if tr_vs else None,
+        "traffic": traffic,
         "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, %s)" % (n_sm, sm_mhz, peak_kind),
         "ops_per_vehicle_step": ADJ_OPS_PER_VS,
         "avg_launch_ms": bwd_avg_ms,

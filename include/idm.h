@@ -55,6 +55,7 @@ extern "C" {
 #define IDM_STATUS_LANE_TOO_LONG 1u
 #define IDM_STATUS_BAD_LANE_OFF 2u
 #define IDM_STATUS_NONFINITE 4u
+#define IDM_STATUS_TIMEOUT 8u   /* a bounded device wait gave up (tensor-core kernels) */
 
 /* Gap floor (m): the gap is max(p_h - p - length_h, IDM_GAP_FLOOR), with zero
  * derivative below the floor.  The paper is silent on gaps <= 0. */
@@ -212,6 +213,21 @@ int idm_fit(idm_ctx_t *ctx, const idm_scene_t *scene, idm_params_t *params,
             const float *p_init, const float *v_init, const idm_sim_t *sim,
             const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
             const float *box_lo, const float *box_hi, double *loss_hist, void *stream);
+
+/* idm_fit that also scores every iterate against a second target set
+ * (no counterpart in the paper; used to measure the error of the fitted
+ * trajectory against the noise-free truth while fitting to noisy targets).
+ *   eval_targets (device, same layout as targets): second target set.
+ *   eval_hist (device out, double [n_iter]): the loss L of the parameters
+ *     before update t against eval_targets, computed by the same forward
+ *     that writes the checkpoints (no extra simulation).
+ * Both must be given, or both NULL (then this is idm_fit).  The updates are
+ * identical to idm_fit's. */
+int idm_fit_eval(idm_ctx_t *ctx, const idm_scene_t *scene, idm_params_t *params,
+                 const float *p_init, const float *v_init, const idm_sim_t *sim,
+                 const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
+                 const float *box_lo, const float *box_hi, double *loss_hist,
+                 const float *eval_targets, double *eval_hist, void *stream);
 
 /* ---- batched uneven scenarios ------------------------------------------ */
 

@@ -139,16 +139,25 @@ def loss_grad(theta, p_init, v_init, scene, K, dt, targets, obs_stride=1, a_min=
 
 
 def fit(theta, p_init, v_init, scene, K, dt, targets, obs_stride, n_iter, lr0=0.1, lr1=0.01,
-        box_lo=(20.0, 0.1, 1.0, 0.5, 0.1), box_hi=(60.0, 5.0, 10.0, 10.0, 5.0), a_min=-10.0, ctx=None):
+        box_lo=(20.0, 0.1, 1.0, 0.5, 0.1), box_hi=(60.0, 5.0, 10.0, 10.0, 5.0), a_min=-10.0, ctx=None,
+        eval_targets=None):
     """Adam fit of (v0, T, s0, a_max, b) in place on a float32 (6, N) CUDA
-    tensor; returns the float64 loss history (n_iter,)."""
+    tensor; returns the float64 loss history (n_iter,).  With eval_targets
+    (same layout as targets) returns (loss history, eval loss history): the
+    second is the loss of every iterate against eval_targets."""
     ctx = ctx or default_context()
     assert theta.is_cuda and theta.dtype == torch.float32 and theta.is_contiguous()
     p_init, v_init, targets = _f32(p_init), _f32(v_init), _f32(targets)
     hist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
-    lib.idm_fit(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
-                targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi, hist, _stream())
-    return hist[:n_iter]
+    if eval_targets is None:
+        lib.idm_fit(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                    targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi, hist, _stream())
+        return hist[:n_iter]
+    eval_targets = _f32(eval_targets)
+    ehist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
+    lib.idm_fit_eval(ctx.handle, scene.c(), lib.make_params(theta), p_init, v_init, lib.make_sim(K, dt, a_min),
+                     targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi, hist, eval_targets, ehist, _stream())
+    return hist[:n_iter], ehist[:n_iter]
 
 
 def layout(lane_id, pos, n_lanes, ctx=None):

@@ -243,11 +243,16 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
 
 int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
                   float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
-                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t))
+                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t),
+                  const float *eval_targets, double *eval_hist)
 {
     int rc;
     if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
     if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
+    const bool eval = eval_targets && eval_hist;
+    if (eval && (rc = ensure(c, c->eval_part, sizeof(double) * (size_t)c->seg.n / sizeof(Seg) * P.G_f + 8,
+                             "eval loss partials")))
+        return rc;
 
     SimArgs &a = P.a;
     a.adam_m = (float *)c->adam_m.p;
@@ -262,6 +267,8 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
         SimArgs a;
         int vpt, G, grid_f, grid_b, wpb, wpb_b, n_iter, profiling, loss_per_seg;
         const double *hist;
+        const float *eval_targets;
+        const double *eval_hist;
         unsigned char extra[64];
     } key;
     memset(&key, 0, sizeof key);
@@ -269,6 +276,8 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     key.vpt = P.vpt * 16 + P.vpt_f; key.G = P.G * 16 + P.G_f; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f;
     key.wpb_b = P.wpb_b; key.n_iter = n_iter; key.profiling = c->profiling; key.loss_per_seg = P.loss_per_seg;
     key.hist = loss_hist;
+    key.eval_targets = eval ? eval_targets : nullptr;
+    key.eval_hist = eval ? eval_hist : nullptr;
     if (extra_len > sizeof key.extra) extra_len = sizeof key.extra;
     if (extra_key) memcpy(key.extra, extra_key, extra_len);
     static_assert(sizeof(Key) <= sizeof(((idm_ctx *)0)->fit_key), "fit key too large");
@@ -291,8 +300,13 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
             e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) {
-                a.work = (int *)c->ctl.p + CTL_WORK_F;
-                e = idm::launch_forward(P.vpt_f, P.G_f, false, false, true, a, P.grid_f, P.wpb_f, cs);
+                SimArgs af = a;
+                af.work = (int *)c->ctl.p + CTL_WORK_F;
+                if (eval) {
+                    af.eval_targets = eval_targets;
+                    af.eval_part = (double *)c->eval_part.p;
+                }
+                e = idm::launch_forward(P.vpt_f, P.G_f, false, false, true, af, P.grid_f, P.wpb_f, cs);
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 1], cs, cudaEventRecordExternal);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 2], cs, cudaEventRecordExternal);
@@ -302,6 +316,8 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
             }
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it + 3], cs, cudaEventRecordExternal);
             if (e == cudaSuccess) e = finalize(c, P, it, loss_hist, cs);  // loss of the parameters before update it
+            if (e == cudaSuccess && eval)
+                e = idm::launch_loss_finalize((const double *)c->eval_part.p, a.n_seg, P.G_f, eval_hist + it, cs);
         }
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "capturing the fit"); }
@@ -527,7 +543,18 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
             const idm_sim_t *sim, const float *targets, int32_t obs_stride, int32_t n_iter, float lr0, float lr1,
             const float *box_lo, const float *box_hi, double *loss_hist, void *stream)
 {
+    return idm_fit_eval(c, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi,
+                        loss_hist, nullptr, nullptr, stream);
+}
+
+int idm_fit_eval(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const float *p_init,
+                 const float *v_init, const idm_sim_t *sim, const float *targets, int32_t obs_stride, int32_t n_iter,
+                 float lr0, float lr1, const float *box_lo, const float *box_hi, double *loss_hist,
+                 const float *eval_targets, double *eval_hist, void *stream)
+{
     if (!c) return IDM_ERR_ARG;
+    if ((eval_targets == nullptr) != (eval_hist == nullptr))
+        return fail(c, IDM_ERR_ARG, "eval_targets and eval_hist must be given together");
     int rc;
     if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
     if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
@@ -546,7 +573,7 @@ int idm_fit(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, const 
     if ((rc = backward_grid(c, &P, false, true, false, scene->n_lanes))) return rc;
     P.a.targets = targets;
     return run_fit_graph(c, P, n_iter, (size_t)scene->n_vehicles, box_lo, box_hi, lr0, lr1, loss_hist, nullptr, 0,
-                         st, single_finalize);
+                         st, single_finalize, eval_targets, eval_hist);
 }
 
 int idm_set_profiling(idm_ctx_t *c, int on)

@@ -46,7 +46,7 @@ struct idm_ctx {
     int G_req = 0;
     int C = 8;
     int wpb = 8;
-    idm::abi::Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor;
+    idm::abi::Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor, eval_part;
     idm::abi::Buf scen_tab, scen_seg_off, scen_seg_idx, lane_off_dev;  // batched scenarios
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t fit_exec = nullptr;
@@ -71,10 +71,13 @@ int check_params(idm_ctx *c, const idm_params_t *p, bool all);
 int forward_grid(idm_ctx *c, Prep *P, int L);
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L);
 // Capture (or reuse) the n_iter-iteration fit graph for plan P and launch it.
-// finalize(it, stream) enqueues the loss reduction of iteration it.
+// finalize(it, stream) enqueues the loss reduction of iteration it.  With
+// eval_targets and eval_hist set, each iteration's forward also records the
+// loss against eval_targets in eval_hist[it] (single scene only).
 int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
                   float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
-                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t));
+                  cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t),
+                  const float *eval_targets = nullptr, double *eval_hist = nullptr);
 
 }  // namespace abi
 }  // namespace idm

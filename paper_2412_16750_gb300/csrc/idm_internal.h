@@ -58,6 +58,10 @@ struct SimArgs {
     int N_total;
     float lr0, lr1;
     float lo[5], hi[5];
+    // forward only: squared error against a second target set (same layout
+    // as targets), per warp like loss_part; NULL = off
+    const float *eval_targets;
+    double *eval_part;
 };
 
 // Launchers (idm_sim.cu).  Return cudaError_t of the launch.

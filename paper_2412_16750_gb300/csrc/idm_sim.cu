@@ -347,11 +347,11 @@ __device__ __forceinline__ f2 load_pair(const float *base, int q, bool vx, bool 
 // adjoint's recompute, which evaluates the residuals anyway.)
 // ---------------------------------------------------------------------------
 struct FwdFlags {
-    bool traj, vtraj, ckpt;
+    bool traj, vtraj, ckpt, eval;
 };
 
 template <int NP, bool D4>
-__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int lb, Grp &g,
+__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
                                                 const VehConst2 (&kc)[NP], State2 (&st)[NP], const bool (&vx)[NP],
                                                 const bool (&vy)[NP], FwdFlags f)
 {
@@ -360,6 +360,8 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     const int wl = lb + g.w * 64 * NP;  // scenario-local index of this warp's first slot
     int next_ck = 0, ck_idx = 0;
     int xp = 0;
+    int obs_k = sc.obs_stride, obs_row = 0;  // next observed step and its target row (eval)
+    float esum = 0.0f, ecomp = 0.0f;         // squared residuals (eval), Kahan over observed steps
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
             float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
@@ -383,6 +385,22 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
                 if (f.vtraj) store_pair(a.vtraj + row, q, st[p].v, vx[p], vy[p]);
             }
         }
+        if (f.eval && k == obs_k) {
+            if (obs_row < sc.n_obs) {
+                const float *y = a.eval_targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
+                f2 e = F2(0.0f);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    f2 r = residual2(st[p], load_pair(y, 64 * p + 2 * lane, vx[p], vy[p]));
+                    r.x = vx[p] ? r.x : 0.0f;
+                    r.y = vy[p] ? r.y : 0.0f;
+                    e = fma2(r, r, e);
+                }
+                kahan_add(esum, ecomp, __fadd_rn(e.x, e.y));
+            }
+            obs_k += sc.obs_stride;
+            ++obs_row;
+        }
         if (k == sc.K) break;
 
         f2 vcur[NP], vh[NP];
@@ -403,6 +421,10 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
         if (vy[p] && !(isfinite(st[p].v.y) && isfinite(st[p].ph.y))) bad = true;
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (f.eval) {
+        const double part = warp_sum_double((double)esum - (double)ecomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.eval_part[(size_t)s_idx * g.G + g.w] = part;
+    }
 }
 
 template <int VPT>
@@ -427,9 +449,9 @@ forward_kernel(SimArgs a, FwdFlags f)
         bool vx[NP], vy[NP];
         load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
         if (segment_is_d4<NP>(kc, vx, vy))
-            forward_segment<NP, true>(a, sc, lb, g, kc, st, vx, vy, f);
+            forward_segment<NP, true>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
         else
-            forward_segment<NP, false>(a, sc, lb, g, kc, st, vx, vy, f);
+            forward_segment<NP, false>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
     }
 }
 
@@ -790,7 +812,7 @@ cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int 
 cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
                            cudaStream_t st)
 {
-    FwdFlags f{traj, vtraj, ckpt};
+    FwdFlags f{traj, vtraj, ckpt, a.eval_targets != nullptr && a.eval_part != nullptr};
     void *fn = nullptr;
     switch (vpt) {
     case 2: fn = (void *)forward_kernel<2>; break;

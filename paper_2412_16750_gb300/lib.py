@@ -86,6 +86,10 @@ _SIGS = {
                                ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                _vp, _vp]),
+    "idm_fit_eval": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                    ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                    _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -240,6 +244,15 @@ def idm_fit(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter
     return check(ctx, load().idm_fit(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
                                      ctypes.byref(sim), ptr(targets), obs_stride, n_iter, lr0, lr1, lo, hi,
                                      ptr(loss_hist), stream_ptr(stream)))
+
+
+def idm_fit_eval(ctx, scene, params, p_init, v_init, sim, targets, obs_stride, n_iter, lr0, lr1, box_lo, box_hi,
+                 loss_hist=None, eval_targets=None, eval_hist=None, stream=None):
+    lo = (ctypes.c_float * 5)(*box_lo)
+    hi = (ctypes.c_float * 5)(*box_hi)
+    return check(ctx, load().idm_fit_eval(ctx, ctypes.byref(scene), ctypes.byref(params), ptr(p_init), ptr(v_init),
+                                          ctypes.byref(sim), ptr(targets), obs_stride, n_iter, lr0, lr1, lo, hi,
+                                          ptr(loss_hist), ptr(eval_targets), ptr(eval_hist), stream_ptr(stream)))
 
 
 def idm_batch_sizes(batch, ckpt_interval=8):

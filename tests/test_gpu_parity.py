@@ -239,6 +239,55 @@ def test_fit_config0(api):
     np.testing.assert_allclose(th.double().cpu().numpy(), th_ref, rtol=1e-4, atol=1e-5)
 
 
+def test_fit_eval_history(api):
+    # idm_fit_eval: same updates as idm_fit; the eval history is the loss of
+    # each iterate against the second target set (here the clean truth,
+    # checked against the oracle at the iterates the oracle fit produces).
+    sc = synth.config0()
+    K, s = sc["K"], 2
+    P_true, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT,
+                               A_MIN)
+    clean = synth.f32(P_true[s::s][: K // s])
+    Y = noisy_targets(sc, K, s, np.random.default_rng(111))
+    n_iter = 4
+    th0 = synth.plain_init(1000)
+    ref_eval = []
+    for m in range(n_iter):  # iterate m of the n_iter schedule: replay the first m updates in the oracle
+        th_m = th0 if m == 0 else _oracle_fit_prefix(sc, th0, Y, K, s, n_iter, m)
+        Pm, _ = oracle.forward(sc["lane_off"], sc["length"], th_m, sc["p_init"], sc["v_init"], K, DT, A_MIN)
+        ref_eval.append(oracle.mse_seed(Pm, clean, s)[0])
+    th_a, th_b = cuda(th0), cuda(th0)
+    hist_a = api.fit(th_a, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, cuda(Y), s, n_iter)
+    hist_b, ev = api.fit(th_b, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, cuda(Y), s, n_iter,
+                         eval_targets=cuda(clean))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hist_a.cpu().numpy(), hist_b.cpu().numpy())
+    np.testing.assert_array_equal(th_a.cpu().numpy(), th_b.cpu().numpy())
+    np.testing.assert_allclose(ev.cpu().numpy(), np.array(ref_eval), rtol=1e-4)
+    # with the fitting targets as the second set, both histories agree
+    th_c = cuda(th0)
+    hist_c, ev_c = api.fit(th_c, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT, cuda(Y), s,
+                           n_iter, eval_targets=cuda(Y))
+    np.testing.assert_allclose(ev_c.cpu().numpy(), hist_c.cpu().numpy(), rtol=1e-5)
+
+
+def _oracle_fit_prefix(sc, th0, Y, K, s, n_iter, m):
+    """Parameters after the first m Adam updates of an n_iter-iteration fit
+    (oracle steps with the n_iter learning-rate schedule)."""
+    th = np.array(th0, dtype=np.float64, copy=True)
+    N = th.shape[1]
+    m1, v1 = np.zeros((5, N)), np.zeros((5, N))
+    for it in range(m):
+        P, V = oracle.forward(sc["lane_off"], sc["length"], th, sc["p_init"], sc["v_init"], K, DT, A_MIN)
+        _, gP = oracle.mse_seed(P, Y, s)
+        g, _, _ = oracle.adjoint(sc["lane_off"], sc["length"], th, K, DT, P, V, gP, None, A_MIN)
+        th5 = np.ascontiguousarray(th[:5])
+        oracle.adam_step(th5, np.ascontiguousarray(g[:5]), m1, v1, it + 1, oracle.lr_schedule(it, n_iter, 0.1, 0.01),
+                         synth.BOX_LO, synth.BOX_HI)
+        th[:5] = th5
+    return th
+
+
 def test_layout_bitexact(api):
     rng = np.random.default_rng(109)
     N, L = 20000, 613
