@@ -15,3 +15,4 @@ from .ref import (  # noqa: F401
     layout,
     PARAM_NAMES,
 )
+from . import mlp_oracle  # noqa: F401,E402

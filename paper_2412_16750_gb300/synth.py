@@ -163,3 +163,43 @@ def unsorted_view(sc, rng):
     lane_id = np.repeat(np.arange(len(lane_off) - 1, dtype=np.int32), np.diff(lane_off))
     order = rng.permutation(N)
     return dict(lane_id=lane_id[order], p_init=sc["p_init"][order], order=order)
+
+
+# ---------------------------------------------------------------------------
+# Learned initializer (no counterpart in the paper)
+# ---------------------------------------------------------------------------
+
+# (fan_in, fan_out) of the four layers 80 -> 256 -> 256 -> 256 -> 5.
+MLP_SIZES = ((80, 256), (256, 256), (256, 256), (256, 5))
+
+
+def mlp_init(seed=0):
+    """Flat initial weights (float32-exact float64), in the order W1, b1, ...,
+    W4, b4 with W stored row = output unit: every entry uniform in
+    [-1/sqrt(fan_in), 1/sqrt(fan_in)]."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 3 + 1000 * seed))
+    parts = []
+    for fan_in, fan_out in MLP_SIZES:
+        bound = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
+        parts.append(rng.uniform(-bound, bound, size=fan_out))
+    return f32(np.concatenate(parts))
+
+
+def config3_train(n_lanes=100000, per_lane=100, K=20, seed=0):
+    """Training scenes of the initializer: 100,000 lanes x 100 vehicles (10M
+    samples) with the config-0 parameter and state ranges, simulated for the
+    20-step observed prefix."""
+    rng = rng_for(3, salt=1 + seed)
+    sc = make_scene([per_lane] * n_lanes, rng)
+    sc.update(K=K, dt=0.1, obs_stride=1, name="%dx%d K=%d (initializer training)" % (n_lanes, per_lane, K))
+    return sc
+
+
+def config3_fit(n_lanes=2000, per_lane=100, K=100):
+    """Fit scenes of the initializer experiment: 2,000 lanes x 100 vehicles
+    (200K), 100 steps, every step observed."""
+    rng = rng_for(3)
+    sc = make_scene([per_lane] * n_lanes, rng)
+    sc.update(K=K, dt=0.1, obs_stride=1, name="%dx%d K=%d" % (n_lanes, per_lane, K))
+    return sc
