@@ -267,3 +267,102 @@ class IdmFunction(torch.autograd.Function):
         scene, K, dt, a_min, ctx = fctx.cfg
         g, gp, gv = backward(theta, p_init, v_init, scene, K, dt, gtraj.contiguous(), None, a_min, ctx=ctx)
         return g, gp, gv, None, None, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# Learned initializer (include/idm_mlp.h; no counterpart in the paper)
+# ---------------------------------------------------------------------------
+
+BOX_LO = (20.0, 0.1, 1.0, 0.5, 0.1)
+BOX_HI = (60.0, 5.0, 10.0, 10.0, 5.0)
+
+
+class Mlp:
+    """The 80-256-256-256-5 GELU network of the learned initializer: bf16
+    weights on the tensor cores, FP32 master weights and Adam state."""
+
+    def __init__(self, max_batch=8192, weights=None):
+        self.handle = lib.idm_mlp_create(max_batch)
+        self.max_batch = max_batch
+        if weights is not None:
+            self.set_weights(weights)
+
+    def set_weights(self, w):
+        w = torch.as_tensor(w).to(device="cuda", dtype=torch.float32).contiguous()
+        assert w.numel() == lib.IDM_MLP_N_PARAMS
+        lib.idm_mlp_set_weights(self.handle, w, _stream())
+        torch.cuda.current_stream().synchronize()  # the copy source may be a temporary
+
+    def get_weights(self):
+        w = torch.empty(lib.IDM_MLP_N_PARAMS, device="cuda", dtype=torch.float32)
+        lib.idm_mlp_get_weights(self.handle, w, _stream())
+        return w
+
+    def forward(self, X):
+        """sigmoid outputs (B, 5) of bf16 features X (B, 80)."""
+        B = X.shape[0]
+        out = torch.empty((B, 5), device="cuda", dtype=torch.float32)
+        lib.idm_mlp_forward(self.handle, _bf16(X), B, out, _stream())
+        return out
+
+    def predict_params(self, X, theta, box_lo=BOX_LO, box_hi=BOX_HI):
+        """Writes rows 0-4 (v0, T, s0, a_max, b) of the (6, B) tensor theta."""
+        assert theta.is_cuda and theta.dtype == torch.float32 and theta.is_contiguous()
+        B = X.shape[0]
+        lib.idm_mlp_predict_params(self.handle, _bf16(X), B, lib.make_params(theta), box_lo, box_hi, _stream())
+        return theta
+
+    def loss_grad(self, X, labels):
+        B = X.shape[0]
+        loss = torch.zeros((), device="cuda", dtype=torch.float64)
+        grad = torch.empty(lib.IDM_MLP_N_PARAMS, device="cuda", dtype=torch.float32)
+        lib.idm_mlp_loss_grad(self.handle, _bf16(X), _f32(labels), B, loss, grad, _stream())
+        return loss, grad
+
+    def train_step(self, X, labels, lr):
+        loss = torch.zeros((), device="cuda", dtype=torch.float64)
+        lib.idm_mlp_train_step(self.handle, _bf16(X), _f32(labels), X.shape[0], lr, loss, _stream())
+        return loss
+
+    def train(self, X, labels, batch, n_steps, lr0=1e-3, lr1=1e-4):
+        """n_steps Adam steps over consecutive batches of (X, labels); returns
+        the loss history (float64, n_steps)."""
+        hist = torch.zeros(max(n_steps, 1), device="cuda", dtype=torch.float64)
+        lib.idm_mlp_train(self.handle, _bf16(X), _f32(labels), X.shape[0], batch, n_steps, lr0, lr1, hist,
+                          _stream())
+        return hist[:n_steps]
+
+    def status(self):
+        return lib.idm_mlp_status(self.handle, _stream())
+
+    def close(self):
+        if self.handle is not None:
+            lib.idm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bf16(t):
+    assert t.is_cuda and t.dtype == torch.bfloat16 and t.is_contiguous()
+    return t
+
+
+def mlp_features(scene, p_init, v_init, K, dt, targets, obs_stride=1, perm=None, theta=None, box_lo=BOX_LO,
+                 box_hi=BOX_HI):
+    """Feature rows (bf16 (n, 80)) of the vehicles perm (default all); with
+    theta (6, N) also the normalized labels (n, 5)."""
+    p_init, v_init, targets = _f32(p_init), _f32(v_init), _f32(targets)
+    perm_t = perm.to(device="cuda", dtype=torch.int32).contiguous() if perm is not None else None
+    n = perm_t.numel() if perm_t is not None else scene.n_vehicles
+    X = torch.empty((n, lib.IDM_MLP_IN), device="cuda", dtype=torch.bfloat16)
+    labels = None
+    if theta is not None:
+        labels = torch.empty((n, 5), device="cuda", dtype=torch.float32)
+    lib.idm_mlp_features(scene.c(), p_init, v_init, lib.make_sim(K, dt, -10.0), targets, obs_stride, perm_t, n, X,
+                         lib.make_params(theta) if theta is not None else None, labels, box_lo, box_hi, _stream())
+    return (X, labels) if theta is not None else X

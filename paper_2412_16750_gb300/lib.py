@@ -21,6 +21,13 @@ IDM_ERR_LANE = 6
 IDM_STATUS_LANE_TOO_LONG = 1
 IDM_STATUS_BAD_LANE_OFF = 2
 IDM_STATUS_NONFINITE = 4
+IDM_STATUS_TIMEOUT = 8
+
+IDM_MLP_IN = 80
+IDM_MLP_HIDDEN = 256
+IDM_MLP_OUT = 5
+IDM_MLP_PREFIX = 20
+IDM_MLP_N_PARAMS = 153605
 
 GAP_FLOOR = 0.1
 
@@ -86,6 +93,24 @@ _SIGS = {
                                ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                _vp, _vp]),
+    # learned initializer (include/idm_mlp.h)
+    "idm_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]),
+    "idm_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32]),
+    "idm_mlp_destroy": (ctypes.c_int, [_vp]),
+    "idm_mlp_last_error": (ctypes.c_char_p, [_vp]),
+    "idm_mlp_set_weights": (ctypes.c_int, [_vp, _vp, _vp]),
+    "idm_mlp_get_weights": (ctypes.c_int, [_vp, _vp, _vp]),
+    "idm_mlp_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "idm_mlp_features": (ctypes.c_int, [ctypes.POINTER(idm_scene_t), _vp, _vp, ctypes.POINTER(idm_sim_t), _vp,
+                                        ctypes.c_int32, _vp, ctypes.c_int32, _vp, ctypes.POINTER(idm_params_t), _vp,
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _vp]),
+    "idm_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
+    "idm_mlp_predict_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(idm_params_t),
+                                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _vp]),
+    "idm_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
+    "idm_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp]),
+    "idm_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_float, _vp, _vp]),
     "idm_fit_eval": (ctypes.c_int, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_params_t), _vp, _vp,
                                     ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                     ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -300,3 +325,87 @@ def make_params(theta):
 
 def make_sim(K, dt, a_min=-10.0):
     return idm_sim_t(int(K), float(dt), float(a_min))
+
+
+# ---- learned initializer (include/idm_mlp.h) --------------------------------
+
+def _box(v):
+    return (ctypes.c_float * 5)(*v) if v is not None else None
+
+
+def mcheck(mlp, rc):
+    if rc != IDM_OK:
+        msg = load().idm_mlp_last_error(mlp)
+        raise IdmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def idm_gemm_bf16(A, B, M, N, K, C, status, stream=None):
+    """Raw status code (no object to hold a message)."""
+    return load().idm_gemm_bf16(ptr(A), ptr(B), M, N, K, ptr(C), ptr(status), stream_ptr(stream))
+
+
+def idm_mlp_create(max_batch):
+    h = _vp()
+    rc = load().idm_mlp_create(ctypes.byref(h), max_batch)
+    if rc != IDM_OK:
+        raise IdmError(rc, "idm_mlp_create failed")
+    return h
+
+
+def idm_mlp_destroy(mlp):
+    return load().idm_mlp_destroy(mlp)
+
+
+def idm_mlp_last_error(mlp):
+    m = load().idm_mlp_last_error(mlp)
+    return m.decode() if m else ""
+
+
+def idm_mlp_set_weights(mlp, weights, stream=None):
+    return mcheck(mlp, load().idm_mlp_set_weights(mlp, ptr(weights), stream_ptr(stream)))
+
+
+def idm_mlp_get_weights(mlp, weights, stream=None):
+    return mcheck(mlp, load().idm_mlp_get_weights(mlp, ptr(weights), stream_ptr(stream)))
+
+
+def idm_mlp_status(mlp, stream=None):
+    bits = ctypes.c_uint32(0)
+    rc = load().idm_mlp_status(mlp, stream_ptr(stream), ctypes.byref(bits))
+    return rc, bits.value
+
+
+def idm_mlp_features(scene, p_init, v_init, sim, targets, obs_stride, perm, n_rows, X, label_params=None,
+                     labels=None, box_lo=None, box_hi=None, stream=None):
+    rc = load().idm_mlp_features(ctypes.byref(scene), ptr(p_init), ptr(v_init), ctypes.byref(sim), ptr(targets),
+                                 obs_stride, ptr(perm), n_rows, ptr(X),
+                                 ctypes.byref(label_params) if label_params is not None else None, ptr(labels),
+                                 _box(box_lo), _box(box_hi), stream_ptr(stream))
+    if rc != IDM_OK:
+        raise IdmError(rc, "idm_mlp_features: bad arguments")
+    return rc
+
+
+def idm_mlp_forward(mlp, X, B, out, stream=None):
+    return mcheck(mlp, load().idm_mlp_forward(mlp, ptr(X), B, ptr(out), stream_ptr(stream)))
+
+
+def idm_mlp_predict_params(mlp, X, B, params, box_lo, box_hi, stream=None):
+    return mcheck(mlp, load().idm_mlp_predict_params(mlp, ptr(X), B, ctypes.byref(params), _box(box_lo),
+                                                     _box(box_hi), stream_ptr(stream)))
+
+
+def idm_mlp_loss_grad(mlp, X, labels, B, loss_out, grad, stream=None):
+    return mcheck(mlp, load().idm_mlp_loss_grad(mlp, ptr(X), ptr(labels), B, ptr(loss_out), ptr(grad),
+                                                stream_ptr(stream)))
+
+
+def idm_mlp_train_step(mlp, X, labels, B, lr, loss_out=None, stream=None):
+    return mcheck(mlp, load().idm_mlp_train_step(mlp, ptr(X), ptr(labels), B, lr, ptr(loss_out),
+                                                 stream_ptr(stream)))
+
+
+def idm_mlp_train(mlp, X, labels, n_samples, batch, n_steps, lr0, lr1, loss_hist=None, stream=None):
+    return mcheck(mlp, load().idm_mlp_train(mlp, ptr(X), ptr(labels), n_samples, batch, n_steps, lr0, lr1,
+                                            ptr(loss_hist), stream_ptr(stream)))

@@ -1,5 +1,5 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports
-every entry point include/idm.h declares.  No compute call is made."""
+every entry point include/*.h declares.  No compute call is made."""
 import ctypes
 import os
 import re
@@ -10,7 +10,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "idm.h")).read()
+    src = ""
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", name)).read() + "\n"
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|int|size_t)\s*\**\s*(idm_\w+)\s*\(", src, flags=re.M)))
 
