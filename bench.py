@@ -62,6 +62,14 @@ def parse():
     p.add_argument("--G", type=int, default=8, help="warps per segment")
     p.add_argument("--ckpt", type=int, default=8)
     p.add_argument("--wpb", type=int, default=8)
+    # learned-versus-plain initial guess (time to fit 0.5 m RMSE)
+    p.add_argument("--no-init-experiment", action="store_true")
+    p.add_argument("--init-only", action="store_true", help="run only the initializer experiment")
+    p.add_argument("--init-train-lanes", type=int, default=100000, help="x 100 vehicles = training samples")
+    p.add_argument("--mlp-batch", type=int, default=8192)
+    p.add_argument("--mlp-epochs", type=int, default=2)
+    p.add_argument("--fit-iters", type=int, default=500)
+    p.add_argument("--rmse-target", type=float, default=0.5)
     return p.parse_args()
 
 
@@ -253,6 +261,139 @@ def run_e2e(a, e2e_steps, step, barrier, max_over_ranks, stream, dev, u_lane, u_
     return ms, h2d, d2h
 
 
+# Algorithmic FLOPs of one training sample of the initializer (forward,
+# input-gradient of layers 2-4, weight gradients; the 5-wide output layer
+# counted at its real width).
+MLP_FWD_FLOP = 2 * (80 * 256 + 256 * 256 + 256 * 256 + 256 * 5)
+MLP_TRAIN_FLOP = 2 * MLP_FWD_FLOP + 2 * (256 * 5 + 2 * 256 * 256)
+
+
+def time_to_fit(a, dev):
+    """Initializer experiment: train the network on simulated noisy 20-step
+    prefixes, then fit a 200K-vehicle scene (2,000 lanes x 100, 100 steps,
+    every step observed, noise 0.5 m) from the learned and from the plain
+    initial guess with the same Adam schedule; report iterations and wall
+    time until the fitted trajectory is within --rmse-target (RMSE against
+    the noise-free truth) and the network's training throughput."""
+    import torch
+    from paper_2412_16750_gb300 import api, synth
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20241216 + 3)
+    out = {}
+
+    # ---- training set ------------------------------------------------------
+    tr = synth.config3_train(n_lanes=a.init_train_lanes)
+    Ntr = int(tr["lane_off"][-1])
+    scene = api.Scene.from_lane_off(cu(tr["lane_off"], torch.int32), cu(tr["length"]), 100)
+    th = cu(tr["theta_true"])
+    p0, v0 = cu(tr["p_init"]), cu(tr["v_init"])
+    del tr
+    P = api.simulate(th, p0, v0, scene, 20, DT)
+    Y = P[1:]
+    Y.add_(0.5 * torch.randn(Y.shape, device=dev, generator=gen))
+    perm = torch.randperm(Ntr, device=dev, generator=gen).to(torch.int32)
+    X, lab = api.mlp_features(scene, p0, v0, 20, DT, Y, 1, perm=perm, theta=th)
+    del P, Y, perm, th, p0, v0, scene
+    torch.cuda.empty_cache()
+    net = api.Mlp(max_batch=a.mlp_batch, weights=synth.mlp_init(0))
+    n_steps = a.mlp_epochs * (Ntr // a.mlp_batch)
+    net.train(X, lab, a.mlp_batch, 20, 2e-3, 2e-3)          # warm-up (modules, caches)
+    net.set_weights(synth.mlp_init(0))
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    hist = net.train(X, lab, a.mlp_batch, n_steps, 2e-3, 2e-4)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    rc, bits = net.status()
+    if rc != 0:
+        raise RuntimeError("initializer status %d bits %d" % (rc, bits))
+    samples = n_steps * a.mlp_batch
+    label_mean = lab.double().mean(0).cpu().numpy()
+    label_var = float(lab.double().var(0).mean().item())     # MSE of the best input-free guess
+    del X, lab
+    torch.cuda.empty_cache()
+    out["mlp"] = {"train_samples": Ntr, "epochs": a.mlp_epochs, "batch": a.mlp_batch, "steps": n_steps,
+                  "train_s": train_ms / 1e3, "samples_per_s": samples / (train_ms / 1e3),
+                  "tflops": MLP_TRAIN_FLOP * samples / (train_ms / 1e3) / 1e12,
+                  "flop_per_sample": MLP_TRAIN_FLOP,
+                  "loss_first": float(hist[:10].mean().item()), "loss_last": float(hist[-10:].mean().item()),
+                  "label_variance": label_var}
+
+    # ---- fit scene ---------------------------------------------------------------
+    fs = synth.config3_fit()
+    N, K = int(fs["lane_off"][-1]), fs["K"]
+    scene = api.Scene.from_lane_off(cu(fs["lane_off"], torch.int32), cu(fs["length"]), 100)
+    th_true = cu(fs["theta_true"])
+    p0, v0 = cu(fs["p_init"]), cu(fs["v_init"])
+    P = api.simulate(th_true, p0, v0, scene, K, DT)
+    clean = P[1:].contiguous()
+    Y = (clean + 0.5 * torch.randn(clean.shape, device=dev, generator=gen)).contiguous()
+    plain = cu(synth.plain_init(N))
+    ctx = api.Context()
+    th_buf = torch.empty_like(plain)
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    # per-iteration time of the fit (graph captured by the first call)
+    for _ in range(2):
+        th_buf.copy_(plain)
+        _, fit_ms = timed(lambda: api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx))
+    ms_iter = fit_ms / a.fit_iters
+
+    def first_below(ev_hist):
+        rmse = np.sqrt(ev_hist.cpu().numpy() / N)
+        hit = np.nonzero(rmse <= a.rmse_target)[0]
+        return (int(hit[0]) if hit.size else None), rmse
+
+    th_buf.copy_(plain)
+    _, ev_plain = api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx, eval_targets=clean)
+    it_plain, rmse_plain = first_below(ev_plain)
+    # learned initial guess: features of the first 20 observations + inference
+    for _ in range(2):
+        th_buf.copy_(plain)
+        _, init_ms = timed(lambda: net.predict_params(
+            api.mlp_features(scene, p0, v0, K, DT, Y, 1), th_buf))
+    _, ev_learned = api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx, eval_targets=clean)
+    it_learned, rmse_learned = first_below(ev_learned)
+    # ablation: every vehicle starts at the mean of the training labels (what
+    # the network could know without looking at the trajectories)
+    lo, hi = np.array(synth.BOX_LO), np.array(synth.BOX_HI)
+    mean_th = synth.plain_init(N)
+    mean_th[:5] = (lo + (hi - lo) * label_mean)[:, None]
+    th_buf.copy_(cu(mean_th))
+    _, ev_mean = api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx, eval_targets=clean)
+    it_mean, rmse_mean = first_below(ev_mean)
+    wall = lambda it, extra: (extra + it * ms_iter) / 1e3 if it is not None else None
+    out["fit"] = {"workload": "2000 lanes x 100 vehicles (200K), 100 steps, every step observed, noise 0.5 m; "
+                              "Adam %d iterations, lr 0.1 -> 0.01" % a.fit_iters,
+                  "rmse_target_m": a.rmse_target, "ms_per_iteration": ms_iter,
+                  "plain": {"iterations": it_plain, "seconds": wall(it_plain, 0.0),
+                            "rmse_m_at": {str(i): float(rmse_plain[i]) for i in (0, 10, 50, 100, a.fit_iters - 1)
+                                          if i < a.fit_iters}},
+                  "learned": {"iterations": it_learned, "seconds": wall(it_learned, init_ms),
+                              "init_ms": init_ms,
+                              "rmse_m_at": {str(i): float(rmse_learned[i])
+                                            for i in (0, 10, 50, 100, a.fit_iters - 1) if i < a.fit_iters}},
+                  "training_mean_ablation": {"iterations": it_mean, "seconds": wall(it_mean, 0.0),
+                                             "rmse_m_at": {str(i): float(rmse_mean[i])
+                                                           for i in (0, 10, 50, 100, a.fit_iters - 1)
+                                                           if i < a.fit_iters}}}
+    ctx.close()
+    net.close()
+    return out
+
+
 def run_gpu(a, rank, world, local_rank):
     import torch
     from paper_2412_16750_gb300 import api, lib, synth
@@ -263,6 +404,11 @@ def run_gpu(a, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if a.init_only:
+        if rank == 0:
+            print(json.dumps({"time_to_fit": time_to_fit(a, dev)}), flush=True)
+        return 0
 
     # ---- synthetic batch (seeded per rank), unsorted arrival order -------
     rng = synth.rng_for(1, rank)
@@ -419,6 +565,8 @@ def run_gpu(a, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
     }
+    if world == 1 and not a.no_init_experiment:
+        line["time_to_fit"] = time_to_fit(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, secs, desc = oracle_sample(iters=30)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
