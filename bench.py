@@ -70,6 +70,16 @@ def parse():
     p.add_argument("--mlp-epochs", type=int, default=2)
     p.add_argument("--fit-iters", type=int, default=500)
     p.add_argument("--rmse-target", type=float, default=0.5)
+    # batched uneven scenarios (one graph-captured launch per fit iteration)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-only", action="store_true", help="run only the batched-scenario measurement")
+    p.add_argument("--batch-scen", type=int, default=4096)
+    p.add_argument("--batch-iters", type=int, default=20)
+    # long horizon: fit on the first 2,000 of 3,000 steps, predict the rest
+    p.add_argument("--no-long-horizon", action="store_true")
+    p.add_argument("--long-only", action="store_true", help="run only the initializer + long-horizon measurement")
+    p.add_argument("--long-lanes", type=int, default=20000)
+    p.add_argument("--long-iters", type=int, default=50)
     return p.parse_args()
 
 
@@ -394,6 +404,139 @@ def time_to_fit(a, dev):
     return out
 
 
+def long_horizon(a, dev, net):
+    """2M vehicles, 3,000 steps: fit (v0, T, s0, a_max, b) on noisy
+    observations of steps 1..2,000 from the learned initial guess with
+    --long-iters Adam iterations (checkpoints every 45 steps, about
+    sqrt(2000)), then simulate all 3,000 steps with the fitted parameters
+    and score steps 2,001..3,000 against the truth; sampled lanes are
+    re-simulated by the FP64 oracle with the same fitted parameters."""
+    import torch
+    import oracle
+    from paper_2412_16750_gb300 import api, synth
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20241216 + 4)
+    K_fit, K_all, C = 2000, 3000, 45
+    sc = synth.make_scene([100] * a.long_lanes, synth.rng_for(4))
+    N = int(sc["lane_off"][-1])
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    scene = api.Scene.from_lane_off(cu(sc["lane_off"], torch.int32), cu(sc["length"]), 100)
+    p0, v0 = cu(sc["p_init"]), cu(sc["v_init"])
+    ctx = api.Context(ckpt_interval=C)
+    truth = api.simulate(cu(sc["theta_true"]), p0, v0, scene, K_all, DT, ctx=ctx)
+    Y = (truth[1:K_fit + 1] + 0.5 * torch.randn((K_fit, N), device=dev, generator=gen)).contiguous()
+    th = cu(synth.plain_init(N))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    net.predict_params(api.mlp_features(scene, p0, v0, K_fit, DT, Y, 1), th)
+    e[1].record(stream)
+    hist = api.fit(th, p0, v0, scene, K_fit, DT, Y, 1, a.long_iters, ctx=ctx)
+    e[2].record(stream)
+    pred = api.simulate(th, p0, v0, scene, K_all, DT, ctx=ctx)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    rc, flags = ctx.status()
+    if rc != 0:
+        raise RuntimeError("long-horizon status %d flags %d" % (rc, flags))
+    peak = torch.cuda.max_memory_allocated(dev)
+    ws = lib_workspace(ctx, scene, K_fit)
+    err = (pred[K_fit + 1:] - truth[K_fit + 1:]).double()
+    rmse_pred = float(torch.sqrt((err * err).mean()).item())
+    err_fit = (pred[1:K_fit + 1] - truth[1:K_fit + 1]).double()
+    rmse_fit = float(torch.sqrt((err_fit * err_fit).mean()).item())
+    # FP64 oracle on sampled lanes with the GPU's fitted parameters
+    lanes = np.linspace(0, a.long_lanes - 1, 8).astype(int)
+    th_h = th.double().cpu().numpy()
+    pred_h = None
+    worst = 0.0
+    for l in lanes:
+        i0, i1 = int(sc["lane_off"][l]), int(sc["lane_off"][l + 1])
+        lo = np.array([0, i1 - i0], dtype=np.int32)
+        P, _ = oracle.forward(lo, sc["length"][i0:i1], th_h[:, i0:i1], sc["p_init"][i0:i1], sc["v_init"][i0:i1],
+                              K_all, DT, A_MIN)
+        pred_h = pred[:, i0:i1].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(pred_h - P))))
+    out = {"workload": "%d lanes x 100 vehicles (%.1fM), fit steps 1-%d (noise 0.5 m), predict steps %d-%d; "
+                       "learned initial guess + %d Adam iterations, checkpoints every %d steps"
+                       % (a.long_lanes, N / 1e6, K_fit, K_fit + 1, K_all, a.long_iters, C),
+           "init_ms": e[0].elapsed_time(e[1]), "fit_s": e[1].elapsed_time(e[2]) / 1e3,
+           "predict_ms": e[2].elapsed_time(e[3]),
+           "fit_vehicle_steps_per_s": a.long_iters * N * K_fit / (e[1].elapsed_time(e[2]) * 1e-3),
+           "rmse_fit_window_m": rmse_fit, "rmse_prediction_m": rmse_pred,
+           "final_mse_m2": float(hist[-1].item()) / N,
+           "oracle_check": {"lanes": len(lanes), "max_abs_diff_m": worst, "steps": K_all},
+           "peak_hbm_gb": {"torch_allocated": peak / 1e9, "library_workspace": ws / 1e9}}
+    ctx.close()
+    return out
+
+
+def lib_workspace(ctx, scene, K):
+    from paper_2412_16750_gb300 import lib
+    return lib.idm_workspace_bytes(ctx.handle, scene.c(), lib.make_sim(K, DT, A_MIN))
+
+
+def batched(a, dev):
+    """Batched uneven scenarios: 4,096 scenarios (lanes U[1,64], vehicles per
+    lane U[2,200], horizons U[50,500], observed every 10th step) fitted
+    together, one forward and one adjoint launch per Adam iteration, the whole
+    fit one CUDA graph; kernel shape chosen by the autotuner (cached)."""
+    import torch
+    from paper_2412_16750_gb300 import api, synth, tune
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20241216 + 2)
+    sc = synth.config2(a.batch_scen)
+    N = int(sc["lane_off"][-1])
+    b = api.Batch(sc["scen_lane_off"], sc["K"], sc["dt"], sc["obs_stride"], sc["lane_off"], sc["length"], A_MIN)
+    th_true = cu(sc["theta_true"])
+    p0, v0 = cu(sc["p_init"]), cu(sc["v_init"])
+    ctx = api.Context()
+    # clean observed targets of every scenario (rows j*10 of its trajectory block)
+    traj = api.batch_forward(th_true, p0, v0, b, ctx=ctx)
+    nv = np.diff(b.veh_off)
+    clean = torch.empty(int(b.tgt_off[-1]), device=dev)
+    for q in range(b.n_scen):
+        K, st, n = int(b.K[q]), int(b.obs_stride[q]), int(nv[q])
+        blk = traj[b.traj_off[q]:b.traj_off[q + 1]].view(K + 1, n)
+        clean[b.tgt_off[q]:b.tgt_off[q + 1]].view(-1, n).copy_(blk[st::st][:K // st])
+    del traj
+    torch.cuda.empty_cache()
+    Y = clean + 0.5 * torch.randn(clean.shape, device=dev, generator=gen)
+    plain = cu(synth.plain_init(N))
+    max_lane = int(np.diff(sc["lane_off"]).max())
+    sig = tune.signature(max_lane, N, float(np.mean(sc["K"])), 10, kind="batch")
+    run = lambda c: api.batch_loss_grad(plain, p0, v0, b, Y, ctx=c)
+    shape, how, timings = tune.tuned(ctx, run, max_lane, sig, repeats=2)
+    units = int(np.sum(nv.astype(np.int64) * b.K.astype(np.int64)))    # vehicle-steps per forward
+    th = torch.empty_like(plain)
+    for _ in range(2):                                                  # first call captures the graph
+        th.copy_(plain)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hist, _ = api.batch_fit(th, p0, v0, b, Y, a.batch_iters, ctx=ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_iter = e0.elapsed_time(e1) / a.batch_iters
+    rc, flags = ctx.status()
+    if rc != 0:
+        raise RuntimeError("batched status %d flags %d" % (rc, flags))
+    _, tot_clean, _, _, _ = api.batch_loss_grad(th, p0, v0, b, clean, ctx=ctx)
+    _, tot0, _, _, _ = api.batch_loss_grad(plain, p0, v0, b, clean, ctx=ctx)
+    out = {"workload": sc["name"], "vehicles": N, "lanes": int(sc["scen_lane_off"][-1]),
+           "vehicle_steps_per_iteration": units, "iterations": a.batch_iters, "ms_per_iteration": ms_iter,
+           "vehicle_steps_per_s": units / (ms_iter * 1e-3), "launches_per_iteration": 3,
+           "shape": {"vpt": shape[0], "warps_per_segment": shape[1], "ckpt_interval": shape[2],
+                     "warps_per_block": shape[3], "source": how, "candidates_timed": len(timings)},
+           "rmse_vs_clean_m": {"initial": math.sqrt(float(tot0.item()) / N),
+                               "after_%d_iterations" % a.batch_iters: math.sqrt(float(tot_clean.item()) / N)}}
+    ctx.close()
+    return out
+
+
 def run_gpu(a, rank, world, local_rank):
     import torch
     from paper_2412_16750_gb300 import api, lib, synth
@@ -405,9 +548,19 @@ def run_gpu(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if a.batched_only:
+        if rank == 0:
+            print(json.dumps({"batched": batched(a, dev)}), flush=True)
+        return 0
     if a.init_only:
         if rank == 0:
-            print(json.dumps({"time_to_fit": time_to_fit(a, dev)}), flush=True)
+            ttf, net = time_to_fit(a, dev)
+            print(json.dumps({"time_to_fit": ttf}), flush=True)
+        return 0
+    if a.long_only:
+        if rank == 0:
+            ttf, net = time_to_fit(a, dev)
+            print(json.dumps({"time_to_fit": ttf, "long_horizon": long_horizon(a, dev, net)}), flush=True)
         return 0
 
     # ---- synthetic batch (seeded per rank), unsorted arrival order -------
@@ -566,7 +719,12 @@ def run_gpu(a, rank, world, local_rank):
         "clocks": clk,
     }
     if world == 1 and not a.no_init_experiment:
-        line["time_to_fit"] = time_to_fit(a, dev)
+        line["time_to_fit"], net = time_to_fit(a, dev)
+        if not a.no_long_horizon:
+            line["long_horizon"] = long_horizon(a, dev, net)
+        net.close()
+    if world == 1 and not a.no_batched:
+        line["batched"] = batched(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, secs, desc = oracle_sample(iters=30)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,

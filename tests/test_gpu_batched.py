@@ -169,3 +169,35 @@ def test_config2_full_size_sampled(api):
             nr = np.linalg.norm(gr[q])
             if nr > 0:
                 assert np.linalg.norm(g[q, a:e] - gr[q]) / nr <= 1e-4
+
+
+def test_autotuned_shape_keeps_parity(api, tmp_path):
+    """The autotuner times the batched loss + gradient over candidate shapes,
+    caches the fastest and applies it; results under that shape still match
+    the oracle, and a second call is served from the cache."""
+    from paper_2412_16750_gb300 import tune
+    sc, rng = small_batch(203)
+    Y = cuda(targets_for(sc, rng))
+    N = int(sc["lane_off"][-1])
+    theta = cuda(synth.f32(sc["theta_true"] * rng.uniform(0.9, 1.1, size=(6, N))))
+    p0, v0 = cuda(sc["p_init"]), cuda(sc["v_init"])
+    b = batch_of(api, sc)
+    max_lane = int(np.diff(sc["lane_off"]).max())
+    sig = tune.signature(max_lane, N, float(np.mean(sc["K"])), 1, kind="batch")
+    path = str(tmp_path / "tune.json")
+    ctx = api.Context()
+    run = lambda c: api.batch_loss_grad(theta, p0, v0, b, Y, ctx=c)
+    shape, how, timings = tune.tuned(ctx, run, max_lane, sig, repeats=2, path=path)
+    assert how == "tuned" and len(timings) >= 4
+    assert 32 * shape[0] * shape[1] >= max_lane
+    assert ctx.tuning == tuple(shape)
+    sl, tot, g, _, _ = run(ctx)
+    ctx2 = api.Context()
+    sl2, tot2, g2, _, _ = run(ctx2)                 # default shape
+    torch.cuda.synchronize()
+    assert ctx.check_status() == 0
+    np.testing.assert_allclose(sl.cpu().numpy(), sl2.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    gn, g2n = g.double().cpu().numpy(), g2.double().cpu().numpy()
+    np.testing.assert_allclose(gn, g2n, rtol=0, atol=1e-4 * np.abs(g2n).max())
+    shape2, how2, _ = tune.tuned(api.Context(), run, max_lane, sig, path=path)
+    assert how2 == "cache" and tuple(shape2) == tuple(shape)

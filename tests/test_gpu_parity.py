@@ -219,6 +219,34 @@ def test_long_horizon_positions(api):
     assert np.max(np.abs(traj - P)) <= 5e-3
 
 
+def test_long_horizon_fit_then_predict(api):
+    """Fit on the first 400 of 600 steps with checkpoints every 20 steps
+    (about sqrt(400)), then predict all 600 steps with the fitted
+    parameters: the fit matches the oracle's fit, the prediction the
+    oracle's simulation of the same parameters."""
+    rng = np.random.default_rng(112)
+    sc = synth.make_scene([50] * 8, rng)
+    N = 400
+    K_fit, K_all = 400, 600
+    P_true, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K_all, DT,
+                               A_MIN)
+    Y = synth.f32(P_true[1:K_fit + 1] + rng.normal(0, 0.5, size=(K_fit, N)))
+    th0 = synth.plain_init(N)
+    n_iter = 6
+    th_ref, _ = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K_fit, DT, Y, 1, n_iter,
+                           0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    ctx = api.Context(ckpt_interval=20)
+    th = cuda(th0)
+    api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K_fit, DT, cuda(Y), 1, n_iter, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.check_status() == 0
+    th_gpu = th.double().cpu().numpy()
+    np.testing.assert_allclose(th_gpu, th_ref, rtol=1e-4, atol=1e-5)
+    traj = api.simulate(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K_all, DT, A_MIN, ctx=ctx)
+    P_pred, _ = oracle.forward(sc["lane_off"], sc["length"], th_gpu, sc["p_init"], sc["v_init"], K_all, DT, A_MIN)
+    assert np.max(np.abs(traj.double().cpu().numpy() - P_pred)) <= 5e-3
+
+
 # ---------------------------------------------------------------------------
 # fit, layout
 # ---------------------------------------------------------------------------
