@@ -400,8 +400,7 @@ def time_to_fit(a, dev):
                                                            for i in (0, 10, 50, 100, a.fit_iters - 1)
                                                            if i < a.fit_iters}}}
     ctx.close()
-    net.close()
-    return out
+    return out, net
 
 
 def long_horizon(a, dev, net):
