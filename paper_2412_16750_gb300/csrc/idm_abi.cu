@@ -92,7 +92,7 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
         g = 8;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
         // shrink the segment while the adjoint tape would not fit shared memory
-        while (idm::backward_smem_bytes(v, false, c->C, g, g) > 227 * 1024) {
+        while (idm::backward_smem_bytes(v, false, c->C, g, g, false) > 227 * 1024) {
             if (g > 1 && 32 * v * (g / 2) >= max_lane) g /= 2;
             else if (v > 1 && 32 * (v / 2) * g >= max_lane) v /= 2;
             else break;
@@ -226,10 +226,18 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
 {
     const size_t smem_max = 227 * 1024;
     const int G = P->G;
-    const size_t per_group = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G);
-    if (per_group > smem_max)
+    // prefetching the next checkpoint segment doubles two stages; use it
+    // when it does not cost a resident group per SM
+    const size_t g_pf = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G, true);
+    const size_t g_1 = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G, false);
+    if (g_1 > smem_max)
         return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per segment exceeds shared memory; lower "
-                                    "ckpt_interval", per_group);
+                                    "ckpt_interval", g_1);
+    const size_t sm_smem = 228 * 1024;
+    const size_t reg_cap = std::max(1, 16 / G);  // groups per SM the register file allows (~16 warps)
+    const bool pf = g_pf <= smem_max && sm_smem / (g_pf + 1024) >= std::min<size_t>(sm_smem / (g_1 + 1024), reg_cap);
+    P->a.bwd_pf = pf ? 1 : 0;
+    const size_t per_group = pf ? g_pf : g_1;
     int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
     if (G * 32 * groups > 256) groups = std::max(1, 256 / (32 * G));
     P->wpb_b = groups * G;

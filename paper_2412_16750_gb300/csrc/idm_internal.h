@@ -62,6 +62,10 @@ struct SimArgs {
     // as targets), per warp like loss_part; NULL = off
     const float *eval_targets;
     double *eval_part;
+    // adjoint: 1 = copy the next checkpoint segment's targets and checkpoint
+    // into double-buffered shared stages while the current segment runs
+    // (needs more shared memory), 0 = load each segment when it starts
+    int bwd_pf;
 };
 
 // Launchers (idm_sim.cu).  Return cudaError_t of the launch.
@@ -76,7 +80,7 @@ cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, con
                            cudaStream_t st);
 cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
-size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb);
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb, bool prefetch);
 size_t forward_smem_bytes(int vpt, int G, int wpb);
 cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st);
 int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);

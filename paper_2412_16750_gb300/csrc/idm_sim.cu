@@ -468,11 +468,15 @@ forward_kernel(SimArgs a, FwdFlags f)
 // Gradient increments accumulate in registers per checkpoint segment and
 // are added to per-slot totals in shared memory.
 // ---------------------------------------------------------------------------
-// Shared floats of one group: tape v/gap[/seed] [C][G*SL], totals [6][G*SL],
-// control area.
-__host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, int C, int G)
+// Shared floats of one group: tape v/gap [C][G*SL], target/seed tapes
+// [C][G*SL] (MSE only), checkpoint stages [4][G*SL], totals [6][G*SL],
+// control area.  With prefetch the target tape and the checkpoint stage are
+// doubled and the next checkpoint segment's targets and checkpoint are
+// copied (cp.async) into the idle pair while the current segment runs.
+__host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, int C, int G, bool pf)
 {
-    return ((dense ? 2 : 3) * C + 6) * 32 * vpt * G + grp_ctrl_floats(G);
+    const int nb = pf ? 2 : 1;
+    return ((dense ? 2 : 2 + nb) * C + 4 * nb + 6) * 32 * vpt * G + grp_ctrl_floats(G);
 }
 
 __device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
@@ -487,9 +491,11 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     const int SLG = SL * g.G;
     const int lane = g.lane;
     const int wb = g.w * SL;                        // this warp's first slot in the group
+    const int nb = a.bwd_pf ? 2 : 1;                // stages (double-buffered with prefetch)
     float *tg = tv + a.C * SLG;
-    float *tr = tg + a.C * SLG;                     // targets, then seeds (MSE only)
-    float *acc = tv + (DENSE ? 2 : 3) * a.C * SLG;  // gradient totals [6][SLG]
+    float *trb = tg + a.C * SLG;                    // nb tapes: targets, then seeds (MSE only)
+    float *ckb = tv + (DENSE ? 2 : 2 + nb) * a.C * SLG;  // nb checkpoint stages [4][SLG]
+    float *acc = ckb + nb * 4 * SLG;                // gradient totals [6][SLG]
     const int Ns = sc.n_veh;
     const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
@@ -506,36 +512,60 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
     }
 
-    const int n_ck = (sc.K + a.C - 1) / a.C;
-    for (int cs = n_ck - 1; cs >= 0; --cs) {
+    // first observed step >= max(c0, 1) of a checkpoint segment and its
+    // target row (one division per segment; the step loops count instead)
+    auto first_obs = [&](int c0, int &obs_k, int &obs_row) {
+        obs_row = (c0 + sc.obs_stride - 1) / sc.obs_stride;
+        if (obs_row == 0) obs_row = 1;
+        obs_k = obs_row * sc.obs_stride;
+        obs_row -= 1;
+    };
+    // cp.async of segment cs's observed targets and checkpoint into the
+    // stage of its parity (each thread copies only its own slots)
+    auto prefetch_segment = [&](int cs) {
         const int c0 = cs * a.C;
         const int n = min(a.C, sc.K - c0);
-        // first observed step >= max(c0, 1) and its target row (one division
-        // per checkpoint segment; the step loops count instead of dividing)
-        int obs_row = (c0 + sc.obs_stride - 1) / sc.obs_stride;
-        if (obs_row == 0) obs_row = 1;
-        int obs_k = obs_row * sc.obs_stride;
-        obs_row -= 1;
-        if (!DENSE) {  // fetch the segment's observed targets into the seed tape
+        const int par = a.bwd_pf ? (cs & 1) : 0;
+        if (!DENSE) {
+            float *tr = trb + par * a.C * SLG;
+            int obs_k, obs_row;
+            first_obs(c0, obs_k, obs_row);
             const float *yrow = a.targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
             for (int k = obs_k, r = obs_row; k < c0 + n && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
                 prefetch_row<NP>(tr + (k - c0) * SLG + wb, yrow, lane, vx, vy);
-            cp_async_commit();
         }
+        float *ck = ckb + par * 4 * SLG;
+        const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * Ns, lane, vx, vy);
+        cp_async_commit();
+    };
+
+    const int n_ck = (sc.K + a.C - 1) / a.C;
+    if (a.bwd_pf) prefetch_segment(n_ck - 1);
+    for (int cs = n_ck - 1; cs >= 0; --cs) {
+        const int c0 = cs * a.C;
+        const int n = min(a.C, sc.K - c0);
+        int obs_k, obs_row;
+        first_obs(c0, obs_k, obs_row);
+        const int par = a.bwd_pf ? (cs & 1) : 0;
+        float *tr = trb + par * a.C * SLG;
+        if (!a.bwd_pf) prefetch_segment(cs);
+        cp_async_wait<0>();  // this segment's targets and checkpoint (this thread's own slots)
         {
-            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+            const float *ck = ckb + par * 4 * SLG + wb;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
-                st[p].ph = load_pair(base, q, vx[p], vy[p]);
-                st[p].pl = load_pair(base + (size_t)Ns, q, vx[p], vy[p]);
-                const f2 v = load_pair(base + 2 * (size_t)Ns, q, vx[p], vy[p]);
-                const f2 gp = load_pair(base + 3 * (size_t)Ns, q, vx[p], vy[p]);
-                st[p].v = v;
+                const f2 ph = lds2(ck + q), pl = lds2(ck + SLG + q), v = lds2(ck + 2 * SLG + q);
+                const f2 gp = lds2(ck + 3 * SLG + q);
+                st[p].ph = make_float2(vx[p] ? ph.x : 0.0f, vy[p] ? ph.y : 0.0f);
+                st[p].pl = make_float2(vx[p] ? pl.x : 0.0f, vy[p] ? pl.y : 0.0f);
+                st[p].v = make_float2(vx[p] ? v.x : 0.0f, vy[p] ? v.y : 0.0f);
                 st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
             }
         }
-        if (!DENSE) cp_async_wait<0>();
+        if (a.bwd_pf && cs > 0) prefetch_segment(cs - 1);  // lands while this segment runs
         f2 lseg = F2(0.0f);
         // recompute the segment into the tape
         for (int s = 0; s < n; ++s) {
@@ -760,8 +790,8 @@ backward_kernel(SimArgs a)
     extern __shared__ float smem[];
     const int G = a.G;
     const int warp = threadIdx.x >> 5;
-    float *gbase = smem + (warp / G) * bwd_group_floats(VPT, DENSE, a.C, G);
-    float *ctrl = gbase + bwd_group_floats(VPT, DENSE, a.C, G) - grp_ctrl_floats(G);
+    float *gbase = smem + (warp / G) * bwd_group_floats(VPT, DENSE, a.C, G, a.bwd_pf != 0);
+    float *ctrl = gbase + bwd_group_floats(VPT, DENSE, a.C, G, a.bwd_pf != 0) - grp_ctrl_floats(G);
     Grp g = make_grp(G, ctrl);
     int par = 0;
     for (;;) {
@@ -829,9 +859,9 @@ cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, con
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
-size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb)
+size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb, bool prefetch)
 {
-    return (size_t)bwd_group_floats(vpt, dense_seed, C, G) * (wpb / G) * sizeof(float);
+    return (size_t)bwd_group_floats(vpt, dense_seed, C, G, prefetch) * (wpb / G) * sizeof(float);
 }
 
 size_t forward_smem_bytes(int vpt, int G, int wpb)
@@ -866,7 +896,7 @@ cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool wan
     if (dense_seed && adam) return cudaErrorInvalidValue;
     void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam);
     if (!fn) return cudaErrorInvalidValue;
-    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, G, wpb);
+    size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, G, wpb, a.bwd_pf != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SimArgs args = a;
