@@ -116,10 +116,13 @@ int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
 /* Kernel shape.  Whole lanes are packed into segments of at most
  * 32 * vpt * warps_per_segment vehicles, each simulated by warps_per_segment
  * warps of one block.  vpt: vehicles per thread (2, 4 or 8; 0 = choose);
- * warps_per_segment: 1, 2, 4 or 8 (0 = choose; default 8 with vpt 2);
- * ckpt_interval: steps between stored checkpoints of the adjoint (1..64,
- * default 8); warps_per_block: 1..16 (default 8; rounded to a multiple of
- * warps_per_segment, and the adjoint caps it by its shared-memory tape). */
+ * warps_per_segment: 1, 2, 4 or 8 (0 = choose; with both 0 the library
+ * takes vpt 4 x 4 warps, 8 x 4 for lanes over 512 vehicles and 8 x 8 over
+ * 1024); ckpt_interval: steps between stored checkpoints of the adjoint
+ * (1..64, default 8); warps_per_block: 1..16 (default 4; rounded to a
+ * multiple of warps_per_segment; the adjoint caps it by its shared-memory
+ * tape and by its register budget: 4 warps for vpt 4 with segments of up to
+ * 4 warps, 8 otherwise). */
 int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block);
 
 /* Longest lane the library can simulate (vehicles): 32 * 8 * 8 = 2048. */

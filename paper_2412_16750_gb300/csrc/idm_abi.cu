@@ -88,13 +88,16 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
 {
     int v = c->vpt_req, g = c->G_req;
     if (v == 0 && g == 0) {
-        v = 2;
-        g = 8;
-        while (32 * v * g < max_lane && v < 8) v <<= 1;
+        // 4 vehicles per thread x 4 warps (512 slots); 8 x 4 and 8 x 8 for
+        // lanes longer than 512 and 1024
+        v = 4;
+        g = 4;
+        if (max_lane > 512) v = 8;
+        if (max_lane > 1024) g = 8;
         // shrink the segment while the adjoint tape would not fit shared memory
         while (idm::backward_smem_bytes(v, false, c->C, g, g, false) > 227 * 1024) {
             if (g > 1 && 32 * v * (g / 2) >= max_lane) g /= 2;
-            else if (v > 1 && 32 * (v / 2) * g >= max_lane) v /= 2;
+            else if (v > 2 && 32 * (v / 2) * g >= max_lane) v /= 2;
             else break;
         }
     } else if (v == 0) {
@@ -234,12 +237,12 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
         return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per segment exceeds shared memory; lower "
                                     "ckpt_interval", g_1);
     const size_t sm_smem = 228 * 1024;
-    const size_t reg_cap = std::max(1, 16 / G);  // groups per SM the register file allows (~16 warps)
+    const size_t reg_cap = std::max(1, idm::backward_resident_warps(P->vpt, G) / G);  // groups per SM by registers
     const bool pf = g_pf <= smem_max && sm_smem / (g_pf + 1024) >= std::min<size_t>(sm_smem / (g_1 + 1024), reg_cap);
     P->a.bwd_pf = pf ? 1 : 0;
     const size_t per_group = pf ? g_pf : g_1;
     int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
-    if (G * 32 * groups > 256) groups = std::max(1, 256 / (32 * G));
+    groups = std::max(1, std::min(groups, idm::backward_max_warps(P->vpt, G) / G));
     P->wpb_b = groups * G;
     size_t smem = per_group * groups;
     int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem);

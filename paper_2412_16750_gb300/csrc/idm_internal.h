@@ -82,6 +82,11 @@ cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool wan
                             int grid, int wpb, cudaStream_t st);
 size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb, bool prefetch);
 size_t forward_smem_bytes(int vpt, int G, int wpb);
+// Largest adjoint block (warps) for a shape: 4 for 4 vehicles per thread in
+// segments of up to 4 warps (register budget), else 8.
+int backward_max_warps(int vpt, int G);
+// Adjoint warps per SM the register budgets allow for a shape.
+int backward_resident_warps(int vpt, int G);
 cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st);
 int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
 

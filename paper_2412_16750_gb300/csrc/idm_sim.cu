@@ -782,8 +782,18 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     }
 }
 
-template <int VPT, bool DENSE, bool ADAM, bool WD>
-__global__ void __launch_bounds__(256, (VPT <= 4 ? 2 : 1))
+// Register budgets: 2 vehicles per thread fit 128 registers (2 blocks of 8
+// warps per SM); 4 per thread need ~168 without spilling, so their blocks
+// are 4 warps (3 blocks per SM) unless the segment has 8 warps (BIG, 256
+// threads, one block per SM); 8 per thread use up to 255.
+template <int VPT, bool BIG>
+struct BwdBounds {
+    static constexpr int threads = (VPT == 4 && !BIG) ? 128 : 256;
+    static constexpr int blocks = VPT == 2 ? 2 : ((VPT == 4 && !BIG) ? 3 : 1);
+};
+
+template <int VPT, bool DENSE, bool ADAM, bool WD, bool BIG>
+__global__ void __launch_bounds__(BwdBounds<VPT, BIG>::threads, BwdBounds<VPT, BIG>::blocks)
 backward_kernel(SimArgs a)
 {
     constexpr int NP = VPT / 2;
@@ -871,30 +881,44 @@ size_t forward_smem_bytes(int vpt, int G, int wpb)
 }
 
 // Kernel variants of the adjoint: seeds from dense gradients or from targets,
-// fused Adam or gradient output, with or without the delta gradient.
-template <int VPT>
+// fused Adam or gradient output, with or without the delta gradient; for 4
+// vehicles per thread a 4-warp and an 8-warp block form.
+template <int VPT, bool BIG>
 static void *backward_fn(bool dense, bool adam, bool wd)
 {
-    if (dense) return wd ? (void *)backward_kernel<VPT, true, false, true> : (void *)backward_kernel<VPT, true, false, false>;
-    if (adam) return (void *)backward_kernel<VPT, false, true, false>;
-    return wd ? (void *)backward_kernel<VPT, false, false, true> : (void *)backward_kernel<VPT, false, false, false>;
+    if (dense)
+        return wd ? (void *)backward_kernel<VPT, true, false, true, BIG>
+                  : (void *)backward_kernel<VPT, true, false, false, BIG>;
+    if (adam) return (void *)backward_kernel<VPT, false, true, false, BIG>;
+    return wd ? (void *)backward_kernel<VPT, false, false, true, BIG>
+              : (void *)backward_kernel<VPT, false, false, false, BIG>;
 }
 
-static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd)
+static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd, int wpb)
 {
     switch (vpt) {
-    case 2: return backward_fn<2>(dense, adam, wd);
-    case 4: return backward_fn<4>(dense, adam, wd);
-    case 8: return backward_fn<8>(dense, adam, wd);
+    case 2: return backward_fn<2, false>(dense, adam, wd);
+    case 4: return wpb > 4 ? backward_fn<4, true>(dense, adam, wd) : backward_fn<4, false>(dense, adam, wd);
+    case 8: return backward_fn<8, false>(dense, adam, wd);
     }
     return nullptr;
+}
+
+int backward_max_warps(int vpt, int G) { return (vpt == 4 && G <= 4) ? 4 : 8; }
+
+int backward_resident_warps(int vpt, int G)
+{
+    if (vpt == 2) return 16;
+    if (vpt == 4 && G <= 4) return 12;
+    return 8;
 }
 
 cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool want_delta, const SimArgs &a, int grid,
                             int wpb, cudaStream_t st)
 {
     if (dense_seed && adam) return cudaErrorInvalidValue;
-    void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam);
+    if (wpb > backward_max_warps(vpt, G) || wpb % G) return cudaErrorInvalidValue;
+    void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam, wpb);
     if (!fn) return cudaErrorInvalidValue;
     size_t smem = backward_smem_bytes(vpt, dense_seed, a.C, G, wpb, a.bwd_pf != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -917,7 +941,7 @@ int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool 
         smem = forward_smem_bytes(vpt, G, wpb);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
-        fn = backward_fn_v(vpt, dense, adam, want_delta && !adam);
+        fn = backward_fn_v(vpt, dense, adam, want_delta && !adam, wpb);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     if (!fn) return 1;
