@@ -211,6 +211,10 @@ def alu_peak_ginst(sm_mhz, n_sm):
 ADJ_OPS_PER_VS = 118.0
 
 
+# Sources of the adjoint kernel: the committed ncu summary records their hash.
+ADJOINT_SOURCES = ("idm_adjoint.cuh", "idm_sim_common.cuh", "idm_device.cuh")
+
+
 def adjoint_traffic(n_vehicles, K, ckpt):
     """DRAM bytes of one adjoint launch from the committed ncu summary
     (N K a + N b, captured at checkpoint interval 8), or None if absent,
@@ -219,8 +223,9 @@ def adjoint_traffic(n_vehicles, K, ckpt):
     if not os.path.exists(path) or ckpt != 8:
         return None
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_sim.cu"), "rb").read()
-    src += open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", "idm_device.cuh"), "rb").read()
+    src = b""
+    for name in ADJOINT_SOURCES:
+        src += open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", name), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     got_sha, per_vs, per_v = None, None, 0.0
     for line in open(path):

@@ -94,12 +94,6 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
         g = 4;
         if (max_lane > 512) v = 8;
         if (max_lane > 1024) g = 8;
-        // shrink the segment while the adjoint tape would not fit shared memory
-        while (idm::backward_smem_bytes(v, false, c->C, g, g, false) > 227 * 1024) {
-            if (g > 1 && 32 * v * (g / 2) >= max_lane) g /= 2;
-            else if (v > 2 && 32 * (v / 2) * g >= max_lane) v /= 2;
-            else break;
-        }
     } else if (v == 0) {
         v = 2;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
@@ -228,24 +222,42 @@ int forward_grid(idm_ctx *c, Prep *P, int L)
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L)
 {
     const size_t smem_max = 227 * 1024;
-    const int G = P->G;
-    // prefetching the next checkpoint segment doubles two stages; use it
-    // when it does not cost a resident group per SM
-    const size_t g_pf = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G, true);
-    const size_t g_1 = idm::backward_smem_bytes(P->vpt, dense, c->C, G, G, false);
-    if (g_1 > smem_max)
-        return fail(c, IDM_ERR_ARG, "adjoint tape of %zu bytes per segment exceeds shared memory; lower "
-                                    "ckpt_interval", g_1);
     const size_t sm_smem = 228 * 1024;
+    const int G = P->G;
     const size_t reg_cap = std::max(1, idm::backward_resident_warps(P->vpt, G) / G);  // groups per SM by registers
-    const bool pf = g_pf <= smem_max && sm_smem / (g_pf + 1024) >= std::min<size_t>(sm_smem / (g_1 + 1024), reg_cap);
+    auto groups_per_sm = [&](int T, bool pf) -> size_t {
+        const size_t b = idm::backward_smem_bytes(P->vpt, dense, T, G, G, pf);
+        return b > smem_max ? 0 : sm_smem / (b + 1024);
+    };
+    // tape depth: the checkpoint interval, or less when a deeper tape would
+    // cost resident groups (blocks inside a checkpoint segment then restart
+    // from sub-checkpoints written by an extra forward pass)
+    int T = c->C;
+    const size_t want = std::min(reg_cap, std::max<size_t>(groups_per_sm(1, false), 1));
+    while (T > 1 && groups_per_sm(T, false) < want) --T;
+    if (groups_per_sm(T, false) == 0)
+        return fail(c, IDM_ERR_ARG, "adjoint tape does not fit shared memory for vpt %d x %d warps", P->vpt, G);
+    // prefetching the next block doubles two stages; use it when it does not
+    // cost a resident group per SM
+    const bool pf = groups_per_sm(T, true) >= std::min(reg_cap, groups_per_sm(T, false));
     P->a.bwd_pf = pf ? 1 : 0;
-    const size_t per_group = pf ? g_pf : g_1;
+    P->a.tape_T = T;
+    if (T < c->C) {
+        const size_t rows = (size_t)((c->C + T - 1) / T - 1);
+        int rc;
+        if ((rc = ensure(c, c->sub_ckpt, sizeof(float) * 4 * rows * (size_t)std::max(P->a.N_total, 1),
+                         "sub-checkpoints")))
+            return rc;
+        P->a.sub_ckpt = (float *)c->sub_ckpt.p;
+    } else {
+        P->a.sub_ckpt = nullptr;
+    }
+    const size_t per_group = idm::backward_smem_bytes(P->vpt, dense, T, G, G, pf);
     int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
     groups = std::max(1, std::min(groups, idm::backward_max_warps(P->vpt, G) / G));
     P->wpb_b = groups * G;
     size_t smem = per_group * groups;
-    int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem);
+    int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem, T < c->C);
     int blocks_needed = (L * G + P->wpb_b - 1) / P->wpb_b;
     P->grid_b = std::min(blocks_needed, c->n_sm * occ_b);
     P->grid_b = P->grid_b < 1 ? 1 : P->grid_b;
@@ -425,7 +437,10 @@ size_t idm_workspace_bytes(const idm_ctx_t *c, const idm_scene_t *s, const idm_s
     if (!c || !s || !sim || sim->K < 1) return 0;
     size_t N = (size_t)s->n_vehicles, L = (size_t)s->n_lanes;
     size_t n_ck = (size_t)((sim->K + c->C - 1) / c->C);
-    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + 16 * n_ck * N;
+    // sub-checkpoints when the adjoint's tape is shallower than the interval
+    // (at most ceil(C/2) - 1 rows; typically none for C <= 8)
+    const size_t sub = c->C > 8 ? (size_t)((c->C + 1) / 2 - 1) : 0;
+    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + 16 * n_ck * N + 16 * sub * N;
 }
 
 int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)

@@ -1,0 +1,760 @@
+// Adjoint kernel templates; each idm_adjoint<VPT>.cu instantiates the
+// variants of one vehicles-per-thread value (so they compile in parallel).
+#pragma once
+#include "idm_sim_common.cuh"
+
+namespace idm {
+
+// ---------------------------------------------------------------------------
+// Adjoint.  Per segment of C steps (last first): cp.async the observed
+// targets of the C steps into the seed tape, reload the checkpoint,
+// recompute the C steps into the group's shared tape of (v, raw gap, seed),
+// then run the reverse recurrences
+//   lp_k = seed_k + lp_{k+1} + mu A_p + mu_f A_ph(f)
+//   lv_k = dt lp_{k+1} + lv_{k+1} + mu A_v + mu_f A_vh(f)
+// with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle
+// (and across warps through the group's exchange cells).  The coefficients
+// of step k-1 are evaluated while the dependent chain of step k runs.
+// Gradient increments accumulate in registers per checkpoint segment and
+// are added to per-slot totals in shared memory.
+// ---------------------------------------------------------------------------
+template <int NP, bool DENSE, bool ADAM, bool WD, bool D4>
+__device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
+                                                 Grp &g, float *tv, const VehConst2 (&kc)[NP], State2 (&st)[NP],
+                                                 const bool (&vx)[NP], const bool (&vy)[NP])
+{
+    constexpr int SL = 64 * NP;
+    const int SLG = SL * g.G;
+    const int lane = g.lane;
+    const int wb = g.w * SL;                        // this warp's first slot in the group
+    const int nb = a.bwd_pf ? 2 : 1;                // stages (double-buffered with prefetch)
+    float *tg = tv + a.C * SLG;                     // (tape depth = checkpoint interval here)
+    float *trb = tg + a.C * SLG;                    // nb tapes: targets, then seeds (MSE only)
+    float *ckb = tv + (DENSE ? 2 : 2 + nb) * a.C * SLG;  // nb checkpoint stages [4][SLG]
+    float *acc = ckb + nb * 4 * SLG;                // gradient totals [6][SLG]
+    const int Ns = sc.n_veh;
+    const int wl = lb + wb;                         // scenario-local index of this warp's first slot
+    const float dt = sc.dt;
+    const f2 seed_scale = F2(2.0f * sc.inv_nobs);
+    int xp = 0, fp = 0;
+    float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
+
+    f2 lp[NP], lv[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        lp[p] = F2(0.0f);
+        lv[p] = F2(0.0f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
+    }
+
+    // first observed step >= max(c0, 1) of a checkpoint segment and its
+    // target row (one division per segment; the step loops count instead)
+    auto first_obs = [&](int c0, int &obs_k, int &obs_row) {
+        obs_row = (c0 + sc.obs_stride - 1) / sc.obs_stride;
+        if (obs_row == 0) obs_row = 1;
+        obs_k = obs_row * sc.obs_stride;
+        obs_row -= 1;
+    };
+    // cp.async of segment cs's observed targets and checkpoint into the
+    // stage of its parity (each thread copies only its own slots)
+    auto prefetch_segment = [&](int cs) {
+        const int c0 = cs * a.C;
+        const int n = min(a.C, sc.K - c0);
+        const int par = a.bwd_pf ? (cs & 1) : 0;
+        if (!DENSE) {
+            float *tr = trb + par * a.C * SLG;
+            int obs_k, obs_row;
+            first_obs(c0, obs_k, obs_row);
+            const float *yrow = a.targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
+            for (int k = obs_k, r = obs_row; k < c0 + n && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
+                prefetch_row<NP>(tr + (k - c0) * SLG + wb, yrow, lane, vx, vy);
+        }
+        float *ck = ckb + par * 4 * SLG;
+        const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * Ns, lane, vx, vy);
+        cp_async_commit();
+    };
+
+    const int n_ck = (sc.K + a.C - 1) / a.C;
+    if (a.bwd_pf) prefetch_segment(n_ck - 1);
+    for (int cs = n_ck - 1; cs >= 0; --cs) {
+        const int c0 = cs * a.C;
+        const int n = min(a.C, sc.K - c0);
+        int obs_k, obs_row;
+        first_obs(c0, obs_k, obs_row);
+        const int par = a.bwd_pf ? (cs & 1) : 0;
+        float *tr = trb + par * a.C * SLG;
+        if (!a.bwd_pf) prefetch_segment(cs);
+        cp_async_wait<0>();  // this segment's targets and checkpoint (this thread's own slots)
+        {
+            const float *ck = ckb + par * 4 * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                const f2 ph = lds2(ck + q), pl = lds2(ck + SLG + q), v = lds2(ck + 2 * SLG + q);
+                const f2 gp = lds2(ck + 3 * SLG + q);
+                st[p].ph = make_float2(vx[p] ? ph.x : 0.0f, vy[p] ? ph.y : 0.0f);
+                st[p].pl = make_float2(vx[p] ? pl.x : 0.0f, vy[p] ? pl.y : 0.0f);
+                st[p].v = make_float2(vx[p] ? v.x : 0.0f, vy[p] ? v.y : 0.0f);
+                st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+            }
+        }
+        if (a.bwd_pf && cs > 0) prefetch_segment(cs - 1);  // lands while this segment runs
+        f2 lseg = F2(0.0f);
+        // recompute the segment into the tape
+        for (int s = 0; s < n; ++s) {
+            const int k = c0 + s;
+            float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                sts2(rv + q, st[p].v);
+                sts2(rg + q, st[p].gap);
+            }
+            if (!DENSE && k == obs_k) {
+                if (obs_row < sc.n_obs) {
+                    float *rr = tr + s * SLG + wb;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], lds2(rr + q));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        sts2(rr + q, mul2(seed_scale, r));
+                        lseg = fma2(r, r, lseg);
+                    }
+                }
+                obs_k += sc.obs_stride;
+                ++obs_row;
+            }
+            f2 vcur[NP], vh[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+            const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+            leader_vals2<NP>(vcur, vh, lane, lead_in);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+                euler2(st[p], as, vh[p], dt);
+            }
+        }
+        if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = load_pair(a.gP + row, q, vx[p], vy[p]);
+                    lv[p] = a.gV ? load_pair(a.gV + row, q, vx[p], vy[p]) : F2(0.0f);
+                }
+            } else {
+                const int k = sc.K;
+                const bool obs = sc.n_obs > 0 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
+                if (obs) {
+                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], load_pair(y, q, vx[p], vy[p]));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        lp[p] = mul2(seed_scale, r);
+                        lseg = fma2(r, r, lseg);
+                    }
+                }
+            }
+        }
+        kahan_add(lsum, lcomp, __fadd_rn(lseg.x, lseg.y));
+        grp_sync(g);  // the whole group's tape is written
+
+        f2 sacc[6][NP];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) sacc[q][p] = F2(0.0f);
+
+        // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
+        int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
+        int obs_hi = row_hi * sc.obs_stride;
+        AdjJac2 J[NP];
+        {
+            const float *rv = tv + (n - 1) * SLG + wb, *rg = tg + (n - 1) * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                const f2 v = lds2(rv + q);
+                const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+            }
+        }
+        for (int s = n - 1; s >= 0; --s) {
+            const int k = c0 + s;
+            f2 to_lp[NP], to_lv[NP], t1[NP], nlv[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const f2 mu = mul2(F2(dt), lv[p]);
+                to_lp[p] = mul2(mu, J[p].Aph);
+                to_lv[p] = mul2(mu, J[p].Avh);
+                t1[p] = sub2(lp[p], to_lp[p]);                          // lp + mu A_p
+                nlv[p] = fma2(mu, J[p].Av, fma2(F2(dt), lp[p], lv[p]));  // dt lp + lv + mu A_v
+                sacc[0][p] = fma2(mu, J[p].w0n, sacc[0][p]);
+                sacc[1][p] = fma2(mu, J[p].w0nv, sacc[1][p]);
+                sacc[2][p] = fma2(mu, J[p].w0nvdv, sacc[2][p]);
+                sacc[3][p] = fma2(mu, J[p].fa, sacc[3][p]);
+                sacc[4][p] = fma2(mu, J[p].frd, sacc[4][p]);
+                if (WD) sacc[5][p] = fma2(mu, J[p].frdl, sacc[5][p]);
+            }
+            if (s > 0) {
+                const float *rv = tv + (s - 1) * SLG + wb, *rg = tg + (s - 1) * SLG + wb;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    const f2 v = lds2(rv + q);
+                    const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                }
+            }
+            float in_p, in_v;
+            grp_follow_in(g, to_lp[0].x, to_lv[0].x, in_p, in_v, fp);
+            f2 from_p[NP], from_v[NP];
+            follower_vals2<NP>(to_lp, from_p, lane, in_p);
+            follower_vals2<NP>(to_lv, from_v, lane, in_v);
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)k * Ns + wl;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = add2(add2(t1[p], from_p[p]), load_pair(a.gP + row, q, vx[p], vy[p]));
+                    lv[p] = add2(nlv[p], from_v[p]);
+                    if (a.gV) lv[p] = add2(lv[p], load_pair(a.gV + row, q, vx[p], vy[p]));
+                }
+            } else if (k == obs_hi && k >= 1 && row_hi <= sc.n_obs) {
+                const float *rr = tr + s * SLG + wb;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(add2(t1[p], from_p[p]), lds2(rr + 64 * p + 2 * lane));
+                    lv[p] = add2(nlv[p], from_v[p]);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(t1[p], from_p[p]);
+                    lv[p] = add2(nlv[p], from_v[p]);
+                }
+            }
+            if (!DENSE && k == obs_hi) {
+                obs_hi -= sc.obs_stride;
+                --row_hi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float *ap = acc + q * SLG + wb + 64 * p + 2 * lane;
+                sts2(ap, add2(lds2(ap), sacc[q][p]));
+            }
+        grp_sync(g);  // the tape may be overwritten by the next segment
+    }
+
+    // epilogue: parameter gradients from the factored sums
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(c ? vy[p] : vx[p])) continue;
+            const int q = wb + 64 * p + 2 * lane + c;
+            const int gi = sg.veh_begin + q;
+            const float v0 = a.v0[gi], b = a.b[gi];
+            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
+            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
+            const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
+            const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+            float gr[6];
+            gr[0] = am * dl * A4 / v0;                 // v0
+            gr[1] = -A1;                               // T
+            gr[2] = -A0;                               // s0
+            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
+            gr[4] = A2 * cc / (2.0f * b);              // b
+            gr[5] = -am * A5;                          // delta
+            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
+            if (ADAM) {
+                const int it = a.iter;
+                const int t = it + 1;
+                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
+                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const size_t mi = (size_t)r * a.N_total + gi;
+                    float m = 0.9f * a.adam_m[mi] + 0.1f * gr[r];
+                    float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[r] * gr[r];
+                    a.adam_m[mi] = m;
+                    a.adam_v[mi] = vv;
+                    float x = th[r][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+                    x = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
+                    th[r][gi] = x;
+                }
+            } else {
+                if (a.g_v0) a.g_v0[gi] = gr[0];
+                if (a.g_T) a.g_T[gi] = gr[1];
+                if (a.g_s0) a.g_s0[gi] = gr[2];
+                if (a.g_am) a.g_am[gi] = gr[3];
+                if (a.g_b) a.g_b[gi] = gr[4];
+                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
+                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
+                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
+            }
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (!DENSE) {
+        const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
+    }
+}
+
+// The same adjoint when the tape is shallower than the checkpoint interval:
+// each checkpoint segment is first run forward once writing sub-checkpoints
+// every T steps (global scratch, this thread's own slots), then processed as
+// tape blocks of T steps, last first.
+template <int NP, bool DENSE, bool ADAM, bool WD, bool D4>
+__device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
+                                                 Grp &g, float *tv, const VehConst2 (&kc)[NP], State2 (&st)[NP],
+                                                 const bool (&vx)[NP], const bool (&vy)[NP])
+{
+    constexpr int SL = 64 * NP;
+    const int SLG = SL * g.G;
+    const int lane = g.lane;
+    const int wb = g.w * SL;                        // this warp's first slot in the group
+    const int nb = a.bwd_pf ? 2 : 1;                // stages (double-buffered with prefetch)
+    const int T = a.tape_T;                         // tape depth (steps per block)
+    float *tg = tv + T * SLG;
+    float *trb = tg + T * SLG;                      // nb tapes: targets, then seeds (MSE only)
+    float *ckb = tv + (DENSE ? 2 : 2 + nb) * T * SLG;  // nb state stages [4][SLG]
+    float *acc = ckb + nb * 4 * SLG;                // gradient totals [6][SLG]
+    const int Ns = sc.n_veh;
+    const int wl = lb + wb;                         // scenario-local index of this warp's first slot
+    const float dt = sc.dt;
+    const f2 seed_scale = F2(2.0f * sc.inv_nobs);
+    int xp = 0, fp = 0;
+    float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
+
+    f2 lp[NP], lv[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        lp[p] = F2(0.0f);
+        lv[p] = F2(0.0f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
+    }
+
+    // first observed step >= max(c0, 1) of a checkpoint segment and its
+    // target row (one division per segment; the step loops count instead)
+    auto first_obs = [&](int c0, int &obs_k, int &obs_row) {
+        obs_row = (c0 + sc.obs_stride - 1) / sc.obs_stride;
+        if (obs_row == 0) obs_row = 1;
+        obs_k = obs_row * sc.obs_stride;
+        obs_row -= 1;
+    };
+    // Blocks.  Checkpoint segment cs (steps [cs C, cs C + len)) is processed
+    // as ceil(len / T) tape blocks of at most T steps, last first.  Block j > 0
+    // starts from sub-checkpoint row j - 1, written by a forward pass over
+    // the segment; block 0 starts from the checkpoint.
+    auto seg_len = [&](int cs) { return min(a.C, sc.K - cs * a.C); };
+    auto n_sub = [&](int cs) { return (seg_len(cs) + T - 1) / T; };
+    auto block_src = [&](int cs, int j, const float *&base, size_t &stride) {
+        if (j == 0) {
+            base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+            stride = (size_t)Ns;
+        } else {
+            base = a.sub_ckpt + (size_t)(j - 1) * 4 * a.N_total + sg.veh_begin + wb;
+            stride = (size_t)a.N_total;
+        }
+    };
+    // cp.async of block (cs, j)'s observed targets and starting state into
+    // stage par (each thread copies only its own slots)
+    auto prefetch_block = [&](int cs, int j, int par) {
+        const int b0 = cs * a.C + j * T;
+        const int bn = min(T, seg_len(cs) - j * T);
+        if (!DENSE) {
+            float *tr = trb + par * T * SLG;
+            int obs_k, obs_row;
+            first_obs(b0, obs_k, obs_row);
+            const float *yrow = a.targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
+            for (int k = obs_k, r = obs_row; k < b0 + bn && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
+                prefetch_row<NP>(tr + (k - b0) * SLG + wb, yrow, lane, vx, vy);
+        }
+        float *ck = ckb + par * 4 * SLG;
+        const float *base;
+        size_t stride;
+        block_src(cs, j, base, stride);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * stride, lane, vx, vy);
+        cp_async_commit();
+    };
+    // one forward step of the pair state (the leader's speed by shuffle)
+    auto fwd_step = [&]() {
+        f2 vcur[NP], vh[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+        leader_vals2<NP>(vcur, vh, lane, lead_in);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+            euler2(st[p], as, vh[p], dt);
+        }
+    };
+
+    const int n_ck = (sc.K + a.C - 1) / a.C;
+    int par = 0;
+    bool have_next = false;  // the next block's stage is already being filled
+    if (a.bwd_pf && n_sub(n_ck - 1) == 1) {
+        prefetch_block(n_ck - 1, 0, 0);
+        have_next = true;
+    }
+    for (int cs = n_ck - 1; cs >= 0; --cs) {
+      const int nsub = n_sub(cs);
+      if (nsub > 1) {  // forward pass over the segment writing the sub-checkpoints
+        {
+            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                st[p].ph = load_pair(base, q, vx[p], vy[p]);
+                st[p].pl = load_pair(base + (size_t)Ns, q, vx[p], vy[p]);
+                st[p].v = load_pair(base + 2 * (size_t)Ns, q, vx[p], vy[p]);
+                const f2 gp = load_pair(base + 3 * (size_t)Ns, q, vx[p], vy[p]);
+                st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+            }
+        }
+        for (int j = 1; j < nsub; ++j) {
+            for (int s = 0; s < T; ++s) fwd_step();
+            float *row = a.sub_ckpt + (size_t)(j - 1) * 4 * a.N_total + sg.veh_begin + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                store_pair(row, q, st[p].ph, vx[p], vy[p]);
+                store_pair(row + (size_t)a.N_total, q, st[p].pl, vx[p], vy[p]);
+                store_pair(row + 2 * (size_t)a.N_total, q, st[p].v, vx[p], vy[p]);
+                store_pair(row + 3 * (size_t)a.N_total, q, st[p].gap, vx[p], vy[p]);
+            }
+        }
+        __threadfence_block();  // the rows are read back below (this thread's own slots)
+      }
+      for (int j = nsub - 1; j >= 0; --j) {
+        const int c0 = cs * a.C + j * T;
+        const int n = min(T, seg_len(cs) - j * T);
+        int obs_k, obs_row;
+        first_obs(c0, obs_k, obs_row);
+        if (!have_next) prefetch_block(cs, j, par);
+        float *tr = trb + par * T * SLG;
+        cp_async_wait<0>();  // this block's targets and starting state (this thread's own slots)
+        {
+            const float *ck = ckb + par * 4 * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                const f2 ph = lds2(ck + q), pl = lds2(ck + SLG + q), v = lds2(ck + 2 * SLG + q);
+                const f2 gp = lds2(ck + 3 * SLG + q);
+                st[p].ph = make_float2(vx[p] ? ph.x : 0.0f, vy[p] ? ph.y : 0.0f);
+                st[p].pl = make_float2(vx[p] ? pl.x : 0.0f, vy[p] ? pl.y : 0.0f);
+                st[p].v = make_float2(vx[p] ? v.x : 0.0f, vy[p] ? v.y : 0.0f);
+                st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+            }
+        }
+        // start filling the other stage with the next block when its state exists
+        have_next = false;
+        if (a.bwd_pf) {
+            if (j > 0) {
+                prefetch_block(cs, j - 1, par ^ 1);
+                have_next = true;
+            } else if (cs > 0 && n_sub(cs - 1) == 1) {
+                prefetch_block(cs - 1, 0, par ^ 1);
+                have_next = true;
+            }
+        }
+        f2 lseg = F2(0.0f);
+        // recompute the segment into the tape
+        for (int s = 0; s < n; ++s) {
+            const int k = c0 + s;
+            float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                sts2(rv + q, st[p].v);
+                sts2(rg + q, st[p].gap);
+            }
+            if (!DENSE && k == obs_k) {
+                if (obs_row < sc.n_obs) {
+                    float *rr = tr + s * SLG + wb;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], lds2(rr + q));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        sts2(rr + q, mul2(seed_scale, r));
+                        lseg = fma2(r, r, lseg);
+                    }
+                }
+                obs_k += sc.obs_stride;
+                ++obs_row;
+            }
+            f2 vcur[NP], vh[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+            const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+            leader_vals2<NP>(vcur, vh, lane, lead_in);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+                euler2(st[p], as, vh[p], dt);
+            }
+        }
+        if (c0 + n == sc.K) {  // state is now at step K: seed of the final step
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = load_pair(a.gP + row, q, vx[p], vy[p]);
+                    lv[p] = a.gV ? load_pair(a.gV + row, q, vx[p], vy[p]) : F2(0.0f);
+                }
+            } else {
+                const int k = sc.K;
+                const bool obs = sc.n_obs > 0 && (k % sc.obs_stride) == 0 && k / sc.obs_stride <= sc.n_obs;
+                if (obs) {
+                    const float *y = a.targets + sc.tgt_off + (size_t)(k / sc.obs_stride - 1) * Ns + wl;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const int q = 64 * p + 2 * lane;
+                        f2 r = residual2(st[p], load_pair(y, q, vx[p], vy[p]));
+                        r.x = vx[p] ? r.x : 0.0f;
+                        r.y = vy[p] ? r.y : 0.0f;
+                        lp[p] = mul2(seed_scale, r);
+                        lseg = fma2(r, r, lseg);
+                    }
+                }
+            }
+        }
+        kahan_add(lsum, lcomp, __fadd_rn(lseg.x, lseg.y));
+        grp_sync(g);  // the whole group's tape is written
+
+        f2 sacc[6][NP];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) sacc[q][p] = F2(0.0f);
+
+        // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
+        int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
+        int obs_hi = row_hi * sc.obs_stride;
+        AdjJac2 J[NP];
+        {
+            const float *rv = tv + (n - 1) * SLG + wb, *rg = tg + (n - 1) * SLG + wb;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                const f2 v = lds2(rv + q);
+                const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+            }
+        }
+        for (int s = n - 1; s >= 0; --s) {
+            const int k = c0 + s;
+            f2 to_lp[NP], to_lv[NP], t1[NP], nlv[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const f2 mu = mul2(F2(dt), lv[p]);
+                to_lp[p] = mul2(mu, J[p].Aph);
+                to_lv[p] = mul2(mu, J[p].Avh);
+                t1[p] = sub2(lp[p], to_lp[p]);                          // lp + mu A_p
+                nlv[p] = fma2(mu, J[p].Av, fma2(F2(dt), lp[p], lv[p]));  // dt lp + lv + mu A_v
+                sacc[0][p] = fma2(mu, J[p].w0n, sacc[0][p]);
+                sacc[1][p] = fma2(mu, J[p].w0nv, sacc[1][p]);
+                sacc[2][p] = fma2(mu, J[p].w0nvdv, sacc[2][p]);
+                sacc[3][p] = fma2(mu, J[p].fa, sacc[3][p]);
+                sacc[4][p] = fma2(mu, J[p].frd, sacc[4][p]);
+                if (WD) sacc[5][p] = fma2(mu, J[p].frdl, sacc[5][p]);
+            }
+            if (s > 0) {
+                const float *rv = tv + (s - 1) * SLG + wb, *rg = tg + (s - 1) * SLG + wb;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    const f2 v = lds2(rv + q);
+                    const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
+                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                }
+            }
+            float in_p, in_v;
+            grp_follow_in(g, to_lp[0].x, to_lv[0].x, in_p, in_v, fp);
+            f2 from_p[NP], from_v[NP];
+            follower_vals2<NP>(to_lp, from_p, lane, in_p);
+            follower_vals2<NP>(to_lv, from_v, lane, in_v);
+            if (DENSE) {
+                const size_t row = sc.traj_off + (size_t)k * Ns + wl;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    lp[p] = add2(add2(t1[p], from_p[p]), load_pair(a.gP + row, q, vx[p], vy[p]));
+                    lv[p] = add2(nlv[p], from_v[p]);
+                    if (a.gV) lv[p] = add2(lv[p], load_pair(a.gV + row, q, vx[p], vy[p]));
+                }
+            } else if (k == obs_hi && k >= 1 && row_hi <= sc.n_obs) {
+                const float *rr = tr + s * SLG + wb;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(add2(t1[p], from_p[p]), lds2(rr + 64 * p + 2 * lane));
+                    lv[p] = add2(nlv[p], from_v[p]);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    lp[p] = add2(t1[p], from_p[p]);
+                    lv[p] = add2(nlv[p], from_v[p]);
+                }
+            }
+            if (!DENSE && k == obs_hi) {
+                obs_hi -= sc.obs_stride;
+                --row_hi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float *ap = acc + q * SLG + wb + 64 * p + 2 * lane;
+                sts2(ap, add2(lds2(ap), sacc[q][p]));
+            }
+        grp_sync(g);  // the tape may be overwritten by the next block
+        if (a.bwd_pf) par ^= 1;
+      }
+    }
+
+    // epilogue: parameter gradients from the factored sums
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(c ? vy[p] : vx[p])) continue;
+            const int q = wb + 64 * p + 2 * lane + c;
+            const int gi = sg.veh_begin + q;
+            const float v0 = a.v0[gi], b = a.b[gi];
+            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
+            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
+            const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
+            const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+            float gr[6];
+            gr[0] = am * dl * A4 / v0;                 // v0
+            gr[1] = -A1;                               // T
+            gr[2] = -A0;                               // s0
+            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
+            gr[4] = A2 * cc / (2.0f * b);              // b
+            gr[5] = -am * A5;                          // delta
+            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
+            if (ADAM) {
+                const int it = a.iter;
+                const int t = it + 1;
+                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
+                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const size_t mi = (size_t)r * a.N_total + gi;
+                    float m = 0.9f * a.adam_m[mi] + 0.1f * gr[r];
+                    float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[r] * gr[r];
+                    a.adam_m[mi] = m;
+                    a.adam_v[mi] = vv;
+                    float x = th[r][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+                    x = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
+                    th[r][gi] = x;
+                }
+            } else {
+                if (a.g_v0) a.g_v0[gi] = gr[0];
+                if (a.g_T) a.g_T[gi] = gr[1];
+                if (a.g_s0) a.g_s0[gi] = gr[2];
+                if (a.g_am) a.g_am[gi] = gr[3];
+                if (a.g_b) a.g_b[gi] = gr[4];
+                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
+                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
+                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
+            }
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (!DENSE) {
+        const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
+    }
+}
+
+// Register budgets: 2 vehicles per thread fit 128 registers (2 blocks of 8
+// warps per SM); 4 per thread need ~168 without spilling, so their blocks
+// are 4 warps (3 blocks per SM) unless the segment has 8 warps (BIG, 256
+// threads, one block per SM); 8 per thread use up to 255.
+template <int VPT, bool BIG>
+struct BwdBounds {
+    static constexpr int threads = (VPT == 4 && !BIG) ? 128 : 256;
+    static constexpr int blocks = VPT == 2 ? 2 : ((VPT == 4 && !BIG) ? 3 : 1);
+};
+
+template <int VPT, bool DENSE, bool ADAM, bool WD, bool BIG, bool SUB>
+__global__ void __launch_bounds__(BwdBounds<VPT, BIG>::threads, BwdBounds<VPT, BIG>::blocks)
+backward_kernel(SimArgs a)
+{
+    constexpr int NP = VPT / 2;
+    extern __shared__ float smem[];
+    const int G = a.G;
+    const int warp = threadIdx.x >> 5;
+    float *gbase = smem + (warp / G) * bwd_group_floats(VPT, DENSE, a.tape_T, G, a.bwd_pf != 0);
+    float *ctrl = gbase + bwd_group_floats(VPT, DENSE, a.tape_T, G, a.bwd_pf != 0) - grp_ctrl_floats(G);
+    Grp g = make_grp(G, ctrl);
+    int par = 0;
+    for (;;) {
+        const int s_idx = grp_next(g, a.work, par);
+        if (s_idx >= *a.n_seg) break;
+        const Seg sg = a.seg[s_idx];
+        const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
+        const int lb = sg.veh_begin - sc.veh_begin;
+        VehConst2 kc[NP];
+        State2 st[NP];
+        bool vx[NP], vy[NP];
+        load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
+        if constexpr (SUB) {
+            if (segment_is_d4<NP>(kc, vx, vy))
+                backward_segment_blocks<NP, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
+            else
+                backward_segment_blocks<NP, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
+        } else {
+            if (segment_is_d4<NP>(kc, vx, vy))
+                backward_segment<NP, DENSE, ADAM, WD, true>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
+            else
+                backward_segment<NP, DENSE, ADAM, WD, false>(a, sc, sg, s_idx, lb, g, gbase, kc, st, vx, vy);
+        }
+    }
+}
+
+// Kernel variants of one vehicles-per-thread value: seeds from dense
+// gradients or from targets, fused Adam or gradient output, with or without
+// the delta gradient, block form (BIG) and tape blocks (SUB).
+template <int VPT, bool BIG, bool SUB>
+inline void *backward_fn_t(bool dense, bool adam, bool wd)
+{
+    if (dense)
+        return wd ? (void *)backward_kernel<VPT, true, false, true, BIG, SUB>
+                  : (void *)backward_kernel<VPT, true, false, false, BIG, SUB>;
+    if (adam) return (void *)backward_kernel<VPT, false, true, false, BIG, SUB>;
+    return wd ? (void *)backward_kernel<VPT, false, false, true, BIG, SUB>
+              : (void *)backward_kernel<VPT, false, false, false, BIG, SUB>;
+}
+
+}  // namespace idm

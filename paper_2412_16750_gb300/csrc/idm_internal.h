@@ -47,6 +47,8 @@ struct SimArgs {
     double *loss_part;          // [n_seg * G] per-warp loss
     float *ckpt;
     int C;                      // checkpoint interval (steps)
+    int tape_T;                 // adjoint tape depth (steps, <= C); tape_T < C uses sub_ckpt
+    float *sub_ckpt;            // [ceil(C/tape_T)-1][4][N_total] states inside a checkpoint segment
     unsigned *status;
     // adjoint
     const float *gP, *gV;       // dense trajectory gradients (scenario-local time-major)
@@ -80,7 +82,7 @@ cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, con
                            cudaStream_t st);
 cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool want_delta, const SimArgs &a,
                             int grid, int wpb, cudaStream_t st);
-size_t backward_smem_bytes(int vpt, bool dense_seed, int C, int G, int wpb, bool prefetch);
+size_t backward_smem_bytes(int vpt, bool dense_seed, int T, int G, int wpb, bool prefetch);
 size_t forward_smem_bytes(int vpt, int G, int wpb);
 // Largest adjoint block (warps) for a shape: 4 for 4 vehicles per thread in
 // segments of up to 4 warps (register budget), else 8.
@@ -88,7 +90,14 @@ int backward_max_warps(int vpt, int G);
 // Adjoint warps per SM the register budgets allow for a shape.
 int backward_resident_warps(int vpt, int G);
 cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st);
-int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem);
+int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem,
+                     bool sub = false);
+// Adjoint kernel variants (idm_adjoint{2,4,8}.cu): dense or target seeds,
+// fused Adam, delta gradient, 8-warp block form (4 vehicles/thread only),
+// tape blocks with sub-checkpoints.
+void *backward_fn_vpt2(bool dense, bool adam, bool wd, bool big, bool sub);
+void *backward_fn_vpt4(bool dense, bool adam, bool wd, bool big, bool sub);
+void *backward_fn_vpt8(bool dense, bool adam, bool wd, bool big, bool sub);
 
 // Layout (idm_layout.cu).
 cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,

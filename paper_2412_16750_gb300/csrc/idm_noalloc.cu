@@ -133,6 +133,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
     const bool want_delta = grad && grad->delta;
     if ((rc = forward_grid(&c, &P, (int)L))) return rc;
     if ((rc = backward_grid(&c, &P, false, false, want_delta, (int)L))) return rc;
+    if (P.a.tape_T != c.C) return IDM_ERR_WORKSPACE;  // would need sub-checkpoint scratch
 
     // the array keeps the previous call's contents: clear counters and status
     if (cudaMemsetAsync(base, 0, o_seg, st) != cudaSuccess) return IDM_ERR_CUDA;
