@@ -291,7 +291,7 @@ def time_to_fit(a, dev):
     time until the fitted trajectory is within --rmse-target (RMSE against
     the noise-free truth) and the network's training throughput."""
     import torch
-    from paper_2412_16750_gb300 import api, synth
+    from paper_2412_16750_gb300 import api, synth, tune
     cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -351,6 +351,10 @@ def time_to_fit(a, dev):
     plain = cu(synth.plain_init(N))
     ctx = api.Context()
     th_buf = torch.empty_like(plain)
+    # kernel shape for this problem size (autotuner, cached per GPU)
+    sig = tune.signature(100, N, K, 1, kind="fit")
+    shape, shape_src, _ = tune.tuned(ctx, lambda c: api.loss_grad(plain, p0, v0, scene, K, DT, Y, 1, ctx=c,
+                                                                  want_state_grad=False), 100, sig, repeats=3)
 
     def timed(fn):
         e0, e1 = ev(), ev()
@@ -393,6 +397,8 @@ def time_to_fit(a, dev):
     out["fit"] = {"workload": "2000 lanes x 100 vehicles (200K), 100 steps, every step observed, noise 0.5 m; "
                               "Adam %d iterations, lr 0.1 -> 0.01" % a.fit_iters,
                   "rmse_target_m": a.rmse_target, "ms_per_iteration": ms_iter,
+                  "shape": {"vpt": shape[0], "warps_per_segment": shape[1], "ckpt_interval": shape[2],
+                            "warps_per_block": shape[3], "source": shape_src},
                   "plain": {"iterations": it_plain, "seconds": wall(it_plain, 0.0),
                             "rmse_m_at": {str(i): float(rmse_plain[i]) for i in (0, 10, 50, 100, a.fit_iters - 1)
                                           if i < a.fit_iters}},

@@ -108,8 +108,9 @@ int idm_mlp_forward(idm_mlp_t *mlp, const void *X, int32_t B, float *out, void *
 
 /* Initial parameters for a fit: for each row r < B, params->{v0, T, s0,
  * a_max, b}[r] = box_lo + (box_hi - box_lo) * sigmoid(o) (box HOST [5]);
- * params->delta is not touched.  Rows are processed in chunks of max_batch,
- * so B may exceed max_batch. */
+ * params->delta is not touched.  B may exceed max_batch: larger inputs are
+ * processed in chunks of 131,072 rows through two activation buffers
+ * (128 MiB) that the first such call allocates and the network keeps. */
 int idm_mlp_predict_params(idm_mlp_t *mlp, const void *X, int32_t B, idm_params_t *params, const float *box_lo,
                            const float *box_hi, void *stream);
 

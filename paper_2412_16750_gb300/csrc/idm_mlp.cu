@@ -452,6 +452,11 @@ struct idm_mlp {
     double *loss_part = nullptr, *loss_tmp = nullptr;
     unsigned *status = nullptr;
     int t = 0;  // Adam steps taken
+    // inference ping-pong activations for chunks larger than the training
+    // batch (allocated by the first inference call that needs them)
+    void *inf_arena = nullptr;
+    bf16 *IH[2] = {};
+    int inf_rows = 0;
     char err[256] = {0};
 };
 
@@ -496,12 +501,17 @@ GemmArgs base_args(idm_mlp *n)
 }
 
 // Forward through the three hidden layers for Bp rows (X rows < B valid).
-// store_train: keep Z and the transposed activations for the backward pass.
-int hidden_forward(idm_mlp *n, const bf16 *X, int B, int Bp, bool store_train, cudaStream_t st)
+// store_train: keep Z and the transposed activations for the backward pass
+// (outputs in H[0..2]); otherwise the activations alternate between the two
+// buffers of out (the last layer's lands in out[0]).
+int hidden_forward(idm_mlp *n, const bf16 *X, int B, int Bp, bool store_train, cudaStream_t st,
+                   bf16 *const *out = nullptr)
 {
     for (int l = 0; l < 3; ++l) {
+        bf16 *dst = store_train || !out ? n->H[l] : out[l & 1 ? 1 : 0];
+        const bf16 *src = l == 0 ? X : (store_train || !out ? n->H[l - 1] : out[(l - 1) & 1 ? 1 : 0]);
         GemmArgs g = base_args(n);
-        g.A = l == 0 ? X : n->H[l - 1];
+        g.A = src;
         g.B = n->Wb[l];
         g.M_valid = l == 0 ? B : Bp;
         g.M_rows = Bp;
@@ -511,7 +521,7 @@ int hidden_forward(idm_mlp *n, const bf16 *X, int B, int Bp, bool store_train, c
         g.k_chunk = g.K;
         g.bias = n->w + (l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : OFF_B3);
         g.Z = store_train ? n->Z[l] : nullptr;
-        g.H = n->H[l];
+        g.H = dst;
         g.HT = store_train ? n->HT[l] : nullptr;
         g.ldt = Bp;
         MCK(gemm<GELU_FWD>(g, Bp, 1, st));
@@ -617,6 +627,36 @@ int fwd_bwd(idm_mlp *n, const bf16 *X, const float *labels, int B, double *loss_
         up = n->dZ[buf];
         up_width = HID;
     }
+    return IDM_OK;
+}
+
+// Rows per inference chunk and the activation buffers for it: the training
+// buffers when the chunk fits them, else dedicated ping-pong buffers of
+// INFER_CHUNK rows.
+constexpr int INFER_CHUNK = 131072;
+
+int infer_buffers(idm_mlp *n, int B, int *chunk, bf16 **buf)
+{
+    if (B <= n->bp_cap) {
+        *chunk = n->max_batch;
+        buf[0] = n->H[0];
+        buf[1] = n->H[1];
+        return IDM_OK;
+    }
+    if (!n->inf_arena) {
+        const size_t bytes = 2 * (size_t)INFER_CHUNK * HID * sizeof(bf16);
+        if (cudaMalloc(&n->inf_arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            n->inf_arena = nullptr;
+            return mfail(n, IDM_ERR_CUDA, "cannot allocate %zu bytes of inference buffers", bytes);
+        }
+        n->IH[0] = (bf16 *)n->inf_arena;
+        n->IH[1] = n->IH[0] + (size_t)INFER_CHUNK * HID;
+        n->inf_rows = INFER_CHUNK;
+    }
+    *chunk = n->inf_rows;
+    buf[0] = n->IH[0];
+    buf[1] = n->IH[1];
     return IDM_OK;
 }
 
@@ -784,10 +824,9 @@ int idm_mlp_create(idm_mlp_t **out, int32_t max_batch)
 int idm_mlp_destroy(idm_mlp_t *n)
 {
     if (!n) return IDM_OK;
-    if (n->arena) {
-        cudaDeviceSynchronize();
-        cudaFree(n->arena);
-    }
+    if (n->arena || n->inf_arena) cudaDeviceSynchronize();
+    if (n->arena) cudaFree(n->arena);
+    if (n->inf_arena) cudaFree(n->inf_arena);
     delete n;
     return IDM_OK;
 }
@@ -912,14 +951,16 @@ int idm_mlp_predict_params(idm_mlp_t *n, const void *X, int32_t B, idm_params_t 
     if (!box_lo || !box_hi) return mfail(n, IDM_ERR_ARG, "box_lo and box_hi (host) are required");
     cudaStream_t st = (cudaStream_t)stream;
     float *outs[OUT] = {params->v0, params->T, params->s0, params->a_max, params->b};
-    for (int r0 = 0; r0 < B; r0 += n->max_batch) {
-        const int b = std::min(n->max_batch, B - r0);
+    int chunk, rc;
+    bf16 *buf[2];
+    if ((rc = infer_buffers(n, B, &chunk, buf))) return rc;
+    for (int r0 = 0; r0 < B; r0 += chunk) {
+        const int b = std::min(chunk, B - r0);
         const int Bp = round128(b);
         const bf16 *Xc = (const bf16 *)X + (size_t)r0 * IN;
-        int rc;
-        if ((rc = hidden_forward(n, Xc, b, Bp, false, st))) return rc;
+        if ((rc = hidden_forward(n, Xc, b, Bp, false, st, buf))) return rc;
         GemmArgs g = base_args(n);
-        g.A = n->H[2];
+        g.A = buf[0];
         g.B = n->Wb[3];
         g.M_valid = b;
         g.M_rows = Bp;

@@ -247,3 +247,21 @@ def test_learned_init_beats_plain(api):
     r_plain = fit_rmse(synth.plain_init(1000), 30)
     r_learned = fit_rmse(th_learned.double().cpu().numpy(), 30)
     assert r_learned < r_plain, (r_learned, r_plain)
+
+
+def test_predict_params_large_chunks_match_one_pass(api):
+    """More rows than one inference chunk (131,072): the chunked pass through
+    the network's inference buffers equals one pass through the training
+    buffers of a network sized for all rows (same kernels per row)."""
+    B = 131072 + 1000
+    w = synth.mlp_init(5)
+    rng = np.random.default_rng(70)
+    X = to_bf16_cuda(rng.normal(scale=0.7, size=(B, 80)))
+    a, b = api.Mlp(max_batch=1024, weights=w), api.Mlp(max_batch=B, weights=w)
+    ta = torch.zeros((6, B), device="cuda", dtype=torch.float32)
+    tb = torch.zeros((6, B), device="cuda", dtype=torch.float32)
+    a.predict_params(X, ta)
+    b.predict_params(X, tb)
+    torch.cuda.synchronize()
+    assert torch.equal(ta, tb)
+    assert a.status() == (0, 0) and b.status() == (0, 0)
