@@ -90,12 +90,14 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
-// Epilogue of one 128 x BN tile; thread = row m0 + threadIdx.x, tw = this
-// warp's tensor-memory lane base.
+// Epilogue of one accumulator row: row r of the output, tw = the tensor-
+// memory address of this row's column 0 of the tile, columns [c0, c1) of the
+// tile (global column n0 + c), split = K-split index (F32_PART), loss_slot =
+// this warp's loss partial (OUT_TRAIN, written by lane 0).
 template <int MODE>
-__device__ __forceinline__ void epilogue(const GemmArgs &g, const tc::TileArgs &t, uint32_t tw, bool empty)
+__device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t tw, int n0, int c0, int c1, bool empty,
+                                             int split, int loss_slot)
 {
-    const int r = t.m0 + threadIdx.x;
     const bool row_ok = r < g.M_rows;
     if constexpr (MODE == OUT_TRAIN || MODE == OUT_INFER) {
         float v[16];
@@ -138,9 +140,9 @@ __device__ __forceinline__ void epilogue(const GemmArgs &g, const tc::TileArgs &
             for (int i = 0; i < OUTP; ++i) g.HT[(size_t)i * g.ldt + r] = __float2bfloat16_rn(d[i]);
         }
         l = warp_sum(l);
-        if ((threadIdx.x & 31) == 0) g.loss_part[blockIdx.x * 4 + (threadIdx.x >> 5)] = l * (double)g.scale;
+        if ((threadIdx.x & 31) == 0) g.loss_part[loss_slot] = l * (double)g.scale;
     } else {
-        for (int c = 0; c < t.BN; c += 16) {
+        for (int c = c0; c < c1; c += 16) {
             float v[16];
             if (empty) {
 #pragma unroll
@@ -148,9 +150,9 @@ __device__ __forceinline__ void epilogue(const GemmArgs &g, const tc::TileArgs &
             } else {
                 tc::tmem_ld16(tw + (uint32_t)c, v);
             }
-            const int n = t.n0 + c;
+            const int n = n0 + c;
             if (MODE == F32_PART) {
-                if (row_ok) store16_f32(g.Cf + ((size_t)blockIdx.z * g.M_rows + r) * g.N + n, v);
+                if (row_ok) store16_f32(g.Cf + ((size_t)split * g.M_rows + r) * g.N + n, v);
                 continue;
             }
             float h[16];
@@ -220,7 +222,9 @@ __global__ void __launch_bounds__(tc::NTHREADS) mlp_gemm_kernel(const GemmArgs g
     t.ke = min(g.K, t.kb + g.k_chunk);
     bool empty = false;
     const bool ok = tc::mainloop(t, smem, tmem, g.status, &empty);
-    if (ok) epilogue<MODE>(g, t, tmem + ((uint32_t)(warp * 32) << 16), empty);
+    if (ok)
+        epilogue_row<MODE>(g, t.m0 + threadIdx.x, tmem + ((uint32_t)(warp * 32) << 16), t.n0, 0, t.BN, empty, blockIdx.z,
+                           blockIdx.x * 4 + warp);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -239,6 +243,207 @@ cudaError_t gemm(const GemmArgs &g, int M_tiles_rows, int splits, cudaStream_t s
     dim3 grid((M_tiles_rows + tc::BM - 1) / tc::BM, g.N / g.BN, splits);
     mlp_gemm_kernel<MODE><<<grid, tc::NTHREADS, smem, st>>>(g);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent weight-stationary GEMM for the batch-sized products
+// (C[M x N] = A[M x K] . W[N x K]^T with N <= 256, K <= 256): each CTA keeps W
+// in shared memory and walks 128-row tiles of A.  Warp 0 streams the A tiles
+// (64 columns per stage, 4-stage ring) with cp.async, warp 1 (one thread)
+// issues the tcgen05.mma of a tile into one of two tensor-memory
+// accumulators, warps 2-9 run the epilogue of the previous tile from the
+// other accumulator.  Hand-offs are mbarriers: full / empty per stage, full /
+// empty per accumulator.  Every wait is bounded and shares an abort flag, so
+// a role that gives up releases the others.
+// ---------------------------------------------------------------------------
+namespace ws {
+constexpr int STAGES = 4;
+constexpr int LAG = 2;          // copy groups in flight before the producer marks a stage full
+constexpr int EPI_WARPS = 8;    // two per tensor-memory lane quarter (column halves)
+constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+__host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
+__host__ __device__ constexpr int ctl_off(int N, int K) { return w_bytes(N, K) + STAGES * tc::A_STAGE_BYTES; }
+__host__ __device__ constexpr int smem_bytes(int N, int K) { return ctl_off(N, K) + 128; }
+}  // namespace ws
+
+template <int MODE>
+__global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const GemmArgs g)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int N = g.N, K = g.K, KC = K >> 3;
+    const int nkt = (K + tc::BK - 1) / tc::BK;
+    const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
+    const uint32_t acc_cols = tc::tmem_cols_for(N), ncols = 2 * acc_cols;
+    const uint32_t sW = tc::smem_u32(smem), sA = sW + ws::w_bytes(N, K);
+    uint8_t *ctl = smem + ws::ctl_off(N, K);
+    const uint32_t bars = tc::smem_u32(ctl);
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (ws::STAGES + s); };
+    auto tfull_bar = [&](int a) { return bars + 8u * (2 * ws::STAGES + a); };
+    auto tempty_bar = [&](int a) { return bars + 8u * (2 * ws::STAGES + 2 + a); };
+    const uint32_t wbar = bars + 8u * (2 * ws::STAGES + 4), drain = wbar + 8u;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ctl + 8 * (2 * ws::STAGES + 6));
+    volatile int *abort = reinterpret_cast<volatile int *>(ctl + 8 * (2 * ws::STAGES + 6) + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), ncols);
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < ws::STAGES; ++s) {
+            tc::mbar_init(full_bar(s), 1);
+            tc::mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tfull_bar(a), 1);
+            tc::mbar_init(tempty_bar(a), ws::EPI_WARPS);
+        }
+        tc::mbar_init(wbar, 1);
+        tc::mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: W once, then the A tiles -------------------------------
+        for (int c = lane; c < N * KC; c += 32) {
+            const int row = c / KC, kc = c - row * KC;
+            tc::cp_async16(sW + (uint32_t)(((row >> 3) * KC + kc) * 128 + (row & 7) * 16), g.B + (size_t)row * K + kc * 8,
+                           16u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(wbar);
+        int q = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int m0 = tile * tc::BM;
+            for (int kt = 0; kt < nkt; ++kt) {
+                const int s = q % ws::STAGES;
+                int got = lane == 0 ? (int)tc::mbar_wait_abort(empty_bar(s), (uint32_t)(((q / ws::STAGES) & 1) ^ 1), abort) : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                const int k0 = kt * tc::BK, nch = min(tc::BK, K - k0) >> 3;
+                const uint32_t dst = sA + (uint32_t)s * tc::A_STAGE_BYTES;
+                for (int c = lane; c < tc::BM * 8; c += 32) {
+                    const int row = c >> 3, kc = c & 7;
+                    if (kc >= nch) continue;
+                    const int m = m0 + row;
+                    const bool in = m < g.M_valid;
+                    tc::cp_async16(dst + tc::tile_off(row, kc), g.A + (size_t)(in ? m : 0) * K + k0 + kc * 8, in ? 16u : 0u);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                if (q >= ws::LAG) {  // the stage LAG groups back has landed
+                    asm volatile("cp.async.wait_group %0;" ::"n"(ws::LAG) : "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(full_bar((q - ws::LAG) % ws::STAGES));
+                }
+                ++q;
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+            for (int r = max(0, q - ws::LAG); r < q; ++r) tc::mbar_arrive(full_bar(r % ws::STAGES));
+    } else if (warp == 1) {
+        // ---- MMA issue (one thread) --------------------------------------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(tc::BM, N);
+            bool ok = tc::mbar_wait_abort(wbar, 0, abort);
+            int q = 0, i = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++i) {
+                const int acc = i & 1, u = i >> 1;
+                if (!(ok = tc::mbar_wait_abort(tempty_bar(acc), (uint32_t)((u & 1) ^ 1), abort))) break;
+                tc::fence_after_sync();
+                for (int kt = 0; kt < nkt && ok; ++kt, ++q) {
+                    const int s = q % ws::STAGES;
+                    if (!(ok = tc::mbar_wait_abort(full_bar(s), (uint32_t)((q / ws::STAGES) & 1), abort))) break;
+                    tc::fence_after_sync();
+                    const int kw = min(tc::BK, K - kt * tc::BK);
+                    const uint32_t a_buf = sA + (uint32_t)s * tc::A_STAGE_BYTES;
+                    for (int ks = 0; ks < (kw >> 4); ++ks) {
+                        const uint64_t ad = tc::smem_desc(a_buf + ks * 256, 128, 1024);
+                        const uint64_t bd = tc::smem_desc(sW + (uint32_t)(kt * 8 + ks * 2) * 128, 128, (uint32_t)KC * 128);
+                        tc::mma_bf16(tmem + (uint32_t)acc * acc_cols, ad, bd, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(empty_bar(s));
+                }
+                if (ok) tc::mma_commit(tfull_bar(acc));
+            }
+            // everything issued has completed before the tensor memory is freed
+            tc::mma_commit(drain);
+            tc::mbar_wait(drain, 0);
+        }
+    } else {
+        // ---- epilogue warps ------------------------------------------------------
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int nch = N >> 4, h0 = (nch + 1) >> 1;
+        const int c0 = half ? h0 * 16 : 0, c1 = half ? N : h0 * 16;
+        const bool out_mode = MODE == OUT_TRAIN || MODE == OUT_INFER;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int acc = i & 1, u = i >> 1;
+            int got = lane == 0 ? (int)tc::mbar_wait_abort(tfull_bar(acc), (uint32_t)(u & 1), abort) : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            tc::fence_after_sync();
+            const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * acc_cols;
+            const int r = tile * tc::BM + quarter * 32 + lane;
+            if (out_mode ? half == 0 : c1 > c0)
+                epilogue_row<MODE>(g, r, tw, 0, c0, c1, false, 0, tile * 4 + quarter);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tempty_bar(acc));
+        }
+    }
+    if (threadIdx.x == 0 && *abort) atomicOr(g.status, IDM_STATUS_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
+// Launch of the persistent GEMM: one CTA per SM (or fewer tiles).
+template <int MODE>
+cudaError_t gemm_ws(const GemmArgs &g, int n_sm, cudaStream_t st)
+{
+    const int smem = ws::smem_bytes(g.N, g.K);
+    cudaError_t e = cudaFuncSetAttribute(mlp_gemm_ws_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_gemm_ws_kernel<MODE>, ws::NTHREADS, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    // resident CTAs must also fit the 512 tensor-memory columns of an SM
+    // (a CTA that cannot allocate would wait for another to finish)
+    occ = std::max(1, std::min(occ, (int)(512 / (2 * tc::tmem_cols_for(g.N)))));
+    const int grid = std::max(1, std::min(ntiles, n_sm * occ));
+    mlp_gemm_ws_kernel<MODE><<<grid, ws::NTHREADS, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+// Batch-sized product: the persistent kernel when there are enough row tiles
+// to keep every SM busy for several tiles (it loads the whole weight matrix
+// once per CTA and overlaps each tile's epilogue with the next tile's
+// products), else one CTA per 128 x BN tile.
+template <int MODE>
+cudaError_t gemm_batch(const GemmArgs &g, int n_sm, cudaStream_t st)
+{
+    const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
+    if (ntiles >= 2 * n_sm) return gemm_ws<MODE>(g, n_sm, st);
+    return gemm<MODE>(g, g.M_rows, 1, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,7 +729,7 @@ int hidden_forward(idm_mlp *n, const bf16 *X, int B, int Bp, bool store_train, c
         g.H = dst;
         g.HT = store_train ? n->HT[l] : nullptr;
         g.ldt = Bp;
-        MCK(gemm<GELU_FWD>(g, Bp, 1, st));
+        MCK(gemm_batch<GELU_FWD>(g, n->n_sm, st));
     }
     return IDM_OK;
 }
@@ -559,7 +764,7 @@ int fwd_bwd(idm_mlp *n, const bf16 *X, const float *labels, int B, double *loss_
         g.label = labels;
         g.loss_part = n->loss_part;
         g.scale = 1.0f / (5.0f * (float)B);
-        MCK(gemm<OUT_TRAIN>(g, Bp, 1, st));
+        MCK(gemm_batch<OUT_TRAIN>(g, n->n_sm, st));
         idm::mlp::loss_sum_kernel<<<1, 256, 0, st>>>(n->loss_part, Bp / 128 * 4, loss_out ? loss_out : n->loss_tmp,
                                                       n->status);
         MCK(cudaGetLastError());
@@ -602,7 +807,7 @@ int fwd_bwd(idm_mlp *n, const bf16 *X, const float *labels, int B, double *loss_
             g.H = l > 0 ? n->dZ[buf] : nullptr;
             g.HT = n->dZT[buf];
             g.ldt = Bp;
-            MCK(gemm<DGELU>(g, Bp, 1, st));
+            MCK(gemm_batch<DGELU>(g, n->n_sm, st));
         }
         // dW_l = dZ_l^T . H_{l-1}  (M = 256, N = fan-in, K = Bp)
         {
@@ -936,7 +1141,7 @@ int idm_mlp_forward(idm_mlp_t *n, const void *X, int32_t B, float *out, void *st
     g.k_chunk = HID;
     g.bias = n->w + OFF_B4;
     g.out[0] = out;
-    MCK(gemm<OUT_INFER>(g, Bp, 1, st));
+    MCK(gemm_batch<OUT_INFER>(g, n->n_sm, st));
     return IDM_OK;
 }
 
@@ -974,7 +1179,7 @@ int idm_mlp_predict_params(idm_mlp_t *n, const void *X, int32_t B, idm_params_t 
             g.lo[q] = box_lo[q];
             g.hi[q] = box_hi[q];
         }
-        MCK(gemm<OUT_INFER>(g, Bp, 1, st));
+        MCK(gemm_batch<OUT_INFER>(g, n->n_sm, st));
     }
     return IDM_OK;
 }

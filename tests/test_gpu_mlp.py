@@ -265,3 +265,25 @@ def test_predict_params_large_chunks_match_one_pass(api):
     torch.cuda.synchronize()
     assert torch.equal(ta, tb)
     assert a.status() == (0, 0) and b.status() == (0, 0)
+
+
+def test_persistent_gemm_path_matches_oracle(api):
+    """A batch large enough (>= 2 row tiles per SM) for the persistent
+    weight-stationary kernel in every batch-sized product: forward outputs,
+    loss and gradients against the FP64 oracle."""
+    B = 2 * 152 * 128 + 77
+    w = synth.mlp_init(6)
+    X, T = random_batch(B, 80)
+    Xc, Tc = to_bf16_cuda(X), torch.as_tensor(T, dtype=torch.float32, device="cuda")
+    net = api.Mlp(max_batch=B, weights=w)
+    wb = bf16_weights(w)
+    S = net.forward(Xc).double().cpu().numpy()
+    np.testing.assert_allclose(S, M.forward(wb, X)["s"], rtol=1e-2, atol=1e-3)
+    loss, g = net.loss_grad(Xc, Tc)
+    torch.cuda.synchronize()
+    L_ref, g_ref = M.loss_grad(wb, X, synth.f32(T))
+    assert abs(loss.item() - L_ref) <= 1e-2 * L_ref
+    gd, rd = M.unpack(g.double().cpu().numpy()), M.unpack(g_ref)
+    for name, _ in M.SHAPES:
+        assert cosine(gd[name], rd[name]) >= 0.999, name
+    assert net.status() == (0, 0)
