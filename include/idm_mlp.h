@@ -8,7 +8,8 @@
  * (v0, T, s0, a_max, b), so that gradient fitting (idm_fit) starts closer
  * to the solution.  The plain initial guess remains the fallback.
  *
- * Network: 80 -> 256 -> 256 -> 256 -> 5, GELU (erf form) after the three
+ * Network: 80 -> 256 -> 256 -> 256 -> 5, GELU (erf form, erf evaluated
+ * with Abramowitz & Stegun 7.1.26 to 1.5e-7) after the three
  * hidden layers, sigmoid on the output mapped linearly onto the parameter
  * box: theta_q = lo_q + (hi_q - lo_q) * sigmoid(o_q).  153,605 parameters.
  * Weights and activations are bf16, products accumulate in FP32 on the
@@ -64,6 +65,12 @@ typedef struct idm_mlp idm_mlp_t;
  * it is exported so that it can be tested on its own. */
 int idm_gemm_bf16(const void *A, const void *B, int32_t M, int32_t N, int32_t K, float *C, uint32_t *status,
                   void *stream);
+
+/* The activation the network's kernels use, on n values (device arrays;
+ * either output may be NULL): gelu(z) = z Phi(z) and gelu'(z) = Phi(z) +
+ * z phi(z), with erf from Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7).
+ * Exported so that the approximation can be tested on its own. */
+int idm_mlp_gelu_eval(const float *z, float *gelu_out, float *gelu_grad_out, int32_t n, void *stream);
 
 /* ---- network object -------------------------------------------------------
  * Creates the network on the current device with workspace for batches of

@@ -26,6 +26,7 @@
 
 #include "../../include/idm.h"
 #include "../../include/idm_mlp.h"
+#include "idm_device.cuh"
 #include "idm_gemm_tc.cuh"
 
 namespace idm {
@@ -60,10 +61,43 @@ struct GemmArgs {
     unsigned *status;
 };
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 and density phi(z) with erf
+// from Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.26: for x >= 0, erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5))))
+// exp(-x^2) with t = 1 / (1 + p x), |error| <= 1.5e-7; odd in x.  The
+// exponential exp(-x^2) = exp(-z^2 / 2) is shared with phi.
+struct NormalCdf {
+    float cdf, pdf;
+};
+__device__ __forceinline__ NormalCdf normal_cdf(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = idm::rcp_approx(fmaf(0.3275911f, x, 1.0f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    const float e = idm::ex2_approx(-x * x * 1.44269504088896341f);  // exp(-x^2)
+    const float half_tail = 0.5f * t * poly * e;            // (1 - erf(x)) / 2
+    NormalCdf r;
+    r.cdf = z >= 0.0f ? 1.0f - half_tail : half_tail;
+    r.pdf = 0.39894228040143268f * e;
+    return r;
+}
+
+__device__ __forceinline__ float gelu(float z) { return z * normal_cdf(z).cdf; }
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    const NormalCdf n = normal_cdf(z);
+    return fmaf(z, n.pdf, n.cdf);
+}
+
+__global__ void gelu_eval_kernel(const float *z, float *g, float *dg, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (g) g[i] = gelu(z[i]);
+    if (dg) dg[i] = gelu_grad(z[i]);
 }
 __device__ __forceinline__ float sigmoid(float o) { return 1.0f / (1.0f + expf(-o)); }
 
@@ -96,7 +130,7 @@ __device__ __forceinline__ double warp_sum(double x)
 // this warp's loss partial (OUT_TRAIN, written by lane 0).
 template <int MODE>
 __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t tw, int n0, int c0, int c1, bool empty,
-                                             int split, int loss_slot)
+                                             int split, int loss_slot, const float *bias)
 {
     const bool row_ok = r < g.M_rows;
     if constexpr (MODE == OUT_TRAIN || MODE == OUT_INFER) {
@@ -109,7 +143,7 @@ __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t 
         }
         float s[OUT];
 #pragma unroll
-        for (int q = 0; q < OUT; ++q) s[q] = sigmoid(v[q] + g.bias[q]);
+        for (int q = 0; q < OUT; ++q) s[q] = sigmoid(v[q] + bias[q]);
         if constexpr (MODE == OUT_INFER) {
             if (r < g.M_valid) {
                 if (g.out[1]) {
@@ -158,7 +192,7 @@ __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t 
             float h[16];
             if (MODE == GELU_FWD) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += g.bias[n + i];
+                for (int i = 0; i < 16; ++i) v[i] += bias[n + i];
                 if (g.Z && row_ok) store16_f32(g.Z + (size_t)r * g.N + n, v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) h[i] = gelu(v[i]);
@@ -224,7 +258,7 @@ __global__ void __launch_bounds__(tc::NTHREADS) mlp_gemm_kernel(const GemmArgs g
     const bool ok = tc::mainloop(t, smem, tmem, g.status, &empty);
     if (ok)
         epilogue_row<MODE>(g, t.m0 + threadIdx.x, tmem + ((uint32_t)(warp * 32) << 16), t.n0, 0, t.BN, empty, blockIdx.z,
-                           blockIdx.x * 4 + warp);
+                           blockIdx.x * 4 + warp, g.bias);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -257,13 +291,20 @@ cudaError_t gemm(const GemmArgs &g, int M_tiles_rows, int splits, cudaStream_t s
 // a role that gives up releases the others.
 // ---------------------------------------------------------------------------
 namespace ws {
-constexpr int STAGES = 4;
-constexpr int LAG = 2;          // copy groups in flight before the producer marks a stage full
+constexpr int MAX_STAGES = 8;
 constexpr int EPI_WARPS = 8;    // two per tensor-memory lane quarter (column halves)
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr int CTL_BYTES = 8 * (2 * MAX_STAGES + 6) + 16;
+constexpr int SMEM_LIMIT = 227 * 1024;
 __host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
-__host__ __device__ constexpr int ctl_off(int N, int K) { return w_bytes(N, K) + STAGES * tc::A_STAGE_BYTES; }
-__host__ __device__ constexpr int smem_bytes(int N, int K) { return ctl_off(N, K) + 128; }
+// A stages that fit beside the resident weights (at least 2)
+__host__ __device__ inline int stages(int N, int K)
+{
+    const int s = (SMEM_LIMIT - w_bytes(N, K) - CTL_BYTES - 4 * N) / tc::A_STAGE_BYTES;  // 4 N: the staged bias
+    return s < 2 ? 2 : (s > MAX_STAGES ? MAX_STAGES : s);
+}
+__host__ __device__ inline int ctl_off(int N, int K) { return w_bytes(N, K) + stages(N, K) * tc::A_STAGE_BYTES; }
+__host__ __device__ inline int smem_bytes(int N, int K) { return ctl_off(N, K) + CTL_BYTES; }
 }  // namespace ws
 
 template <int MODE>
@@ -277,19 +318,20 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
     const uint32_t sW = tc::smem_u32(smem), sA = sW + ws::w_bytes(N, K);
     uint8_t *ctl = smem + ws::ctl_off(N, K);
     const uint32_t bars = tc::smem_u32(ctl);
+    const int S = ws::stages(N, K);
     auto full_bar = [&](int s) { return bars + 8u * s; };
-    auto empty_bar = [&](int s) { return bars + 8u * (ws::STAGES + s); };
-    auto tfull_bar = [&](int a) { return bars + 8u * (2 * ws::STAGES + a); };
-    auto tempty_bar = [&](int a) { return bars + 8u * (2 * ws::STAGES + 2 + a); };
-    const uint32_t wbar = bars + 8u * (2 * ws::STAGES + 4), drain = wbar + 8u;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ctl + 8 * (2 * ws::STAGES + 6));
-    volatile int *abort = reinterpret_cast<volatile int *>(ctl + 8 * (2 * ws::STAGES + 6) + 4);
+    auto empty_bar = [&](int s) { return bars + 8u * (ws::MAX_STAGES + s); };
+    auto tfull_bar = [&](int a) { return bars + 8u * (2 * ws::MAX_STAGES + a); };
+    auto tempty_bar = [&](int a) { return bars + 8u * (2 * ws::MAX_STAGES + 2 + a); };
+    const uint32_t wbar = bars + 8u * (2 * ws::MAX_STAGES + 4), drain = wbar + 8u;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ctl + 8 * (2 * ws::MAX_STAGES + 6));
+    volatile int *abort = reinterpret_cast<volatile int *>(ctl + 8 * (2 * ws::MAX_STAGES + 6) + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), ncols);
     if (threadIdx.x == 32) {
-        for (int s = 0; s < ws::STAGES; ++s) {
-            tc::mbar_init(full_bar(s), 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full_bar(s), 32);  // one asynchronous arrival per producer lane
             tc::mbar_init(empty_bar(s), 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -322,9 +364,9 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int m0 = tile * tc::BM;
-            for (int kt = 0; kt < nkt; ++kt) {
-                const int s = q % ws::STAGES;
-                int got = lane == 0 ? (int)tc::mbar_wait_abort(empty_bar(s), (uint32_t)(((q / ws::STAGES) & 1) ^ 1), abort) : 0;
+            for (int kt = 0; kt < nkt; ++kt, ++q) {
+                const int s = q % S;
+                int got = lane == 0 ? (int)tc::mbar_wait_abort(empty_bar(s), (uint32_t)(((q / S) & 1) ^ 1), abort) : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -339,21 +381,11 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
                     const bool in = m < g.M_valid;
                     tc::cp_async16(dst + tc::tile_off(row, kc), g.A + (size_t)(in ? m : 0) * K + k0 + kc * 8, in ? 16u : 0u);
                 }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                if (q >= ws::LAG) {  // the stage LAG groups back has landed
-                    asm volatile("cp.async.wait_group %0;" ::"n"(ws::LAG) : "memory");
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(full_bar((q - ws::LAG) % ws::STAGES));
-                }
-                ++q;
+                // the stage's full barrier receives one arrival per lane once
+                // that lane's copies have landed
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full_bar(s)) : "memory");
             }
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0)
-            for (int r = max(0, q - ws::LAG); r < q; ++r) tc::mbar_arrive(full_bar(r % ws::STAGES));
     } else if (warp == 1) {
         // ---- MMA issue (one thread) --------------------------------------------
         if (lane == 0) {
@@ -365,8 +397,11 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
                 if (!(ok = tc::mbar_wait_abort(tempty_bar(acc), (uint32_t)((u & 1) ^ 1), abort))) break;
                 tc::fence_after_sync();
                 for (int kt = 0; kt < nkt && ok; ++kt, ++q) {
-                    const int s = q % ws::STAGES;
-                    if (!(ok = tc::mbar_wait_abort(full_bar(s), (uint32_t)((q / ws::STAGES) & 1), abort))) break;
+                    const int s = q % S;
+                    if (!(ok = tc::mbar_wait_abort(full_bar(s), (uint32_t)((q / S) & 1), abort))) break;
+                    // the stage was written by cp.async (generic proxy); the
+                    // tensor core reads it through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc::fence_after_sync();
                     const int kw = min(tc::BK, K - kt * tc::BK);
                     const uint32_t a_buf = sA + (uint32_t)s * tc::A_STAGE_BYTES;
@@ -385,10 +420,17 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
         }
     } else {
         // ---- epilogue warps ------------------------------------------------------
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
-        const int nch = N >> 4, h0 = (nch + 1) >> 1;
-        const int c0 = half ? h0 * 16 : 0, c1 = half ? N : h0 * 16;
+        // warp w serves tensor-memory lanes 32 (w % 4) .. + 31 (its rows of the
+        // tile) and column part (w - 2) / 4 of the tile's 16-column chunks
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
+        const int nparts = ws::EPI_WARPS / 4, nch = N >> 4;
+        const int c0 = 16 * ((nch * part) / nparts), c1 = 16 * ((nch * (part + 1)) / nparts);
         const bool out_mode = MODE == OUT_TRAIN || MODE == OUT_INFER;
+        // the bias, once per CTA, in shared memory (read as broadcasts)
+        float *bias_s = reinterpret_cast<float *>(smem + ws::smem_bytes(N, K));
+        if (g.bias)
+            for (int c = threadIdx.x - 64; c < N; c += 32 * ws::EPI_WARPS) bias_s[c] = g.bias[c];
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * ws::EPI_WARPS) : "memory");
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i & 1, u = i >> 1;
@@ -398,8 +440,8 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
             tc::fence_after_sync();
             const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * acc_cols;
             const int r = tile * tc::BM + quarter * 32 + lane;
-            if (out_mode ? half == 0 : c1 > c0)
-                epilogue_row<MODE>(g, r, tw, 0, c0, c1, false, 0, tile * 4 + quarter);
+            if (out_mode ? part == 0 : c1 > c0)
+                epilogue_row<MODE>(g, r, tw, 0, c0, c1, false, 0, tile * 4 + quarter, bias_s);
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tempty_bar(acc));
@@ -418,7 +460,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
 template <int MODE>
 cudaError_t gemm_ws(const GemmArgs &g, int n_sm, cudaStream_t st)
 {
-    const int smem = ws::smem_bytes(g.N, g.K);
+    const int smem = ws::smem_bytes(g.N, g.K) + 4 * g.N;  // + the bias
     cudaError_t e = cudaFuncSetAttribute(mlp_gemm_ws_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
@@ -929,6 +971,14 @@ int idm_gemm_bf16(const void *A, const void *B, int32_t M, int32_t N, int32_t K,
         return IDM_ERR_CUDA;
     }
     return IDM_OK;
+}
+
+int idm_mlp_gelu_eval(const float *z, float *gelu_out, float *gelu_grad_out, int32_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && !z)) return IDM_ERR_ARG;
+    if (n == 0) return IDM_OK;
+    idm::mlp::gelu_eval_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(z, gelu_out, gelu_grad_out, n);
+    return cudaGetLastError() == cudaSuccess ? IDM_OK : IDM_ERR_CUDA;
 }
 
 int idm_mlp_create(idm_mlp_t **out, int32_t max_batch)

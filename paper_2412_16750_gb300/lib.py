@@ -95,6 +95,7 @@ _SIGS = {
                                _vp, _vp]),
     # learned initializer (include/idm_mlp.h)
     "idm_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]),
+    "idm_mlp_gelu_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp]),
     "idm_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32]),
     "idm_mlp_destroy": (ctypes.c_int, [_vp]),
     "idm_mlp_last_error": (ctypes.c_char_p, [_vp]),
@@ -343,6 +344,11 @@ def mcheck(mlp, rc):
 def idm_gemm_bf16(A, B, M, N, K, C, status, stream=None):
     """Raw status code (no object to hold a message)."""
     return load().idm_gemm_bf16(ptr(A), ptr(B), M, N, K, ptr(C), ptr(status), stream_ptr(stream))
+
+
+def idm_mlp_gelu_eval(z, gelu_out=None, gelu_grad_out=None, stream=None):
+    """Raw status code."""
+    return load().idm_mlp_gelu_eval(ptr(z), ptr(gelu_out), ptr(gelu_grad_out), z.numel(), stream_ptr(stream))
 
 
 def idm_mlp_create(max_batch):

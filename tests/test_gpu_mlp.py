@@ -287,3 +287,23 @@ def test_persistent_gemm_path_matches_oracle(api):
     for name, _ in M.SHAPES:
         assert cosine(gd[name], rd[name]) >= 0.999, name
     assert net.status() == (0, 0)
+
+
+def test_gelu_approximation_error_bound(api):
+    """The kernels' GELU and its derivative (erf by Abramowitz & Stegun
+    7.1.26, |error| <= 1.5e-7) against the FP64 closed forms."""
+    from math import erf, exp, pi, sqrt
+    from paper_2412_16750_gb300 import lib
+    z = np.concatenate([np.linspace(-9, 9, 20001), np.random.default_rng(90).normal(scale=3, size=20000)])
+    z = z.astype(np.float32)
+    zt = torch.as_tensor(z, device="cuda")
+    g = torch.empty_like(zt)
+    dg = torch.empty_like(zt)
+    assert lib.idm_mlp_gelu_eval(zt, g, dg) == lib.IDM_OK
+    torch.cuda.synchronize()
+    zd = z.astype(np.float64)
+    cdf = np.array([0.5 * (1 + erf(x / sqrt(2))) for x in zd])
+    pdf = np.exp(-0.5 * zd * zd) / sqrt(2 * pi)
+    tol = 4e-7 * np.maximum(1.0, np.abs(zd))
+    assert np.all(np.abs(g.double().cpu().numpy() - zd * cdf) <= tol)
+    assert np.all(np.abs(dg.double().cpu().numpy() - (cdf + zd * pdf)) <= tol)
