@@ -59,6 +59,7 @@ struct GemmArgs {
     float *out[OUT];     // OUT_INFER: parameter arrays; else out[0] = [M_valid][5] sigmoid outputs or NULL
     float lo[OUT], hi[OUT];
     unsigned *status;
+    int stages;          // A stages of the persistent kernel
 };
 
 // Normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 and density phi(z) with erf
@@ -297,28 +298,31 @@ constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int CTL_BYTES = 8 * (2 * MAX_STAGES + 6) + 16;
 constexpr int SMEM_LIMIT = 227 * 1024;
 __host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
-// A stages that fit beside the resident weights (at least 2)
-__host__ __device__ inline int stages(int N, int K)
+// A stages that fit beside the resident weights (at least 2); nbias = the
+// staged bias floats
+__host__ __device__ inline int max_stages(int N, int K, int nbias)
 {
-    const int s = (SMEM_LIMIT - w_bytes(N, K) - CTL_BYTES - 4 * N) / tc::A_STAGE_BYTES;  // 4 N: the staged bias
+    const int s = (SMEM_LIMIT - w_bytes(N, K) - CTL_BYTES - 4 * nbias) / tc::A_STAGE_BYTES;
     return s < 2 ? 2 : (s > MAX_STAGES ? MAX_STAGES : s);
 }
-__host__ __device__ inline int ctl_off(int N, int K) { return w_bytes(N, K) + stages(N, K) * tc::A_STAGE_BYTES; }
-__host__ __device__ inline int smem_bytes(int N, int K) { return ctl_off(N, K) + CTL_BYTES; }
+__host__ __device__ inline int ctl_off(int N, int K, int S) { return w_bytes(N, K) + S * tc::A_STAGE_BYTES; }
+__host__ __device__ inline int smem_bytes(int N, int K, int S) { return ctl_off(N, K, S) + CTL_BYTES; }
 }  // namespace ws
 
 template <int MODE>
 __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const GemmArgs g)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    const int N = g.N, K = g.K, KC = K >> 3;
+    // this CTA's columns: [n0, n0 + N) of the product (N = g.BN, the width
+    // of the weight slice it keeps resident)
+    const int N = g.BN, K = g.K, KC = K >> 3, n0 = blockIdx.y * g.BN;
     const int nkt = (K + tc::BK - 1) / tc::BK;
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
     const uint32_t acc_cols = tc::tmem_cols_for(N), ncols = 2 * acc_cols;
     const uint32_t sW = tc::smem_u32(smem), sA = sW + ws::w_bytes(N, K);
-    uint8_t *ctl = smem + ws::ctl_off(N, K);
+    const int S = g.stages;
+    uint8_t *ctl = smem + ws::ctl_off(N, K, S);
     const uint32_t bars = tc::smem_u32(ctl);
-    const int S = ws::stages(N, K);
     auto full_bar = [&](int s) { return bars + 8u * s; };
     auto empty_bar = [&](int s) { return bars + 8u * (ws::MAX_STAGES + s); };
     auto tfull_bar = [&](int a) { return bars + 8u * (2 * ws::MAX_STAGES + a); };
@@ -352,8 +356,8 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
         // ---- producer: W once, then the A tiles -------------------------------
         for (int c = lane; c < N * KC; c += 32) {
             const int row = c / KC, kc = c - row * KC;
-            tc::cp_async16(sW + (uint32_t)(((row >> 3) * KC + kc) * 128 + (row & 7) * 16), g.B + (size_t)row * K + kc * 8,
-                           16u);
+            tc::cp_async16(sW + (uint32_t)(((row >> 3) * KC + kc) * 128 + (row & 7) * 16),
+                           g.B + (size_t)(n0 + row) * K + kc * 8, 16u);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -427,9 +431,9 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
         const int c0 = 16 * ((nch * part) / nparts), c1 = 16 * ((nch * (part + 1)) / nparts);
         const bool out_mode = MODE == OUT_TRAIN || MODE == OUT_INFER;
         // the bias, once per CTA, in shared memory (read as broadcasts)
-        float *bias_s = reinterpret_cast<float *>(smem + ws::smem_bytes(N, K));
+        float *bias_s = reinterpret_cast<float *>(smem + ws::smem_bytes(N, K, S));  // all g.N columns
         if (g.bias)
-            for (int c = threadIdx.x - 64; c < N; c += 32 * ws::EPI_WARPS) bias_s[c] = g.bias[c];
+            for (int c = threadIdx.x - 64; c < g.N; c += 32 * ws::EPI_WARPS) bias_s[c] = g.bias[c];
         asm volatile("bar.sync 1, %0;" ::"n"(32 * ws::EPI_WARPS) : "memory");
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
             const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * acc_cols;
             const int r = tile * tc::BM + quarter * 32 + lane;
             if (out_mode ? part == 0 : c1 > c0)
-                epilogue_row<MODE>(g, r, tw, 0, c0, c1, false, 0, tile * 4 + quarter, bias_s);
+                epilogue_row<MODE>(g, r, tw, n0, c0, c1, false, 0, tile * 4 + quarter, bias_s);
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tempty_bar(acc));
@@ -456,11 +460,18 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
     }
 }
 
-// Launch of the persistent GEMM: one CTA per SM (or fewer tiles).
+// Launch of the persistent GEMM: CTAs keep column slices of nsplit equal
+// parts of the weights; each walks row tiles (grid x) of its slice (grid y).
 template <int MODE>
-cudaError_t gemm_ws(const GemmArgs &g, int n_sm, cudaStream_t st)
+cudaError_t gemm_ws(const GemmArgs &g0, int n_sm, int nsplit, cudaStream_t st)
 {
-    const int smem = ws::smem_bytes(g.N, g.K) + 4 * g.N;  // + the bias
+    GemmArgs g = g0;
+    g.BN = g.N / nsplit;
+    // with split columns every CTA has few row tiles: 4 stages (a whole
+    // K = 256 tile) leave room for a second resident CTA
+    g.stages = ws::max_stages(g.BN, g.K, g.N);
+    if (nsplit > 1 && g.stages > 4) g.stages = 4;
+    const int smem = ws::smem_bytes(g.BN, g.K, g.stages) + 4 * g.N;  // + the bias
     cudaError_t e = cudaFuncSetAttribute(mlp_gemm_ws_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
@@ -470,9 +481,9 @@ cudaError_t gemm_ws(const GemmArgs &g, int n_sm, cudaStream_t st)
         occ = 1;
     // resident CTAs must also fit the 512 tensor-memory columns of an SM
     // (a CTA that cannot allocate would wait for another to finish)
-    occ = std::max(1, std::min(occ, (int)(512 / (2 * tc::tmem_cols_for(g.N)))));
-    const int grid = std::max(1, std::min(ntiles, n_sm * occ));
-    mlp_gemm_ws_kernel<MODE><<<grid, ws::NTHREADS, smem, st>>>(g);
+    occ = std::max(1, std::min(occ, (int)(512 / (2 * tc::tmem_cols_for(g.BN)))));
+    const int grid = std::max(1, std::min(ntiles, (n_sm * occ + nsplit - 1) / nsplit));
+    mlp_gemm_ws_kernel<MODE><<<dim3(grid, nsplit), ws::NTHREADS, smem, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -484,8 +495,11 @@ template <int MODE>
 cudaError_t gemm_batch(const GemmArgs &g, int n_sm, cudaStream_t st)
 {
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
-    if (ntiles >= 2 * n_sm) return gemm_ws<MODE>(g, n_sm, st);
-    return gemm<MODE>(g, g.M_rows, 1, st);
+    // few row tiles: split the columns so that more SMs work (each CTA then
+    // keeps a narrower weight slice)
+    int nsplit = 1;
+    while (ntiles * nsplit < n_sm && g.N / (2 * nsplit) >= 64 && (g.N / (2 * nsplit)) % 16 == 0) nsplit *= 2;
+    return gemm_ws<MODE>(g, n_sm, nsplit, st);
 }
 
 // ---------------------------------------------------------------------------
