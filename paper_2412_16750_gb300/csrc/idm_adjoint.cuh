@@ -15,8 +15,8 @@ namespace idm {
 // with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle
 // (and across warps through the group's exchange cells).  The coefficients
 // of step k-1 are evaluated while the dependent chain of step k runs.
-// Gradient increments accumulate in registers per checkpoint segment and
-// are added to per-slot totals in shared memory.
+// The six factored gradient sums of each slot accumulate in registers over
+// all steps.
 // ---------------------------------------------------------------------------
 template <int NP, bool DENSE, bool ADAM, bool WD, bool D4>
 __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
@@ -31,7 +31,6 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     float *tg = tv + a.C * SLG;                     // (tape depth = checkpoint interval here)
     float *trb = tg + a.C * SLG;                    // nb tapes: targets, then seeds (MSE only)
     float *ckb = tv + (DENSE ? 2 : 2 + nb) * a.C * SLG;  // nb checkpoint stages [4][SLG]
-    float *acc = ckb + nb * 4 * SLG;                // gradient totals [6][SLG]
     const int Ns = sc.n_veh;
     const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
@@ -39,13 +38,15 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     int xp = 0, fp = 0;
     float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
 
-    f2 lp[NP], lv[NP];
+    // lp, lv: adjoints of position and speed; sacc: the six factored
+    // gradient sums of every slot, accumulated in registers over all steps
+    f2 lp[NP], lv[NP], sacc[6][NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         lp[p] = F2(0.0f);
         lv[p] = F2(0.0f);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
+        for (int q = 0; q < 6; ++q) sacc[q][p] = F2(0.0f);
     }
 
     // first observed step >= max(c0, 1) of a checkpoint segment and its
@@ -169,12 +170,6 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         kahan_add(lsum, lcomp, __fadd_rn(lseg.x, lseg.y));
         grp_sync(g);  // the whole group's tape is written
 
-        f2 sacc[6][NP];
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-#pragma unroll
-            for (int p = 0; p < NP; ++p) sacc[q][p] = F2(0.0f);
-
         // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
         int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
         int obs_hi = row_hi * sc.obs_stride;
@@ -249,13 +244,6 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 --row_hi;
             }
         }
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float *ap = acc + q * SLG + wb + 64 * p + 2 * lane;
-                sts2(ap, add2(lds2(ap), sacc[q][p]));
-            }
         grp_sync(g);  // the tape may be overwritten by the next segment
     }
 
@@ -271,8 +259,9 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             const float v0 = a.v0[gi], b = a.b[gi];
             const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
             const float dl = c ? kc[p].delta.y : kc[p].delta.x;
-            const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
-            const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+            const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
+            const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
+            const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
             float gr[6];
             gr[0] = am * dl * A4 / v0;                 // v0
             gr[1] = -A1;                               // T
@@ -336,7 +325,6 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
     float *tg = tv + T * SLG;
     float *trb = tg + T * SLG;                      // nb tapes: targets, then seeds (MSE only)
     float *ckb = tv + (DENSE ? 2 : 2 + nb) * T * SLG;  // nb state stages [4][SLG]
-    float *acc = ckb + nb * 4 * SLG;                // gradient totals [6][SLG]
     const int Ns = sc.n_veh;
     const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
@@ -344,13 +332,15 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
     int xp = 0, fp = 0;
     float lsum = 0.0f, lcomp = 0.0f;  // squared residuals (MSE): Kahan across checkpoint segments
 
-    f2 lp[NP], lv[NP];
+    // lp, lv: adjoints of position and speed; sacc: the six factored
+    // gradient sums of every slot, accumulated in registers over all steps
+    f2 lp[NP], lv[NP], sacc[6][NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         lp[p] = F2(0.0f);
         lv[p] = F2(0.0f);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) sts2(acc + q * SLG + wb + 64 * p + 2 * lane, F2(0.0f));
+        for (int q = 0; q < 6; ++q) sacc[q][p] = F2(0.0f);
     }
 
     // first observed step >= max(c0, 1) of a checkpoint segment and its
@@ -546,12 +536,6 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
         kahan_add(lsum, lcomp, __fadd_rn(lseg.x, lseg.y));
         grp_sync(g);  // the whole group's tape is written
 
-        f2 sacc[6][NP];
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-#pragma unroll
-            for (int p = 0; p < NP; ++p) sacc[q][p] = F2(0.0f);
-
         // last observed step <= c0 + n - 1 (for the MSE seeds of the sweep)
         int row_hi = (c0 + n - 1) / sc.obs_stride;  // target row + 1 of obs_hi
         int obs_hi = row_hi * sc.obs_stride;
@@ -626,13 +610,6 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 --row_hi;
             }
         }
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float *ap = acc + q * SLG + wb + 64 * p + 2 * lane;
-                sts2(ap, add2(lds2(ap), sacc[q][p]));
-            }
         grp_sync(g);  // the tape may be overwritten by the next block
         if (a.bwd_pf) par ^= 1;
       }
@@ -650,8 +627,9 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
             const float v0 = a.v0[gi], b = a.b[gi];
             const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
             const float dl = c ? kc[p].delta.y : kc[p].delta.x;
-            const float A0 = acc[0 * SLG + q], A1 = acc[1 * SLG + q], A2 = acc[2 * SLG + q];
-            const float A3 = acc[3 * SLG + q], A4 = acc[4 * SLG + q], A5 = acc[5 * SLG + q];
+            const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
+            const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
+            const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
             float gr[6];
             gr[0] = am * dl * A4 / v0;                 // v0
             gr[1] = -A1;                               // T

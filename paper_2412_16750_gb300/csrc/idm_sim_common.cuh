@@ -219,8 +219,7 @@ __device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<co
 __device__ __forceinline__ void sts2(float *p, f2 x) { *reinterpret_cast<f2 *>(p) = x; }
 
 // Shared floats of one adjoint group: tape v/gap [T][G*SL], target/seed
-// tapes [T][G*SL] (MSE only), state stages [4][G*SL], totals [6][G*SL],
-// control area; T is the tape depth (the checkpoint interval, or less when
+// tapes [T][G*SL] (MSE only), state stages [4][G*SL], control area; T is the tape depth (the checkpoint interval, or less when
 // blocks restart from sub-checkpoints).  With prefetch the target tape and
 // the state stage are doubled and the next block's targets and starting
 // state are copied (cp.async) into the idle pair while the current block
@@ -228,7 +227,7 @@ __device__ __forceinline__ void sts2(float *p, f2 x) { *reinterpret_cast<f2 *>(p
 __host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, int T, int G, bool pf)
 {
     const int nb = pf ? 2 : 1;
-    return ((dense ? 2 : 2 + nb) * T + 4 * nb + 6) * 32 * vpt * G + grp_ctrl_floats(G);
+    return ((dense ? 2 : 2 + nb) * T + 4 * nb) * 32 * vpt * G + grp_ctrl_floats(G);
 }
 
 }  // namespace idm
