@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--vpt", type=int, default=4)
     p.add_argument("--G", type=int, default=4, help="warps per segment")
     p.add_argument("--ckpt", type=int, default=8)
-    p.add_argument("--wpb", type=int, default=4)
+    p.add_argument("--wpb", type=int, default=8)
     # learned-versus-plain initial guess (time to fit 0.5 m RMSE)
     p.add_argument("--no-init-experiment", action="store_true")
     p.add_argument("--init-only", action="store_true", help="run only the initializer experiment")

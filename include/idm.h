@@ -119,10 +119,12 @@ int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
  * warps_per_segment: 1, 2, 4 or 8 (0 = choose; with both 0 the library
  * takes vpt 4 x 4 warps, 8 x 4 for lanes over 512 vehicles and 8 x 8 over
  * 1024); ckpt_interval: steps between stored checkpoints of the adjoint
- * (1..64, default 8); warps_per_block: 1..16 (default 4; rounded to a
+ * (1..64, default 8); warps_per_block: 1..16 (default 8; rounded to a
  * multiple of warps_per_segment; the adjoint caps it by its shared-memory
  * tape and by its register budget: 4 warps for vpt 4 with segments of up to
- * 4 warps, 8 otherwise). */
+ * 4 warps, 8 otherwise).  The forward runs the same segments with 8
+ * vehicles per thread where the capacity allows (e.g. 8 x 2 warps for the
+ * adjoint's 4 x 4). */
 int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block);
 
 /* Longest lane the library can simulate (vehicles): 32 * 8 * 8 = 2048. */

@@ -21,11 +21,11 @@ PARAM_NAMES = ("v0", "T", "s0", "a_max", "b", "delta")
 class Context:
     """Owns an idm_ctx_t (workspace on the current device)."""
 
-    def __init__(self, workspace_cap_bytes=0, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=4):
+    def __init__(self, workspace_cap_bytes=0, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=8):
         self.handle = lib.idm_ctx_create(workspace_cap_bytes)
         self.set_tuning(vpt, warps_per_segment, ckpt_interval, warps_per_block)
 
-    def set_tuning(self, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=4):
+    def set_tuning(self, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=8):
         lib.idm_set_tuning(self.handle, vpt, warps_per_segment, ckpt_interval, warps_per_block)
         self.tuning = (vpt, warps_per_segment, ckpt_interval, warps_per_block)
 

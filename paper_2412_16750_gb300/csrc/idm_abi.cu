@@ -194,10 +194,14 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
 
 void forward_shape(int vpt, int G, int *vpt_f, int *G_f)
 {
-    // the forward carries fewer live values per vehicle, so it prefers 4
-    // vehicles per thread for the same segment capacity
+    // the forward carries fewer live values per vehicle, so it prefers 8
+    // vehicles per thread (4 pairs of independent chains) for the same
+    // segment capacity, else 4
     const int cap = 32 * vpt * G;
-    if (cap % 128 == 0 && cap / 128 >= 1 && cap / 128 <= 8) {
+    if (cap % 256 == 0 && cap / 256 >= 1 && cap / 256 <= 8) {
+        *vpt_f = 8;
+        *G_f = cap / 256;
+    } else if (cap % 128 == 0 && cap / 128 >= 1 && cap / 128 <= 8) {
         *vpt_f = 4;
         *G_f = cap / 128;
     } else {

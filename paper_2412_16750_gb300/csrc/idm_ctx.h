@@ -45,7 +45,7 @@ struct idm_ctx {
     int vpt_req = 0;
     int G_req = 0;
     int C = 8;
-    int wpb = 4;
+    int wpb = 8;
     idm::abi::Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor, eval_part, sub_ckpt;
     idm::abi::Buf scen_tab, scen_seg_off, scen_seg_idx, lane_off_dev;  // batched scenarios
     cudaStream_t cap_stream = nullptr;

@@ -195,7 +195,7 @@ def idm_status(ctx, stream=None):
     return rc, flags.value
 
 
-def idm_set_tuning(ctx, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=4):
+def idm_set_tuning(ctx, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=8):
     return check(ctx, load().idm_set_tuning(ctx, vpt, warps_per_segment, ckpt_interval, warps_per_block))
 
 
