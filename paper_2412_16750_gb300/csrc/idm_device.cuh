@@ -101,17 +101,16 @@ __device__ __forceinline__ f2 pow_delta2(f2 r, f2 delta)
     return make_float2(r.x > 0.0f ? __powf(r.x, delta.x) : 0.0f, r.y > 0.0f ? __powf(r.y, delta.y) : 0.0f);
 }
 
-__device__ __forceinline__ f2 floor_gap(f2 g)
-{
-    return make_float2(g.x < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : g.x, g.y < IDM_GAP_FLOOR ? IDM_GAP_FLOOR : g.y);
-}
+// max(gap, floor): one min/max op per element (a non-finite gap only arises
+// from a non-finite state, which the status word reports).
+__device__ __forceinline__ f2 floor_gap(f2 g) { return vmax(g, F2(IDM_GAP_FLOOR)); }
 
 // a_lb = max(-v/dt, a_min) with the strict-inequality tie rule (Sec. III-C).
 __device__ __forceinline__ f2 lower_bound(f2 lbv, float a_min, bool &bx, bool &by)
 {
     bx = lbv.x > a_min;
     by = lbv.y > a_min;
-    return make_float2(bx ? lbv.x : a_min, by ? lbv.y : a_min);
+    return vmax(lbv, F2(a_min));  // equal values give a_min either way
 }
 
 // Bounded acceleration a* of two vehicles from their speeds v, raw gaps
