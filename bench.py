@@ -497,7 +497,8 @@ def long_horizon(a, dev, net):
            "predict_ms": e[2].elapsed_time(e[3]),
            "fit_vehicle_steps_per_s": a.long_iters * N * K_fit / (e[1].elapsed_time(e[2]) * 1e-3),
            "rmse_fit_window_m": rmse_fit, "rmse_prediction_m": rmse_pred,
-           "final_mse_m2": float(hist[-1].item()) / N,
+           "rmse_vs_noisy_targets_m": {"before_first_update": math.sqrt(float(hist[0].item()) / N),
+                                       "before_last_update": math.sqrt(float(hist[-1].item()) / N)},
            "oracle_check": {"lanes": len(lanes), "max_abs_diff_m": worst, "steps": K_all},
            "peak_hbm_gb": {"torch_allocated": peak / 1e9, "library_workspace": ws / 1e9}}
     ctx.close()
