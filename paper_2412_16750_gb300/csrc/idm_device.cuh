@@ -46,9 +46,20 @@ __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-// a - b: the negation is exact, so each component is the correctly rounded
-// difference.
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a - b per component, rounded to nearest (the packed subtract instruction,
+// no separate negation).
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 __device__ __forceinline__ f2 ex2(f2 x) { return make_float2(ex2_approx(x.x), ex2_approx(x.y)); }
 __device__ __forceinline__ f2 lg2(f2 x) { return make_float2(lg2_approx(x.x), lg2_approx(x.y)); }
 __device__ __forceinline__ f2 rcp2(f2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
