@@ -60,13 +60,14 @@ def batch_of(api, sc):
     return api.Batch(sc["scen_lane_off"], sc["K"], sc["dt"], sc["obs_stride"], sc["lane_off"], sc["length"], A_MIN)
 
 
-@pytest.mark.parametrize("shape", [(0, 0), (2, 1), (4, 4)])
+@pytest.mark.parametrize("shape", [(0, 0, 4), (2, 1, 4), (4, 4, 4), (4, 4, 30)])
 def test_batch_loss_grad_parity(api, shape):
+    # the last shape's checkpoint interval exceeds the tape depth (tape blocks)
     sc, rng = small_batch(200)
     Y = targets_for(sc, rng)
     N = int(sc["lane_off"][-1])
     theta = synth.f32(sc["theta_true"] * rng.uniform(0.85, 1.15, size=(6, N)))
-    ctx = api.Context(vpt=shape[0], warps_per_segment=shape[1], ckpt_interval=4)
+    ctx = api.Context(vpt=shape[0], warps_per_segment=shape[1], ckpt_interval=shape[2])
     b = batch_of(api, sc)
     sl, tot, g, gp, gv = api.batch_loss_grad(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), b, cuda(Y), ctx=ctx)
     torch.cuda.synchronize()

@@ -108,7 +108,10 @@ def test_loss_grad_config0(api, init):
     grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
 
 
-def test_backward_dense_seeds(api):
+@pytest.mark.parametrize("ckpt", [8, 23])
+def test_backward_dense_seeds(api, ckpt):
+    # ckpt 23 exceeds the shared-memory tape depth: tape blocks restarted
+    # from sub-checkpoints
     sc = synth.config0()
     K = 60
     rng = np.random.default_rng(102)
@@ -119,7 +122,7 @@ def test_backward_dense_seeds(api):
     P, V = oracle.forward(sc["lane_off"], sc["length"], theta, sc["p_init"], sc["v_init"], K, DT, A_MIN)
     g, gp, gv = oracle.adjoint(sc["lane_off"], sc["length"], theta, K, DT, P, V, gP, gV, A_MIN)
     gg, gpg, gvg = api.backward(cuda(theta), cuda(sc["p_init"]), cuda(sc["v_init"]), scene_of(api, sc), K, DT,
-                                cuda(gP), cuda(gV), A_MIN)
+                                cuda(gP), cuda(gV), A_MIN, ctx=api.Context(ckpt_interval=ckpt))
     grad_close(gg.double().cpu().numpy(), g)
     grad_close(np.stack([gpg.double().cpu().numpy(), gvg.double().cpu().numpy()]), np.stack([gp, gv]),
                rows=range(2))
