@@ -16,3 +16,4 @@ from .ref import (  # noqa: F401
     PARAM_NAMES,
 )
 from . import mlp_oracle  # noqa: F401,E402
+from . import recon  # noqa: F401,E402

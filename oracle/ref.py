@@ -16,6 +16,7 @@ PARAM_NAMES = ("v0", "T", "s0", "a_max", "b", "delta")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "idm_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "recon_oracle.c"))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
@@ -28,10 +29,11 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 def build(force=False):
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp] + list(_SRCS) + ["-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -49,6 +51,12 @@ def _load():
             lib.orc_lr.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
             lib.orc_fit.restype = None
             lib.orc_layout.restype = ctypes.c_int
+            lib.orc_recon_nearest_step.restype = ctypes.c_int
+            lib.orc_recon_nearest_step.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.orc_recon_mae_seed.restype = ctypes.c_double
+            for name in ("orc_recon_init_state", "orc_recon_forward", "orc_recon_adjoint", "orc_recon_fit",
+                         "orc_recon_metrics"):
+                getattr(lib, name).restype = None
             _lib = lib
     return _lib
 
