@@ -21,7 +21,9 @@
  *     part of the loss.
  *   - |x| has subgradient sign(x) with sign(0) = 0.
  *   - Initial state (Sec. V-B): p(0) = the first observed position and v(0)
- *     = (second - first observed position) / (their time difference).
+ *     = (second - first observed position) / (their time difference),
+ *     clamped at 0 (the simulator keeps speeds non-negative, Sec. III-C);
+ *     0 with fewer than two observations or equal first timestamps.
  *   - Trajectory i is simulated for K_i = the nearest step of its last
  *     observation; arrays are time-major [K_max (+1)][N]; entries beyond K_i
  *     hold the final state (positions, speeds) or zero (accelerations,
@@ -107,7 +109,8 @@ void orc_recon_init_state(int N, const int32_t *obs_off, const double *obs_t, co
     for (int i = 0; i < N; ++i) {
         int j0 = obs_off[i], n = obs_off[i + 1] - j0;
         p0[i] = n > 0 ? obs_p[j0] : 0.0;
-        v0[i] = n > 1 ? (obs_p[j0 + 1] - obs_p[j0]) / (obs_t[j0 + 1] - obs_t[j0]) : 0.0;
+        double dt01 = n > 1 ? obs_t[j0 + 1] - obs_t[j0] : 0.0;
+        v0[i] = dt01 > 0.0 ? fmax((obs_p[j0 + 1] - obs_p[j0]) / dt01, 0.0) : 0.0;
     }
 }
 

@@ -173,6 +173,11 @@ def test_initial_state_rule():
     p0, v0 = R.init_state(off, t, y)
     np.testing.assert_allclose(p0, [10.0, -4.0])
     np.testing.assert_allclose(v0, [16.0, 20.0])
+    # a backwards first difference, equal timestamps and a single observation give 0
+    p0, v0 = R.init_state(np.array([0, 2, 4, 5], np.int32), np.array([0.0, 1.0, 3.0, 3.0, 7.0]),
+                          np.array([5.0, 4.0, 1.0, 2.0, 9.0]))
+    np.testing.assert_array_equal(v0, [0.0, 0.0, 0.0])
+    np.testing.assert_array_equal(p0, [5.0, 1.0, 9.0])
 
 
 def test_fit_reduces_loss_and_is_stationary_at_the_truth():
