@@ -18,6 +18,22 @@ def nearest_step(t, dt):
     return _load().orc_recon_nearest_step(float(t), float(dt))
 
 
+def nearest_steps(t, dt):
+    """Nearest step of every timestamp (int32 array)."""
+    t = _f64(t)
+    k = np.empty(len(t), dtype=np.int32)
+    _load().orc_recon_nearest_steps(ctypes.c_int64(len(t)), _p(t), ctypes.c_double(dt), _pi(k))
+    return k
+
+
+def horizons(obs_off, obs_k):
+    """K[i] = the nearest step of trajectory i's last observation (0 if none)."""
+    obs_off = np.asarray(obs_off)
+    n = np.diff(obs_off)
+    last = np.maximum(obs_off[1:] - 1, 0)
+    return np.where(n > 0, np.asarray(obs_k)[last] if len(obs_k) else 0, 0).astype(np.int32)
+
+
 def init_state(obs_off, obs_t, obs_p):
     lib = _load()
     obs_off = _i32(obs_off)

@@ -101,6 +101,11 @@ static vl_eval eval_vl(double v, double dp_raw, double dv, const double th[6], d
 /* Nearest step of a timestamp (seconds from the trajectory's start). */
 int orc_recon_nearest_step(double t, double dt) { return (int)floor(t / dt + 0.5); }
 
+void orc_recon_nearest_steps(int64_t n, const double *t, double dt, int32_t *k)
+{
+    for (int64_t j = 0; j < n; ++j) k[j] = orc_recon_nearest_step(t[j], dt);
+}
+
 /* Initial state of Sec. V-B from the first two observations of each
  * trajectory (observations obs_off[i] .. obs_off[i+1]-1, in time order). */
 void orc_recon_init_state(int N, const int32_t *obs_off, const double *obs_t, const double *obs_p, double *p0,

@@ -55,7 +55,7 @@ def _load():
             lib.orc_recon_nearest_step.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.orc_recon_mae_seed.restype = ctypes.c_double
             for name in ("orc_recon_init_state", "orc_recon_forward", "orc_recon_adjoint", "orc_recon_fit",
-                         "orc_recon_metrics"):
+                         "orc_recon_metrics", "orc_recon_nearest_steps"):
                 getattr(lib, name).restype = None
             _lib = lib
     return _lib

@@ -366,3 +366,90 @@ def mlp_features(scene, p_init, v_init, K, dt, targets, obs_stride=1, perm=None,
     lib.idm_mlp_features(scene.c(), p_init, v_init, lib.make_sim(K, dt, -10.0), targets, obs_stride, perm_t, n, X,
                          lib.make_params(theta) if theta is not None else None, labels, box_lo, box_hi, _stream())
     return (X, labels) if theta is not None else X
+
+
+# ---- single-trajectory filtering / reconstruction mode (Sec. IV-A) ----------
+
+# Sec. IV-A: the five parameters start at v_targ 50, T_pref 1, s_min 5,
+# a_max 10, a_pref 2 (delta 4, not fitted) inside the boxes below; the
+# virtual leader starts at a 10 m gap and zero speed difference.
+RECON_INIT = (50.0, 1.0, 5.0, 10.0, 2.0, 4.0)
+RECON_BOX_LO = (20.0, 0.1, 1.0, 5.0, 0.1)
+RECON_BOX_HI = (60.0, 5.0, 10.0, 10.0, 5.0)
+RECON_DP0 = 10.0
+RECON_DV0 = 0.0
+
+
+class Recon:
+    """Observed trajectories (CSR over trajectories) prepared for the
+    reconstruction mode: nearest steps, horizons K and initial states come
+    from idm_recon_prepare.  Per-step tensors are time-major (k_max, N)."""
+
+    def __init__(self, obs_off, obs_t, obs_p, dt, a_min=-10.0, ctx=None):
+        self.ctx = ctx or default_context()
+        self.obs_off = obs_off.to(device="cuda", dtype=torch.int32).contiguous()
+        self.obs_t = _f32(obs_t)
+        self.obs_p = _f32(obs_p)
+        self.N = self.obs_off.numel() - 1
+        self.n_obs = self.obs_p.numel()
+        self.dt, self.a_min = float(dt), float(a_min)
+        self.obs_k = torch.empty(max(self.n_obs, 1), device="cuda", dtype=torch.int32)
+        self.K = torch.empty(max(self.N, 1), device="cuda", dtype=torch.int32)
+        self.p_init = torch.empty(max(self.N, 1), device="cuda", dtype=torch.float32)
+        self.v_init = torch.empty(max(self.N, 1), device="cuda", dtype=torch.float32)
+        km = lib.idm_recon_prepare(self.ctx.handle, self.N, self.n_obs, self.obs_off, self.obs_t, self.obs_p,
+                                   self.dt, self.obs_k, self.K, self.p_init, self.v_init, True, _stream())
+        self.k_max = max(int(km), 1)
+        self.ld = max(self.N, 1)
+
+    def c(self):
+        return lib.idm_recon_t(self.N, self.k_max, self.ld, self.n_obs, lib.ptr(self.obs_off).value,
+                               lib.ptr(self.obs_t).value, lib.ptr(self.obs_p).value, lib.ptr(self.obs_k).value,
+                               lib.ptr(self.K).value, lib.ptr(self.p_init).value, lib.ptr(self.v_init).value,
+                               self.dt, self.a_min)
+
+    def init_vars(self):
+        """(theta (6, N), dp, dv (k_max, N)) at the paper's starting point."""
+        theta = torch.tensor(RECON_INIT, dtype=torch.float32, device="cuda")[:, None].repeat(1, self.N).contiguous()
+        dp = torch.full((self.k_max, self.ld), RECON_DP0, device="cuda", dtype=torch.float32)
+        dv = torch.full((self.k_max, self.ld), RECON_DV0, device="cuda", dtype=torch.float32)
+        return theta, dp, dv
+
+    def forward(self, theta, dp, dv):
+        """(P, V (k_max+1, N), A (k_max, N))."""
+        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        P = torch.empty((self.k_max + 1, self.ld), device="cuda", dtype=torch.float32)
+        V = torch.empty_like(P)
+        A = torch.empty((self.k_max, self.ld), device="cuda", dtype=torch.float32)
+        lib.idm_recon_forward(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, P, V, A, _stream())
+        return P, V, A
+
+    def loss_grad(self, theta, dp, dv):
+        """(loss float64 0-d, g_theta (6, N), g_dp, g_dv (k_max, N), g_p_init, g_v_init)."""
+        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        loss = torch.zeros((), device="cuda", dtype=torch.float64)
+        g = torch.empty((6, self.ld), device="cuda", dtype=torch.float32)
+        gdp = torch.empty((self.k_max, self.ld), device="cuda", dtype=torch.float32)
+        gdv = torch.empty_like(gdp)
+        gp = torch.empty(self.ld, device="cuda", dtype=torch.float32)
+        gv = torch.empty(self.ld, device="cuda", dtype=torch.float32)
+        lib.idm_recon_loss_grad(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, loss,
+                                lib.make_params(g), gdp, gdv, gp, gv, _stream())
+        return loss, g, gdp, gdv, gp, gv
+
+    def fit(self, theta, dp, dv, n_iter=500, lr0=0.1, lr1=0.01, box_lo=RECON_BOX_LO, box_hi=RECON_BOX_HI):
+        """Adam fit in place on theta (6, N), dp, dv (k_max, N), float32 CUDA
+        contiguous; returns the float64 loss history (n_iter,)."""
+        for t in (theta, dp, dv):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        hist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
+        lib.idm_recon_fit(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, n_iter, lr0, lr1, box_lo,
+                          box_hi, hist, _stream())
+        return hist[:n_iter]
+
+    def metrics(self, theta, dp, dv):
+        """float64 (4,): Pos. (fraction), mean |a*|, std |a*|, Imp. (fraction)."""
+        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        out = torch.zeros(4, device="cuda", dtype=torch.float64)
+        lib.idm_recon_metrics(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, out, _stream())
+        return out

@@ -12,6 +12,7 @@
 #include <new>
 
 #include "../../include/idm.h"
+#include "../../include/idm_recon.h"
 #include "idm_ctx.h"
 #include "idm_internal.h"
 
@@ -408,8 +409,11 @@ int idm_ctx_destroy(idm_ctx_t *c)
     cudaDeviceSynchronize();
     if (c->fit_exec) cudaGraphExecDestroy(c->fit_exec);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    Buf *bufs[] = {&c->seg, &c->ctl, &c->status, &c->g0, &c->ckpt, &c->loss_part, &c->loss_tmp,
-                   &c->adam_m, &c->adam_v, &c->lay_counts, &c->lay_cursor};
+    Buf *bufs[] = {&c->seg,      &c->ctl,        &c->status,       &c->g0,           &c->ckpt,
+                   &c->loss_part, &c->loss_tmp,  &c->adam_m,       &c->adam_v,       &c->lay_counts,
+                   &c->lay_cursor, &c->eval_part, &c->sub_ckpt,    &c->scen_tab,     &c->scen_seg_off,
+                   &c->scen_seg_idx, &c->lane_off_dev, &c->rec_oyy, &c->rec_oyc,    &c->rec_tape,
+                   &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -461,6 +465,8 @@ int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
     if (h & (IDM_STATUS_LANE_TOO_LONG | IDM_STATUS_BAD_LANE_OFF))
         return fail(c, IDM_ERR_LANE, "device status 0x%x: lane longer than the segment or malformed lanes", h);
     if (h & IDM_STATUS_NONFINITE) return fail(c, IDM_ERR_NONFINITE, "device status 0x%x: non-finite value", h);
+    if (h & IDM_STATUS_BAD_OBS)
+        return fail(c, IDM_ERR_OBS, "device status 0x%x: malformed observations or horizons", h);
     return IDM_OK;
 }
 

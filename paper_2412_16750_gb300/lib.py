@@ -17,11 +17,13 @@ IDM_ERR_CUDA = 3
 IDM_ERR_NONFINITE = 4
 IDM_ERR_TIMEOUT = 5
 IDM_ERR_LANE = 6
+IDM_ERR_OBS = 7
 
 IDM_STATUS_LANE_TOO_LONG = 1
 IDM_STATUS_BAD_LANE_OFF = 2
 IDM_STATUS_NONFINITE = 4
 IDM_STATUS_TIMEOUT = 8
+IDM_STATUS_BAD_OBS = 16
 
 IDM_MLP_IN = 80
 IDM_MLP_HIDDEN = 256
@@ -51,6 +53,12 @@ class idm_batch_t(ctypes.Structure):
     _fields_ = [("n_scen", ctypes.c_int32), ("scen_lane_off", _vp), ("K", _vp), ("dt", _vp), ("obs_stride", _vp),
                 ("a_min", ctypes.c_float), ("n_lanes", ctypes.c_int32), ("n_vehicles", ctypes.c_int32),
                 ("lane_off_host", _vp), ("lane_off", _vp), ("length", _vp)]
+
+
+class idm_recon_t(ctypes.Structure):
+    _fields_ = [("n_traj", ctypes.c_int32), ("k_max", ctypes.c_int32), ("ld", ctypes.c_int32),
+                ("n_obs", ctypes.c_int64), ("obs_off", _vp), ("obs_t", _vp), ("obs_p", _vp), ("obs_k", _vp),
+                ("K", _vp), ("p_init", _vp), ("v_init", _vp), ("dt", ctypes.c_float), ("a_min", ctypes.c_float)]
 
 
 # name -> (restype, argtypes)
@@ -116,6 +124,18 @@ _SIGS = {
                                     ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                     ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                     _vp, _vp, _vp, _vp]),
+    # single-trajectory reconstruction mode (include/idm_recon.h)
+    "idm_recon_prepare": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_float, _vp,
+                                         _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32), _vp]),
+    "idm_recon_forward": (ctypes.c_int, [_vp, ctypes.POINTER(idm_recon_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                         _vp, _vp, _vp, _vp]),
+    "idm_recon_loss_grad": (ctypes.c_int, [_vp, ctypes.POINTER(idm_recon_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                           _vp, ctypes.POINTER(idm_params_t), _vp, _vp, _vp, _vp, _vp]),
+    "idm_recon_fit": (ctypes.c_int, [_vp, ctypes.POINTER(idm_recon_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                     ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_float), _vp, _vp]),
+    "idm_recon_metrics": (ctypes.c_int, [_vp, ctypes.POINTER(idm_recon_t), ctypes.POINTER(idm_params_t), _vp, _vp,
+                                         _vp, _vp]),
 }
 
 _lib = None
@@ -312,6 +332,41 @@ def idm_batch_fit(ctx, batch, params, p_init, v_init, targets, n_iter, lr0, lr1,
 
 
 # ---- struct builders ---------------------------------------------------------
+
+def idm_recon_prepare(ctx, N, n_obs, obs_off, obs_t, obs_p, dt, obs_k, K, p_init, v_init, want_k_max=True,
+                      stream=None):
+    """Returns max K (the call then waits for the stream) or None."""
+    km = ctypes.c_int32(0)
+    check(ctx, load().idm_recon_prepare(ctx, N, n_obs, ptr(obs_off), ptr(obs_t), ptr(obs_p), dt, ptr(obs_k), ptr(K),
+                                        ptr(p_init), ptr(v_init), ctypes.byref(km) if want_k_max else None,
+                                        stream_ptr(stream)))
+    return km.value if want_k_max else None
+
+
+def idm_recon_forward(ctx, rec, params, dp, dv, P=None, V=None, A=None, stream=None):
+    return check(ctx, load().idm_recon_forward(ctx, ctypes.byref(rec), ctypes.byref(params), ptr(dp), ptr(dv),
+                                               ptr(P), ptr(V), ptr(A), stream_ptr(stream)))
+
+
+def idm_recon_loss_grad(ctx, rec, params, dp, dv, loss_out=None, grad=None, g_dp=None, g_dv=None, g_p_init=None,
+                        g_v_init=None, stream=None):
+    return check(ctx, load().idm_recon_loss_grad(ctx, ctypes.byref(rec), ctypes.byref(params), ptr(dp), ptr(dv),
+                                                 ptr(loss_out), ctypes.byref(grad) if grad is not None else None,
+                                                 ptr(g_dp), ptr(g_dv), ptr(g_p_init), ptr(g_v_init),
+                                                 stream_ptr(stream)))
+
+
+def idm_recon_fit(ctx, rec, params, dp, dv, n_iter, lr0, lr1, box_lo, box_hi, loss_hist=None, stream=None):
+    lo = (ctypes.c_float * 5)(*box_lo)
+    hi = (ctypes.c_float * 5)(*box_hi)
+    return check(ctx, load().idm_recon_fit(ctx, ctypes.byref(rec), ctypes.byref(params), ptr(dp), ptr(dv), n_iter,
+                                           lr0, lr1, lo, hi, ptr(loss_hist), stream_ptr(stream)))
+
+
+def idm_recon_metrics(ctx, rec, params, dp, dv, out, stream=None):
+    return check(ctx, load().idm_recon_metrics(ctx, ctypes.byref(rec), ctypes.byref(params), ptr(dp), ptr(dv),
+                                               ptr(out), stream_ptr(stream)))
+
 
 def make_scene(lane_off, length, max_lane):
     """lane_off (int32 CUDA tensor [L+1]), length (float32 CUDA tensor [N])."""

@@ -203,3 +203,55 @@ def config3_fit(n_lanes=2000, per_lane=100, K=100):
     sc = make_scene([per_lane] * n_lanes, rng)
     sc.update(K=K, dt=0.1, obs_stride=1, name="%dx%d K=%d" % (n_lanes, per_lane, K))
     return sc
+
+
+# ---- observed trajectories for the filtering / reconstruction mode ----------
+#
+# Stand-ins for the paper's trajectory data (Sec. V-B): NGSIM US-101 for
+# filtering (6,101 trajectories, a position every 0.1 s, simulated with dt =
+# 0.1 s) and a non-public Singapore set for reconstruction (21,750
+# trajectories, sampling intervals of at least 1 s, up to 20 minutes long,
+# dt = 1 s).  A trajectory is a smooth speed profile v(t) = vm + A1 sin(w1 t
+# + f1) + A2 sin(w2 t + f2) with vm U[8, 25] m/s, A1 U[0, 0.3 vm], A2 U[0,
+# 0.2 vm] (so v >= vm / 2 > 0), periods U[60, 300] s and U[15, 60] s; its
+# closed-form position from a start U[0, 1000] m is sampled at the
+# observation times and Gaussian noise is added.  Trajectories are returned
+# longest first, so that neighbouring trajectories have similar horizons.
+
+FILTER_SPEC = dict(n=6101, dur=(30.0, 90.0), dense=0.1, noise=0.3, dt=0.1)
+RECON_SPEC = dict(n=21750, dur=(120.0, 1200.0), gap_min=1.0, gap_mean_extra=1.0, noise=1.0, dt=1.0)
+
+
+def recon_observations(n, dur, rng, dense=None, gap_min=1.0, gap_mean_extra=1.0, noise=0.5, sort=True):
+    """(obs_off int32 [n+1], obs_t, obs_p float32-exact float64 [n_obs]).
+    dense: fixed sampling interval (s); else intervals gap_min + Exp(mean
+    gap_mean_extra).  Timestamps start at 0 for every trajectory."""
+    T = rng.uniform(dur[0], dur[1], size=n)
+    if sort:
+        T = np.sort(T)[::-1]
+    vm = rng.uniform(8.0, 25.0, size=n)
+    A1 = rng.uniform(0.0, 0.3, size=n) * vm
+    A2 = rng.uniform(0.0, 0.2, size=n) * vm
+    w1 = 2 * np.pi / rng.uniform(60.0, 300.0, size=n)
+    w2 = 2 * np.pi / rng.uniform(15.0, 60.0, size=n)
+    f1 = rng.uniform(0, 2 * np.pi, size=n)
+    f2 = rng.uniform(0, 2 * np.pi, size=n)
+    p0 = rng.uniform(0.0, 1000.0, size=n)
+    ts = []
+    for i in range(n):
+        if dense is not None:
+            t = np.arange(0.0, T[i] + 1e-9, dense)
+        else:
+            m = int(T[i] / gap_min) + 2
+            t = np.concatenate([[0.0], np.cumsum(gap_min + rng.exponential(gap_mean_extra, size=m))])
+            t = t[t <= T[i]]
+        ts.append(f32(t))
+    counts = np.array([len(t) for t in ts], dtype=np.int64)
+    off = np.zeros(n + 1, dtype=np.int32)
+    off[1:] = np.cumsum(counts)
+    t = np.concatenate(ts)
+    idx = np.repeat(np.arange(n), counts)
+    pos = (p0[idx] + vm[idx] * t - A1[idx] / w1[idx] * (np.cos(w1[idx] * t + f1[idx]) - np.cos(f1[idx]))
+           - A2[idx] / w2[idx] * (np.cos(w2[idx] * t + f2[idx]) - np.cos(f2[idx])))
+    pos = pos + rng.normal(0.0, noise, size=pos.shape)
+    return off, t, f32(pos)
