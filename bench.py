@@ -77,6 +77,9 @@ def parse():
     p.add_argument("--batch-scen", type=int, default=4096)
     p.add_argument("--batch-iters", type=int, default=20)
     # long horizon: fit on the first 2,000 of 3,000 steps, predict the rest
+    p.add_argument("--no-recon", action="store_true")
+    p.add_argument("--recon-only", action="store_true", help="run only the filtering/reconstruction measurement")
+    p.add_argument("--recon-iters", type=int, default=500)
     p.add_argument("--no-long-horizon", action="store_true")
     p.add_argument("--long-only", action="store_true", help="run only the initializer + long-horizon measurement")
     p.add_argument("--long-lanes", type=int, default=20000)
@@ -569,6 +572,94 @@ def batched(a, dev):
     return out
 
 
+# Algorithmic bytes per trajectory-step of one fit iteration of the
+# reconstruction mode: forward reads dp, dv and the observation row (8 B) and
+# writes the tape (8 B); the adjoint reads the tape, dp, dv and four Adam
+# moments (32 B) and writes dp, dv and the moments (24 B).
+RECON_BYTES_PER_STEP = 16 + 8 + 32 + 24
+
+
+def reconstruction(a, dev):
+    """Single-trajectory filtering and reconstruction (Sec. IV-A; settings
+    and metrics of Sec. V-B) on the synthetic stand-ins of the paper's two
+    data sets: every trajectory fitted with 500 Adam iterations (lr 0.1 ->
+    0.01) from the paper's starting point, all trajectories in one launch."""
+    import torch
+    from oracle import recon as R
+    from paper_2412_16750_gb300 import api, synth
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peaks, _ = measured_peaks()
+    out = {}
+    for k, (name, spec, paper_s) in enumerate((("filtering", synth.FILTER_SPEC, 0.308),
+                                               ("reconstruction", synth.RECON_SPEC, 0.164))):
+        rng = np.random.default_rng(synth.SEED_BASE + 50 + k)
+        off, t, p = synth.recon_observations(spec["n"], spec["dur"], rng, dense=spec.get("dense"),
+                                             gap_min=spec.get("gap_min", 1.0),
+                                             gap_mean_extra=spec.get("gap_mean_extra", 1.0), noise=spec["noise"])
+        ctx = api.Context()
+        r = api.Recon(cu(off, torch.int32), cu(t), cu(p), spec["dt"], A_MIN, ctx=ctx)
+        th0, dp0, dv0 = r.init_vars()
+        m0 = r.metrics(th0, dp0, dv0).cpu().numpy()
+        th, dp, dv = th0.clone(), dp0.clone(), dv0.clone()
+        r.fit(th, dp, dv, 3)                                   # warm-up
+        th.copy_(th0), dp.copy_(dp0), dv.copy_(dv0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hist = r.fit(th, dp, dv, a.recon_iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rc, flags = ctx.status()
+        if rc != 0:
+            raise RuntimeError("reconstruction status %d flags %d" % (rc, flags))
+        m1 = r.metrics(th, dp, dv).cpu().numpy()
+        K = r.K.cpu().numpy()[:r.N].astype(np.int64)
+        steps = int(K.sum())
+        h = hist.cpu().numpy()
+        gbs = RECON_BYTES_PER_STEP * steps * a.recon_iters / (ms * 1e-3) / 1e9
+        # the oracle's fit of a bounded sample of the same trajectories
+        n_cpu = 8 if name == "reconstruction" else 16
+        sel = np.linspace(0, spec["n"] - 1, n_cpu).astype(int)
+        offs = np.concatenate([[0], np.cumsum(np.diff(off)[sel])]).astype(np.int32)
+        idx = np.concatenate([np.arange(off[i], off[i + 1]) for i in sel])
+        ok = R.nearest_steps(t[idx], spec["dt"])
+        Ks = R.horizons(offs, ok)
+        p0s, v0s = R.init_state(offs, t[idx], p[idx])
+        ths = np.array(api.RECON_INIT)[:, None].repeat(n_cpu, 1)
+        km = int(Ks.max())
+        tc = time.perf_counter()
+        R.fit(Ks, np.full((km, n_cpu), 10.0), np.zeros((km, n_cpu)), ths, p0s, v0s, spec["dt"], offs, ok, p[idx],
+              a.recon_iters, 0.1, 0.01, api.RECON_BOX_LO, api.RECON_BOX_HI, A_MIN)
+        cpu_s = (time.perf_counter() - tc) / n_cpu
+        out[name] = {
+            "workload": "%d trajectories, %s, durations U[%g, %g] s, noise %g m, dt %g s" % (
+                spec["n"], ("every %g s" % spec["dense"]) if spec.get("dense") else
+                ("intervals %g s + Exp(mean %g s)" % (spec["gap_min"], spec["gap_mean_extra"])),
+                spec["dur"][0], spec["dur"][1], spec["noise"], spec["dt"]),
+            "observations": int(off[-1]), "k_max": r.k_max, "trajectory_steps": steps,
+            "iterations": a.recon_iters, "fit_ms": ms, "s_per_trajectory": ms * 1e-3 / spec["n"],
+            "paper_s_per_trajectory": paper_s,
+            "trajectory_steps_per_s": steps * a.recon_iters / (ms * 1e-3),
+            "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+            "us_per_step_of_longest": ms * 1e3 / (a.recon_iters * r.k_max),
+            "gpu_launches": 1,
+            "loss": {"initial": float(h[0]), "final": float(h[-1])},
+            "metrics_initial": {"pos": float(m0[0]), "acc_mean": float(m0[1]), "acc_std": float(m0[2]),
+                                "imp": float(m0[3])},
+            "metrics_fitted": {"pos": float(m1[0]), "acc_mean": float(m1[1]), "acc_std": float(m1[2]),
+                               "imp": float(m1[3])},
+            "paper_metrics": {"filtering": "Pos 0.08%, Acc 0.5/0.5, Imp 0% (NGSIM)",
+                              "reconstruction": "Pos 0.13%, Acc 0.3/1.1, Imp 0% (Singapore)"}[name],
+            "cpu_oracle_s_per_trajectory": cpu_s, "cpu_oracle_sample": "%d trajectories, 1 core" % n_cpu,
+        }
+        ctx.close()
+        del r, th0, dp0, dv0, th, dp, dv
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(a, rank, world, local_rank):
     import torch
     from paper_2412_16750_gb300 import api, lib, synth
@@ -580,6 +671,10 @@ def run_gpu(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if a.recon_only:
+        if rank == 0:
+            print(json.dumps({"reconstruction": reconstruction(a, dev)}), flush=True)
+        return 0
     if a.batched_only:
         if rank == 0:
             print(json.dumps({"batched": batched(a, dev)}), flush=True)
@@ -757,6 +852,8 @@ def run_gpu(a, rank, world, local_rank):
         net.close()
     if world == 1 and not a.no_batched:
         line["batched"] = batched(a, dev)
+    if world == 1 and not a.no_recon:
+        line["reconstruction"] = reconstruction(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v1, secs1, desc = oracle_sample(iters=30)
         vc, secs_c, cores = oracle_all_cores(iters=10)

@@ -113,23 +113,6 @@ __device__ __forceinline__ float pow_delta1(float r, float delta)
     return r > 0.0f ? __powf(r, delta) : 0.0f;
 }
 
-// Bounded acceleration a* of the ego vehicle at speed v behind the virtual
-// leader (gap dp, speed difference dv): Eq. 1-2 with the Sec. III-C bounds.
-// gap_inv = 1 / max(dp, floor) and u = T + c dv do not depend on v, so they
-// are off the serial chain.
-template <bool D4>
-__device__ __forceinline__ float accel1(float v, float gap_inv, float u, const Par &q, float inv_dt, float a_min)
-{
-    const float s_opt = fmaf(v, u, q.s0);                               // Eq. 1
-    float e1;
-    const float z = softplus1(s_opt, e1) * gap_inv;                     // s* / gap, Sec. III-C
-    const float rd = pow_delta1<D4>(v * q.inv_v0, q.delta);
-    const float a = q.am * ((1.0f - rd) - z * z);                      // Eq. 2
-    const float a_lb = fmaxf(v * -inv_dt, a_min);                       // Sec. III-C
-    float e2;
-    return a_lb + softplus1(a - a_lb, e2);
-}
-
 // Partials of a* at (v, dp, dv) for the reverse step; with sigma2 = d a*/d a,
 // sigma1 = d s*/d s_opt, Sn = 2 a_max z / gap = -d a/d s* and w0n = sigma2
 // Sn sigma1:
@@ -194,9 +177,32 @@ __device__ __forceinline__ Jac1 jac1(float v, float dp, float dv, const Par &q, 
     return J;
 }
 
-// Explicit Euler step (Eq. 3) with the position kept as an FP32 pair
-// (TwoSum plus the exact rounding error of dt v).
-__device__ __forceinline__ void euler1(float &ph, float &pl, float &v, float a_star, float dt)
+// The speed update of one explicit Euler step (Eq. 3) with a* of Eq. 1-2
+// and Sec. III-C, arranged so that the serial chain v -> v' has a single FMA
+// after each softplus: with sp(x) = max(x, 0) + ln 2 log2(1 + exp(-|x|)),
+//   z  = s* / gap = fma(ln2 / gap, log2(1 + e1), max(s_opt, 0) / gap),
+//   v' = v + dt a* = fma(dt ln2, log2(1 + e2), v + dt max(a, a_lb)),
+// everything else (1 - r^delta, a_lb, the max terms) runs beside the chain.
+// a_star receives a* = max(a, a_lb) + ln 2 log2(1 + e2).
+template <bool D4>
+__device__ __forceinline__ float speed_step(float v, float gap_inv, float u, const Par &q, float dt, float inv_dt,
+                                            float a_min, float &a_star)
+{
+    const float s_opt = fmaf(v, u, q.s0);                                       // Eq. 1
+    const float e1 = ex2_approx(fabsf(s_opt) * -LOG2E);
+    const float z = fmaf(LN2 * gap_inv, lg2_approx(1.0f + e1), fmaxf(s_opt, 0.0f) * gap_inv);
+    const float rd = pow_delta1<D4>(v * q.inv_v0, q.delta);
+    const float a = fmaf(-q.am, z * z, q.am * (1.0f - rd));                    // Eq. 2
+    const float a_lb = fmaxf(v * -inv_dt, a_min);                               // Sec. III-C
+    const float l2 = lg2_approx(1.0f + ex2_approx(fabsf(a - a_lb) * -LOG2E));
+    const float m = fmaxf(a, a_lb);
+    a_star = fmaf(LN2, l2, m);
+    return fmaf(dt * LN2, l2, fmaf(dt, m, v));
+}
+
+// The position update of the Euler step (Eq. 3, old speed) on an FP32 pair:
+// TwoSum plus the exact rounding error of dt v.
+__device__ __forceinline__ void euler_pos(float &ph, float &pl, float v, float dt)
 {
     const float d = dt * v;
     const float en = fmaf(-dt, v, d);
@@ -205,7 +211,14 @@ __device__ __forceinline__ void euler1(float &ph, float &pl, float &v, float a_s
     const float err = (ph - (t - bb)) + (d - bb);
     ph = t;
     pl = pl + (err - en);
-    v = fmaf(dt, a_star, v);
+}
+
+__device__ __forceinline__ void kahan(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 __device__ __forceinline__ float sgn(float r) { return (float)((r > 0.0f) - (r < 0.0f)); }
@@ -268,71 +281,78 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
     const float dt = a.dt, inv_dt = a.inv_dt, a_min = a.a_min;
     float v = act ? a.v_init[i] : 0.0f;
     float ph = act ? a.p_init[i] : 0.0f, pl = 0.0f;
-    double L = 0.0;
+    float Ls = 0.0f, Lcomp = 0.0f;   // loss: per-thread Kahan sum of the chunk sums
     const int j_end =
         (MODE == LOSS_GRAD || MODE == FIT || MODE == METRICS) && Ki > 0 ? min(a.obs_off[i + 1], a.n_obs) : 0;
     for (int c = 0; c < nch; ++c) {
         issue(c + S - 1);
         cp_wait<S - 1>();
+        float Lc = 0.0f;
+        // Branch-free over the chunk: a lane past its horizon computes on
+        // stale staged values and keeps its state (selects, predicated stores).
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = c * U + u;
-            if (k < Ki) {
-                const float dp = *slot(sm, c, 0, u, lane), dv = *slot(sm, c, 1, u, lane);
-                const float gap_inv = rcp_approx(fmaxf(dp, IDM_GAP_FLOOR));
-                const float uu = fmaf(dv, q.c, q.T);
-                const float as = accel1<D4>(v, gap_inv, uu, q, inv_dt, a_min);
-                const float v_k = v;
-                euler1(ph, pl, v, as, dt);
-                const size_t o = (size_t)k * ld + i;
-                if (MODE == FWD_OUT) {
+            const bool valid = k < Ki;
+            const float dp = *slot(sm, c, 0, u, lane), dv = *slot(sm, c, 1, u, lane);
+            const float gap_inv = rcp_approx(fmaxf(dp, IDM_GAP_FLOOR));
+            const float uu = fmaf(dv, q.c, q.T);
+            float as;
+            const float vn = speed_step<D4>(v, gap_inv, uu, q, dt, inv_dt, a_min, as);
+            float phn = ph, pln = pl;
+            euler_pos(phn, pln, v, dt);
+            const float v_k = v;
+            v = valid ? vn : v;
+            ph = valid ? phn : ph;
+            pl = valid ? pln : pl;
+            const size_t o = (size_t)k * ld + i;
+            if (MODE == FWD_OUT) {
+                if (valid) {
                     if (a.P) a.P[o + ld] = ph + pl;
                     if (a.V) a.V[o + ld] = v;
                     if (a.A) a.A[o] = as;
-                } else {
-                    float seed = 0.0f;
-                    const int code = __float_as_int(*slot(sm, c, 3, u, lane));
-                    if (code >= 0) {
-                        // observations at step k+1: the staged first one, then any
-                        // further ones from the CSR
-                        const float y = *slot(sm, c, 2, u, lane);
-                        float r = (ph - y) + pl;
-                        seed = sgn(r);
-                        L += fabs((double)r);
+                }
+            } else {
+                // observations at step k+1: the staged first one, then any
+                // further ones from the CSR
+                const int code = valid ? __float_as_int(*slot(sm, c, 3, u, lane)) : -1;
+                const bool has = code >= 0;
+                float r = (ph - *slot(sm, c, 2, u, lane)) + pl;
+                float seed = has ? sgn(r) : 0.0f;
+                Lc += has ? fabsf(r) : 0.0f;
+                if (MODE == METRICS && has) {
+                    ma.pos += fabs((double)r) * len_inv;
+                    ++ma.n_pos;
+                }
+                if (has && (code & 7) > 1) {
+                    const int cnt = code & 7, j0 = code >> 3;
+                    for (int j = j0 + 1; j < j_end; ++j) {
+                        if (cnt < 7 ? j >= j0 + cnt : a.obs_k[j] != k + 1) break;
+                        r = (ph - a.obs_p[j]) + pl;
+                        seed += sgn(r);
+                        Lc += fabsf(r);
                         if (MODE == METRICS) {
                             ma.pos += fabs((double)r) * len_inv;
                             ++ma.n_pos;
                         }
-                        const int cnt = code & 7;
-                        if (cnt > 1) {
-                            const int j0 = code >> 3;
-                            for (int j = j0 + 1; j < j_end; ++j) {
-                                if (cnt < 7 ? j >= j0 + cnt : a.obs_k[j] != k + 1) break;
-                                r = (ph - a.obs_p[j]) + pl;
-                                seed += sgn(r);
-                                L += fabs((double)r);
-                                if (MODE == METRICS) {
-                                    ma.pos += fabs((double)r) * len_inv;
-                                    ++ma.n_pos;
-                                }
-                            }
-                        }
                     }
-                    if (MODE == LOSS_GRAD || MODE == FIT) {
-                        a.tv[o] = v_k;
-                        a.ts[o] = seed;
-                    }
-                    if (MODE == METRICS) {
-                        const double aa = fabs((double)as);
-                        ma.s1 += aa;
-                        ma.s2 += aa * aa;
-                        ++ma.n_a;
-                        ma.imp |= aa > 10.0;
-                    }
+                }
+                if ((MODE == LOSS_GRAD || MODE == FIT) && valid) {
+                    a.tv[o] = v_k;
+                    a.ts[o] = seed;
+                }
+                if (MODE == METRICS && valid) {
+                    const double aa = fabs((double)as);
+                    ma.s1 += aa;
+                    ma.s2 += aa * aa;
+                    ++ma.n_a;
+                    ma.imp |= aa > 10.0;
                 }
             }
         }
+        kahan(Ls, Lcomp, Lc);
     }
+    const double L = (double)Ls - (double)Lcomp;
     cp_wait<0>();
     if (MODE == FWD_OUT && act) {
         // rows beyond the trajectory's horizon hold its final state
@@ -399,32 +419,48 @@ __device__ __forceinline__ void adj_phase(const Args &a, const Par &q, int i, in
     for (int c = 0; c < nch; ++c) {
         issue(c + S - 1);
         cp_wait<S - 1>();
+        // The partials of the U steps are independent of the adjoint state:
+        // all of them first (they overlap), then the serial lambda_p,
+        // lambda_v and sums, updated by selects for the lane's valid steps
+        // (a lane past its horizon computes on stale staged values).
+        Jac1 J[U];
+        float vk[U], dpk[U], dvk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            vk[u] = *slot(sm, c, 0, u, lane);
+            dpk[u] = *slot(sm, c, 2, u, lane);
+            dvk[u] = *slot(sm, c, 3, u, lane);
+            J[u] = jac1<D4, WD>(vk[u], dpk[u], dvk[u], q, inv_dt, a_min);
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = Kw - 1 - (c * U + u);
-            if (k >= 0 && k < Ki) {
-                const float vk = *slot(sm, c, 0, u, lane);
-                lp += *slot(sm, c, 1, u, lane);                         // lambda_p(k+1)
-                const float dp = *slot(sm, c, 2, u, lane), dv = *slot(sm, c, 3, u, lane);
-                const float mu = dt * lv;                                // dt lambda_v(k+1)
-                const Jac1 J = jac1<D4, WD>(vk, dp, dv, q, inv_dt, a_min);
-                const float gdp = mu * J.Adp, gdv = mu * J.Adv;
-                Acc[0] = fmaf(mu, J.w0n, Acc[0]);
-                Acc[1] = fmaf(mu, J.w0n * vk, Acc[1]);
-                Acc[2] = fmaf(mu, (J.w0n * vk) * dv, Acc[2]);
-                Acc[3] = fmaf(mu, J.fa, Acc[3]);
-                Acc[4] = fmaf(mu, J.frd, Acc[4]);
-                if (WD) Acc[5] = fmaf(mu, J.frdl, Acc[5]);
-                lv = fmaf(mu, J.Av, fmaf(dt, lp, lv));                  // lambda_v(k)
-                const size_t o = (size_t)k * ld + i;
-                if (MODE == LOSS_GRAD) {
-                    if (a.g_dp) a.g_dp[o] = gdp;
-                    if (a.g_dv) a.g_dv[o] = gdv;
-                } else if (MODE == FIT) {
-                    float m0 = *slot(sm, c, 4, u, lane), w0 = *slot(sm, c, 5, u, lane);
-                    float m1 = *slot(sm, c, 6, u, lane), w1 = *slot(sm, c, 7, u, lane);
-                    a.dp[o] = adam1(dp, gdp, m0, w0, a1, isb2);
-                    a.dv[o] = adam1(dv, gdv, m1, w1, a1, isb2);
+            const bool valid = k >= 0 && k < Ki;
+            const float lpn = lp + *slot(sm, c, 1, u, lane);             // lambda_p(k+1)
+            const float mu = dt * lv;                                    // dt lambda_v(k+1)
+            const float lvn = fmaf(mu, J[u].Av, fmaf(dt, lpn, lv));      // lambda_v(k)
+            const float gdp = mu * J[u].Adp, gdv = mu * J[u].Adv;
+            const float wv = J[u].w0n * vk[u];
+            Acc[0] = valid ? fmaf(mu, J[u].w0n, Acc[0]) : Acc[0];
+            Acc[1] = valid ? fmaf(mu, wv, Acc[1]) : Acc[1];
+            Acc[2] = valid ? fmaf(mu, wv * dvk[u], Acc[2]) : Acc[2];
+            Acc[3] = valid ? fmaf(mu, J[u].fa, Acc[3]) : Acc[3];
+            Acc[4] = valid ? fmaf(mu, J[u].frd, Acc[4]) : Acc[4];
+            if (WD) Acc[5] = valid ? fmaf(mu, J[u].frdl, Acc[5]) : Acc[5];
+            lp = valid ? lpn : lp;
+            lv = valid ? lvn : lv;
+            const size_t o = (size_t)k * ld + i;
+            if (MODE == LOSS_GRAD) {
+                if (valid && a.g_dp) a.g_dp[o] = gdp;
+                if (valid && a.g_dv) a.g_dv[o] = gdv;
+            } else if (MODE == FIT) {
+                float m0 = *slot(sm, c, 4, u, lane), w0 = *slot(sm, c, 5, u, lane);
+                float m1 = *slot(sm, c, 6, u, lane), w1 = *slot(sm, c, 7, u, lane);
+                const float dpn = adam1(dpk[u], gdp, m0, w0, a1, isb2);
+                const float dvn = adam1(dvk[u], gdv, m1, w1, a1, isb2);
+                if (valid) {
+                    a.dp[o] = dpn;
+                    a.dv[o] = dvn;
                     a.mom[0][o] = m0;
                     a.mom[1][o] = w0;
                     a.mom[2][o] = m1;
