@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--batch-iters", type=int, default=20)
     # long horizon: fit on the first 2,000 of 3,000 steps, predict the rest
     p.add_argument("--no-recon", action="store_true")
+    p.add_argument("--no-crossover", action="store_true")
+    p.add_argument("--crossover-only", action="store_true", help="run only the CPU-backend / GPU crossover")
     p.add_argument("--recon-only", action="store_true", help="run only the filtering/reconstruction measurement")
     p.add_argument("--recon-iters", type=int, default=500)
     p.add_argument("--no-long-horizon", action="store_true")
@@ -660,6 +662,55 @@ def reconstruction(a, dev):
     return out
 
 
+def cpu_gpu_crossover(a, dev):
+    """Time of one loss + gradient (forward and adjoint over K = 100 steps)
+    per vehicle count on the multi-threaded CPU backend (every host core)
+    and on the GPU, lanes of 100 vehicles: the comparison of the paper's
+    Fig. 1 (CPU faster for small counts, GPU beyond about 20K vehicles)."""
+    import torch
+    from paper_2412_16750_gb300 import api, build, cpu, synth
+    build.build_cpu()
+    K, s = 100, 1
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for N in (1000, 4000, 16000, 64000, 256000, 1000000, 2000000):
+        sc = synth.make_scene([min(100, N)] * max(1, N // 100), np.random.default_rng(synth.SEED_BASE + 60))
+        n = len(sc["length"])
+        th = synth.plain_init(n)
+        Y = synth.f32(np.random.default_rng(1).normal(0.0, 1.0, size=(K, n)) + sc["p_init"][None, :] +
+                      np.arange(1, K + 1)[:, None] * 1.5)
+        cs = cpu.Scene(sc["lane_off"], sc["length"])
+        cpu.idm_cpu_loss_grad(th, sc["p_init"], sc["v_init"], cs, K, DT, Y, s, A_MIN)
+        reps = max(1, min(20, int(2e6 // n)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            cpu.idm_cpu_loss_grad(th, sc["p_init"], sc["v_init"], cs, K, DT, Y, s, A_MIN)
+        cpu_ms = (time.perf_counter() - t0) * 1e3 / reps
+        cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+        ctx = api.Context()
+        scene = api.Scene.from_lane_off(cu(sc["lane_off"], torch.int32), cu(sc["length"]))
+        tg, pg, vg, Yg = cu(th), cu(sc["p_init"]), cu(sc["v_init"]), cu(Y)
+        for _ in range(3):
+            api.loss_grad(tg, pg, vg, scene, K, DT, Yg, s, A_MIN, ctx=ctx)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.loss_grad(tg, pg, vg, scene, K, DT, Yg, s, A_MIN, ctx=ctx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gpu_ms = sorted(ts)[len(ts) // 2]
+        ctx.close()
+        rows.append({"vehicles": n, "cpu_ms": cpu_ms, "gpu_ms": gpu_ms,
+                     "cpu_ms_per_timestep": cpu_ms / K, "gpu_ms_per_timestep": gpu_ms / K})
+    cross = next((r["vehicles"] for r in rows if r["gpu_ms"] < r["cpu_ms"]), None)
+    return {"workload": "loss + gradient, K = 100 steps, lanes of 100 vehicles, every step observed",
+            "cpu_threads": cpu.max_threads(), "rows": rows, "gpu_faster_from_vehicles": cross,
+            "paper": "Fig. 1: CPU (16 threads) faster below ~20K vehicles, GPU beyond"}
+
+
 def run_gpu(a, rank, world, local_rank):
     import torch
     from paper_2412_16750_gb300 import api, lib, synth
@@ -671,6 +722,10 @@ def run_gpu(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if a.crossover_only:
+        if rank == 0:
+            print(json.dumps({"cpu_gpu_crossover": cpu_gpu_crossover(a, dev)}), flush=True)
+        return 0
     if a.recon_only:
         if rank == 0:
             print(json.dumps({"reconstruction": reconstruction(a, dev)}), flush=True)
@@ -854,6 +909,8 @@ def run_gpu(a, rank, world, local_rank):
         line["batched"] = batched(a, dev)
     if world == 1 and not a.no_recon:
         line["reconstruction"] = reconstruction(a, dev)
+    if world == 1 and not a.no_crossover:
+        line["cpu_gpu_crossover"] = cpu_gpu_crossover(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v1, secs1, desc = oracle_sample(iters=30)
         vc, secs_c, cores = oracle_all_cores(iters=10)

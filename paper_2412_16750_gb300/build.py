@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libidm.so")
+CPU_LIB = os.path.join(BUILD, "libidm_cpu.so")
+CPU_SRC = os.path.join(CSRC, "idm_cpu.cpp")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -41,7 +43,24 @@ def up_to_date():
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def build_cpu(force=False):
+    """libidm_cpu.so: the multi-threaded CPU backend (g++, OpenMP; no CUDA)."""
+    hdrs = [CPU_SRC, os.path.join(ROOT, "include", "idm_cpu.h"), os.path.join(ROOT, "include", "idm.h")]
+    if not force and os.path.exists(CPU_LIB) and all(os.path.getmtime(h) <= os.path.getmtime(CPU_LIB) for h in hdrs):
+        return CPU_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = CPU_LIB + ".tmp%d" % os.getpid()
+    cmd = [shutil.which("g++") or "g++", "-O3", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+           "-I" + os.path.join(ROOT, "include"), CPU_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("g++ failed for %s:\n%s\n%s" % (CPU_SRC, r.stdout, r.stderr))
+    os.replace(tmp, CPU_LIB)
+    return CPU_LIB
+
+
 def build(force=False, verbose=False, extra_flags=()):
+    build_cpu(force)
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

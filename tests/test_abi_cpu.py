@@ -9,10 +9,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def header_functions():
+CPU_HEADER = "idm_cpu.h"   # declared by libidm_cpu.so, the separate CPU backend
+
+
+def header_functions(cpu=False):
+    """Functions declared by the CUDA library's headers (cpu=False) or by the
+    CPU backend's header (cpu=True)."""
     src = ""
     for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if name.endswith(".h"):
+        if name.endswith(".h") and (name == CPU_HEADER) == cpu:
             src += open(os.path.join(ROOT, "include", name)).read() + "\n"
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|int|size_t)\s*\**\s*(idm_\w+)\s*\(", src, flags=re.M)))
@@ -55,6 +60,17 @@ def test_null_context_is_rejected(libpath):
     assert L.idm_ctx_create(None, 0) == lib.IDM_ERR_ARG
     assert L.idm_ctx_destroy(None) == lib.IDM_OK
     assert L.idm_set_tuning(None, 0, 0, 16, 8) == lib.IDM_ERR_ARG
+
+
+def test_cpu_backend_exports_its_header():
+    from paper_2412_16750_gb300 import build, cpu
+    path = build.build_cpu()
+    lib = ctypes.CDLL(path)
+    names = header_functions(cpu=True)
+    assert names and all(hasattr(lib, n) for n in names)
+    assert set(cpu.exported_symbols()) == set(names)
+    # the CUDA library carries no CPU path
+    assert not any(hasattr(ctypes.CDLL(build.LIB), n) for n in names)
 
 
 def test_missing_library_fails_loudly(tmp_path):
