@@ -673,7 +673,7 @@ def cpu_gpu_crossover(a, dev):
     K, s = 100, 1
     stream = torch.cuda.current_stream(dev)
     rows = []
-    for N in (1000, 4000, 16000, 64000, 256000, 1000000, 2000000):
+    for N in (100, 300, 1000, 4000, 16000, 64000, 256000, 1000000, 2000000):
         sc = synth.make_scene([min(100, N)] * max(1, N // 100), np.random.default_rng(synth.SEED_BASE + 60))
         n = len(sc["length"])
         th = synth.plain_init(n)
