@@ -17,3 +17,4 @@ from .ref import (  # noqa: F401
 )
 from . import mlp_oracle  # noqa: F401,E402
 from . import recon  # noqa: F401,E402
+from . import lanes  # noqa: F401,E402
