@@ -79,6 +79,10 @@ def parse():
     # long horizon: fit on the first 2,000 of 3,000 steps, predict the rest
     p.add_argument("--no-recon", action="store_true")
     p.add_argument("--no-crossover", action="store_true")
+    p.add_argument("--no-pred", action="store_true")
+    p.add_argument("--pred-only", action="store_true", help="run only the lane-geometry prediction measurement")
+    p.add_argument("--pred-scen", type=int, default=10000)
+    p.add_argument("--pred-iters", type=int, default=500)
     p.add_argument("--crossover-only", action="store_true", help="run only the CPU-backend / GPU crossover")
     p.add_argument("--recon-only", action="store_true", help="run only the filtering/reconstruction measurement")
     p.add_argument("--recon-iters", type=int, default=500)
@@ -711,6 +715,61 @@ def cpu_gpu_crossover(a, dev):
             "paper": "Fig. 1: CPU (16 threads) faster below ~20K vehicles, GPU beyond"}
 
 
+def prediction(a, dev):
+    """Training-free prediction with lane geometry (Sec. IV-B, V-C) on a
+    synthetic stand-in for the Waymo Open Motion validation set: assign and
+    project 1 s of history (11 frames at 10 Hz) onto lane centre lines, fit
+    the IDM parameters on the 10 history steps (500 Adam iterations), roll out
+    80 steps (8 s), project back and score against the true future."""
+    import torch
+    from paper_2412_16750_gb300 import api, synth
+    cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sc = synth.prediction_scenes(a.pred_scen, np.random.default_rng(synth.SEED_BASE + 70))
+    H, Fn = sc["n_hist"], sc["n_fut"]
+    N = sc["x"].shape[1]
+    ctx = api.Context()
+    L = api.Lanes(cu(sc["pt_off"], torch.int32), cu(sc["px"]), cu(sc["py"]), ctx=ctx)
+    xh, yh = cu(sc["x"][:H]), cu(sc["y"][:H])
+    lo, hi = cu(sc["lane_lo"], torch.int32), cu(sc["lane_hi"], torch.int32)
+    xt, yt = cu(sc["x"][H:]), cu(sc["y"][H:])
+    api.predict_rollout(L, xh, yh, lo, hi, sc["dt"], Fn, 3, ctx=ctx)          # warm-up
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    lane, _, _ = L.project(xh[H - 1], yh[H - 1], lo, hi, want=("lane",))
+    _, s_hist, _ = L.project(xh, yh, lane.view(N), None, want=("s",))
+    ev[1].record(stream)
+    out = api.predict_rollout(L, xh, yh, lo, hi, sc["dt"], Fn, a.pred_iters, ctx=ctx)
+    perm = out["perm"]
+    tx, ty = torch.empty_like(xt), torch.empty_like(yt)
+    from paper_2412_16750_gb300 import lib
+    lib.idm_gather_rows(ctx.handle, N, Fn, perm, xt, tx, stream)
+    lib.idm_gather_rows(ctx.handle, N, Fn, perm, yt, ty, stream)
+    ade, fde, sums = api.displacement(out["x"], out["y"], tx, ty, 2.0, ctx=ctx)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    rc, flags = ctx.status()
+    if rc != 0:
+        raise RuntimeError("prediction status %d flags %d" % (rc, flags))
+    sums = sums.cpu().numpy()
+    seg_assign = int(np.sum((sc["pt_off"][sc["lane_hi"]] - sc["pt_off"][sc["lane_lo"]]) - (sc["lane_hi"] - sc["lane_lo"])))
+    seg_proj = int(H * np.sum(sc["pt_off"][out["lane"].cpu().numpy() + 1] - sc["pt_off"][out["lane"].cpu().numpy()] - 1))
+    proj_ms = ev[0].elapsed_time(ev[1])
+    total_ms = ev[1].elapsed_time(ev[2])
+    res = {"workload": "%d scenarios, lanes U[2, 8] per scenario (300 m arcs sampled every 2 m), agents U[1, 6] per "
+                       "lane, 1 s history at 10 Hz, 8 s future" % a.pred_scen,
+           "agents": N, "lanes": sc["n_lanes"], "fit_iterations": a.pred_iters,
+           "pipeline_ms": total_ms, "ms_per_scenario": total_ms / a.pred_scen,
+           "projection_ms": proj_ms, "projection_segments": seg_assign + seg_proj,
+           "projection_segments_per_s": (seg_assign + seg_proj) / (proj_ms * 1e-3),
+           "ade_m": float(sums[0] / N), "fde_m": float(sums[1] / N), "miss_rate_2m": float(sums[2] / N),
+           "final_loss": float(out["loss"][-1].item()),
+           "paper": "WOMD validation: minADE 7.862 m, minFDE 15.668 m, miss rate 0.586 (Table II)"}
+    ctx.close()
+    return res
+
+
 def run_gpu(a, rank, world, local_rank):
     import torch
     from paper_2412_16750_gb300 import api, lib, synth
@@ -722,6 +781,10 @@ def run_gpu(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if a.pred_only:
+        if rank == 0:
+            print(json.dumps({"prediction": prediction(a, dev)}), flush=True)
+        return 0
     if a.crossover_only:
         if rank == 0:
             print(json.dumps({"cpu_gpu_crossover": cpu_gpu_crossover(a, dev)}), flush=True)
@@ -909,6 +972,8 @@ def run_gpu(a, rank, world, local_rank):
         line["batched"] = batched(a, dev)
     if world == 1 and not a.no_recon:
         line["reconstruction"] = reconstruction(a, dev)
+    if world == 1 and not a.no_pred:
+        line["prediction"] = prediction(a, dev)
     if world == 1 and not a.no_crossover:
         line["cpu_gpu_crossover"] = cpu_gpu_crossover(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -453,3 +453,105 @@ class Recon:
         out = torch.zeros(4, device="cuda", dtype=torch.float64)
         lib.idm_recon_metrics(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, out, _stream())
         return out
+
+
+# ---- lane geometry and training-free prediction (Sec. IV-B, Sec. V-C) -------
+
+PRED_LENGTH = 4.5          # vehicle length (m) used for the gaps of projected agents
+# the fitting box of the lane fit (a_max down to 0.5 m/s^2), from the start RECON_INIT
+PRED_BOX_LO = (20.0, 0.1, 1.0, 0.5, 0.1)
+PRED_BOX_HI = (60.0, 5.0, 10.0, 10.0, 5.0)
+
+
+class Lanes:
+    """Lane centre lines (polyline CSR) on the device, with their cumulative
+    arc lengths from idm_lane_prepare."""
+
+    def __init__(self, pt_off, px, py, ctx=None):
+        self.ctx = ctx or default_context()
+        self.pt_off = pt_off.to(device="cuda", dtype=torch.int32).contiguous()
+        self.px, self.py = _f32(px), _f32(py)
+        self.n_lanes = self.pt_off.numel() - 1
+        self.n_points = self.px.numel()
+        self.lane_len = torch.empty(self.n_points, device="cuda", dtype=torch.float32)
+        lib.idm_lane_prepare(self.ctx.handle, self.n_lanes, self.n_points, self.pt_off, self.px, self.py,
+                             self.lane_len, _stream())
+
+    def c(self):
+        return lib.idm_lanes_t(self.n_lanes, self.n_points, self.pt_off.data_ptr(), self.px.data_ptr(),
+                               self.py.data_ptr(), self.lane_len.data_ptr())
+
+    def project(self, x, y, lane_lo, lane_hi=None, want=("lane", "s", "d")):
+        """Points (x, y) of shape (rows, cols) onto lanes: (lane, s, d) of the same shape."""
+        x, y = _f32(x), _f32(y)
+        rows, cols = (1, x.numel()) if x.dim() == 1 else tuple(x.shape)
+        lane = torch.empty((rows, cols), device="cuda", dtype=torch.int32) if "lane" in want else None
+        s = torch.empty((rows, cols), device="cuda", dtype=torch.float32) if "s" in want else None
+        d = torch.empty((rows, cols), device="cuda", dtype=torch.float32) if "d" in want else None
+        lo = lane_lo.to(device="cuda", dtype=torch.int32).contiguous()
+        hi = lane_hi.to(device="cuda", dtype=torch.int32).contiguous() if lane_hi is not None else None
+        lib.idm_lane_project(self.ctx.handle, self.c(), rows, cols, x, y, lo, hi, lane, s, d, _stream())
+        return lane, s, d
+
+    def unproject(self, s, lane_of_col):
+        s = _f32(s)
+        rows, cols = (1, s.numel()) if s.dim() == 1 else tuple(s.shape)
+        x = torch.empty((rows, cols), device="cuda", dtype=torch.float32)
+        y = torch.empty_like(x)
+        lib.idm_lane_unproject(self.ctx.handle, self.c(), rows, cols, s,
+                               lane_of_col.to(device="cuda", dtype=torch.int32).contiguous(), x, y, _stream())
+        return x, y
+
+
+def rollout_state(s_rows, row_a, row_b, dt, ctx=None):
+    ctx = ctx or default_context()
+    s_rows = _f32(s_rows)
+    N = s_rows.shape[1]
+    p = torch.empty(N, device="cuda", dtype=torch.float32)
+    v = torch.empty(N, device="cuda", dtype=torch.float32)
+    lib.idm_rollout_state(ctx.handle, N, s_rows, row_a, row_b, dt, p, v, _stream())
+    return p, v
+
+
+def displacement(px, py, tx, ty, miss_m=2.0, ctx=None):
+    """(ade [N], fde [N], sums float64 [3]) of time-major (F, N) predictions."""
+    ctx = ctx or default_context()
+    F, N = px.shape
+    ade = torch.empty(N, device="cuda", dtype=torch.float32)
+    fde = torch.empty(N, device="cuda", dtype=torch.float32)
+    sums = torch.zeros(3, device="cuda", dtype=torch.float64)
+    lib.idm_displacement(ctx.handle, F, N, _f32(px), _f32(py), _f32(tx), _f32(ty), miss_m, ade, fde, sums,
+                         _stream())
+    return ade, fde, sums
+
+
+def predict_rollout(lanes, x_hist, y_hist, lane_lo, lane_hi, dt, n_fut, n_iter=500, lr0=0.1, lr1=0.01,
+                    box_lo=PRED_BOX_LO, box_hi=PRED_BOX_HI, theta0=RECON_INIT, a_min=-10.0, ctx=None):
+    """Training-free prediction (Sec. IV-B, V-C): assign every agent to the
+    nearest candidate lane at the last history frame, project its history
+    onto that lane, order the agents lane by lane (head first), fit the IDM
+    parameters to the H - 1 history steps, roll out n_fut steps from the last
+    history frame and project the rollout back onto the lane centre lines.
+    x_hist, y_hist: (H, N).  Returns a dict (agents in the fitted order given
+    by perm): perm, lane, theta, loss history, s_hist (H, N), x, y (n_fut, N)."""
+    ctx = ctx or default_context()
+    st = _stream()
+    x_hist, y_hist = _f32(x_hist), _f32(y_hist)
+    H, N = x_hist.shape
+    lane, _, _ = lanes.project(x_hist[H - 1], y_hist[H - 1], lane_lo, lane_hi, want=("lane",))
+    lane = lane.view(N)
+    _, s_hist, _ = lanes.project(x_hist, y_hist, lane, None, want=("s",))
+    perm, lane_off, _ = layout(lane, s_hist[0], lanes.n_lanes, ctx=ctx)
+    s_sorted = torch.empty_like(s_hist)
+    lib.idm_gather_rows(ctx.handle, N, H, perm, s_hist, s_sorted, st)
+    lane_sorted = torch.empty(N, device="cuda", dtype=torch.int32)
+    lib.idm_gather(ctx.handle, N, perm, [lane.view(torch.float32)], [lane_sorted.view(torch.float32)], st)
+    scene = Scene.from_lane_off(lane_off, torch.full((N,), PRED_LENGTH, device="cuda", dtype=torch.float32))
+    p0, v0 = rollout_state(s_sorted, 0, 1, dt, ctx=ctx)
+    theta = torch.tensor(theta0, dtype=torch.float32, device="cuda")[:, None].repeat(1, N).contiguous()
+    hist = fit(theta, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, n_iter, lr0, lr1, box_lo, box_hi, a_min, ctx=ctx)
+    pr, vr = rollout_state(s_sorted, H - 2, H - 1, dt, ctx=ctx)
+    traj = simulate(theta, pr, vr, scene, n_fut, dt, a_min, ctx=ctx)
+    x, y = lanes.unproject(traj[1:], lane_sorted)
+    return dict(perm=perm, lane=lane_sorted, lane_off=lane_off, theta=theta, loss=hist, s_hist=s_sorted, x=x, y=y,
+                p_roll=pr, v_roll=vr)

@@ -12,6 +12,7 @@
 #include <new>
 
 #include "../../include/idm.h"
+#include "../../include/idm_lanes.h"
 #include "../../include/idm_recon.h"
 #include "idm_ctx.h"
 #include "idm_internal.h"
@@ -467,6 +468,8 @@ int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
     if (h & IDM_STATUS_NONFINITE) return fail(c, IDM_ERR_NONFINITE, "device status 0x%x: non-finite value", h);
     if (h & IDM_STATUS_BAD_OBS)
         return fail(c, IDM_ERR_OBS, "device status 0x%x: malformed observations or horizons", h);
+    if (h & IDM_STATUS_BAD_LANES)
+        return fail(c, IDM_ERR_LANES, "device status 0x%x: malformed lane polylines or lane index", h);
     return IDM_OK;
 }
 

@@ -18,12 +18,14 @@ IDM_ERR_NONFINITE = 4
 IDM_ERR_TIMEOUT = 5
 IDM_ERR_LANE = 6
 IDM_ERR_OBS = 7
+IDM_ERR_LANES = 8
 
 IDM_STATUS_LANE_TOO_LONG = 1
 IDM_STATUS_BAD_LANE_OFF = 2
 IDM_STATUS_NONFINITE = 4
 IDM_STATUS_TIMEOUT = 8
 IDM_STATUS_BAD_OBS = 16
+IDM_STATUS_BAD_LANES = 32
 
 IDM_MLP_IN = 80
 IDM_MLP_HIDDEN = 256
@@ -59,6 +61,11 @@ class idm_recon_t(ctypes.Structure):
     _fields_ = [("n_traj", ctypes.c_int32), ("k_max", ctypes.c_int32), ("ld", ctypes.c_int32),
                 ("n_obs", ctypes.c_int64), ("obs_off", _vp), ("obs_t", _vp), ("obs_p", _vp), ("obs_k", _vp),
                 ("K", _vp), ("p_init", _vp), ("v_init", _vp), ("dt", ctypes.c_float), ("a_min", ctypes.c_float)]
+
+
+class idm_lanes_t(ctypes.Structure):
+    _fields_ = [("n_lanes", ctypes.c_int32), ("n_points", ctypes.c_int32), ("pt_off", _vp), ("px", _vp),
+                ("py", _vp), ("lane_len", _vp)]
 
 
 # name -> (restype, argtypes)
@@ -124,6 +131,16 @@ _SIGS = {
                                     ctypes.POINTER(idm_sim_t), _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                     ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                     _vp, _vp, _vp, _vp]),
+    # lane geometry of the prediction (include/idm_lanes.h)
+    "idm_lane_prepare": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "idm_lane_project": (ctypes.c_int, [_vp, ctypes.POINTER(idm_lanes_t), ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                        _vp, _vp, _vp, _vp, _vp, _vp]),
+    "idm_lane_unproject": (ctypes.c_int, [_vp, ctypes.POINTER(idm_lanes_t), ctypes.c_int32, ctypes.c_int32, _vp,
+                                          _vp, _vp, _vp, _vp]),
+    "idm_rollout_state": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                         _vp, _vp, _vp]),
+    "idm_displacement": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_float, _vp,
+                                        _vp, _vp, _vp]),
     # single-trajectory reconstruction mode (include/idm_recon.h)
     "idm_recon_prepare": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_float, _vp,
                                          _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int32), _vp]),
@@ -332,6 +349,33 @@ def idm_batch_fit(ctx, batch, params, p_init, v_init, targets, n_iter, lr0, lr1,
 
 
 # ---- struct builders ---------------------------------------------------------
+
+def idm_lane_prepare(ctx, n_lanes, n_points, pt_off, px, py, lane_len_out, stream=None):
+    return check(ctx, load().idm_lane_prepare(ctx, n_lanes, n_points, ptr(pt_off), ptr(px), ptr(py),
+                                              ptr(lane_len_out), stream_ptr(stream)))
+
+
+def idm_lane_project(ctx, lanes, n_rows, n_cols, qx, qy, lane_lo, lane_hi=None, lane_out=None, s_out=None,
+                     d_out=None, stream=None):
+    return check(ctx, load().idm_lane_project(ctx, ctypes.byref(lanes), n_rows, n_cols, ptr(qx), ptr(qy), ptr(lane_lo),
+                                              ptr(lane_hi), ptr(lane_out), ptr(s_out), ptr(d_out),
+                                              stream_ptr(stream)))
+
+
+def idm_lane_unproject(ctx, lanes, n_rows, n_cols, s, lane_of_col, x_out, y_out, stream=None):
+    return check(ctx, load().idm_lane_unproject(ctx, ctypes.byref(lanes), n_rows, n_cols, ptr(s), ptr(lane_of_col),
+                                                ptr(x_out), ptr(y_out), stream_ptr(stream)))
+
+
+def idm_rollout_state(ctx, N, s_rows, row_a, row_b, dt, p_out, v_out, stream=None):
+    return check(ctx, load().idm_rollout_state(ctx, N, ptr(s_rows), row_a, row_b, dt, ptr(p_out), ptr(v_out),
+                                               stream_ptr(stream)))
+
+
+def idm_displacement(ctx, F, N, px, py, tx, ty, miss_m, ade=None, fde=None, sums=None, stream=None):
+    return check(ctx, load().idm_displacement(ctx, F, N, ptr(px), ptr(py), ptr(tx), ptr(ty), miss_m, ptr(ade),
+                                              ptr(fde), ptr(sums), stream_ptr(stream)))
+
 
 def idm_recon_prepare(ctx, N, n_obs, obs_off, obs_t, obs_p, dt, obs_k, K, p_init, v_init, want_k_max=True,
                       stream=None):

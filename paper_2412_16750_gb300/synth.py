@@ -255,3 +255,68 @@ def recon_observations(n, dur, rng, dense=None, gap_min=1.0, gap_mean_extra=1.0,
            - A2[idx] / w2[idx] * (np.cos(w2[idx] * t + f2[idx]) - np.cos(f2[idx])))
     pos = pos + rng.normal(0.0, noise, size=pos.shape)
     return off, t, f32(pos)
+
+
+# ---- scenes for training-free prediction with lane geometry ----------------
+#
+# Stand-in for the Waymo Open Motion validation set (Sec. V-C): scenarios of
+# U[2, 8] lane centre lines, each a circular arc (signed curvature of radius
+# U[60, 1000] m) or, with probability 0.3, a straight line, 300 m long,
+# starting at a point U[0, 200]^2 m with heading U[0, 2 pi), sampled every
+# 2 m.  Every lane carries U[1, 6] agents, the first at arc length U[40, 70] m,
+# each follower U[12, 25] m behind its predecessor; an agent moves along its
+# lane with s(t) = s0 + vm t + (A / w)(cos f - cos(w t + f)) (vm U[3, 15] m/s
+# per lane times U[0.9, 1.1] per agent, A U[0, 0.3 vm], period U[4, 12] s)
+# at a lateral offset d0 + 0.2 sin(w2 t + f2) (d0 N(0, 0.4^2) m) plus
+# position noise N(0, 0.1^2) m per coordinate.  Frames every 0.1 s: 11 of
+# history (1 s) and 80 of future (8 s).  Positions on a lane come from the
+# closed form of the arc, not from its polyline.
+
+def prediction_scenes(n_scen, rng, n_hist=11, n_fut=80, dt=0.1, spacing=2.0, lane_len=300.0):
+    F = n_hist + n_fut
+    t = np.arange(F) * dt
+    s_grid = np.arange(0.0, lane_len + 1e-9, spacing)
+    M = len(s_grid)
+    n_l = rng.integers(2, 9, size=n_scen)
+    L = int(n_l.sum())
+    scen_lane_off = np.zeros(n_scen + 1, np.int32)
+    scen_lane_off[1:] = np.cumsum(n_l)
+    x0, y0 = rng.uniform(0.0, 200.0, size=L), rng.uniform(0.0, 200.0, size=L)
+    h0 = rng.uniform(0.0, 2 * np.pi, size=L)
+    straight = rng.random(L) < 0.3
+    k = np.where(straight, 0.0, rng.choice([-1.0, 1.0], size=L) / rng.uniform(60.0, 1000.0, size=L))
+
+    def arc(l, s):
+        """Point and heading at arc length s (broadcast) of lanes l."""
+        kk, hh, xx, yy = k[l], h0[l], x0[l], y0[l]
+        ks = np.where(kk == 0.0, 1.0, kk)
+        h = hh + kk * s
+        xc = np.where(kk == 0.0, xx + s * np.cos(hh), xx + (np.sin(h) - np.sin(hh)) / ks)
+        yc = np.where(kk == 0.0, yy + s * np.sin(hh), yy - (np.cos(h) - np.cos(hh)) / ks)
+        return xc, yc, h
+
+    lanes = np.arange(L)
+    px, py, _ = arc(lanes[:, None], s_grid[None, :])
+    n_a = rng.integers(1, 7, size=L)
+    A_n = int(n_a.sum())
+    lane_of = np.repeat(lanes, n_a)
+    first = np.repeat(np.cumsum(n_a) - n_a, n_a)
+    rank = np.arange(A_n) - first                       # 0 = the lane's first agent
+    gaps = np.where(rank == 0, 0.0, rng.uniform(12.0, 25.0, size=A_n))
+    csum = np.cumsum(gaps)
+    s0 = np.repeat(rng.uniform(40.0, 70.0, size=L), n_a) - (csum - csum[first])
+    vm = np.repeat(rng.uniform(3.0, 15.0, size=L), n_a) * rng.uniform(0.9, 1.1, size=A_n)
+    A = rng.uniform(0.0, 0.3, size=A_n) * vm
+    w = 2 * np.pi / rng.uniform(4.0, 12.0, size=A_n)
+    f = rng.uniform(0, 2 * np.pi, size=A_n)
+    s = s0[None, :] + vm[None, :] * t[:, None] + (A / w)[None, :] * (np.cos(f)[None, :] - np.cos(w[None, :] * t[:, None] + f[None, :]))
+    d = rng.normal(0.0, 0.4, size=A_n)[None, :] + 0.2 * np.sin(
+        (2 * np.pi / rng.uniform(3.0, 9.0, size=A_n))[None, :] * t[:, None] + rng.uniform(0, 6.3, size=A_n)[None, :])
+    cx, cy, h = arc(lane_of[None, :], s)
+    x = cx - d * np.sin(h) + rng.normal(0.0, 0.1, size=(F, A_n))
+    y = cy + d * np.cos(h) + rng.normal(0.0, 0.1, size=(F, A_n))
+    scen_of = np.repeat(np.repeat(np.arange(n_scen), n_l), n_a)
+    pt_off = (np.arange(L + 1) * M).astype(np.int32)
+    return dict(pt_off=pt_off, px=f32(px.ravel()), py=f32(py.ravel()), x=f32(x), y=f32(y),
+                lane_true=lane_of.astype(np.int32), lane_lo=scen_lane_off[scen_of], lane_hi=scen_lane_off[scen_of + 1],
+                n_hist=n_hist, n_fut=n_fut, dt=float(np.float32(dt)), n_lanes=L)
