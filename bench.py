@@ -579,10 +579,10 @@ def batched(a, dev):
 
 
 # Algorithmic bytes per trajectory-step of one fit iteration of the
-# reconstruction mode: forward reads dp, dv and the observation row (8 B) and
-# writes the tape (8 B); the adjoint reads the tape, dp, dv and four Adam
-# moments (32 B) and writes dp, dv and the moments (24 B).
-RECON_BYTES_PER_STEP = 16 + 8 + 32 + 24
+# reconstruction mode: forward reads dp, dv and the observation row (16 B)
+# and writes the tape (32 B); the adjoint reads the tape, dp, dv and four Adam
+# moments (56 B) and writes dp, dv and the moments (24 B).
+RECON_BYTES_PER_STEP = 16 + 32 + 56 + 24
 
 
 def reconstruction(a, dev):

@@ -12,12 +12,14 @@
 // only the shared-memory column it copied itself, so its own
 // cp.async.wait_group is the only synchronisation.
 //
-// Forward: writes the tape (the speed of step k and the loss seed of step
-// k+1) and the loss, or the requested P/V/A, or the metric sums.  Adjoint:
-// walks the tape backwards.  The model partials of step k depend only on the
-// tape, dp_k and dv_k, so its only serial chain is the adjoint recursion (two
-// FMAs per step) and the rest overlaps across steps.  The fit runs every
-// iteration of its trajectory inside one launch (trajectories are
+// Forward: integrates the state and, while its serial chain (one model
+// evaluation per step) leaves most issue slots idle, evaluates the adjoint's
+// partials of every step (they depend only on the step's speed, dp_k and dv_k)
+// and writes them with the loss seed of step k+1 as the tape; or writes the
+// requested P/V/A, or the metric sums.  Adjoint: walks the tape backwards; its
+// only serial chain is the adjoint recursion (two FMAs per step), the rest
+// (gradient sums, Adam on dp_k and dv_k) is independent across steps.  The fit
+// runs every iteration of its trajectory inside one launch (trajectories are
 // independent), with Adam for dp_k and dv_k fused into the adjoint and Adam
 // for the parameters at its end.
 #include <cuda_runtime.h>
@@ -37,9 +39,11 @@ namespace idm {
 namespace rec {
 
 constexpr int U = 8;                       // steps per staged chunk
-constexpr int S = 4;                       // chunks in flight
-constexpr int NA = 8;                      // staged arrays per step (the fit's adjoint)
-constexpr int STAGE = NA * U * 32;         // floats per chunk
+constexpr int S = 3;                       // chunks in flight
+// A stage holds, per step and lane: three float4 slots (forward: dp, dv and
+// the observation row; adjoint: the two tape halves and the Adam moments or
+// the delta factor) and one float2 slot (adjoint: dp, dv).
+constexpr int STAGE = (3 * 4 + 2) * U * 32;   // floats per chunk
 constexpr int SMEM = (int)sizeof(float) * S * STAGE;
 
 enum Mode { FWD_OUT = 0, LOSS_GRAD = 1, FIT = 2, METRICS = 3 };
@@ -55,8 +59,9 @@ struct Args {
     const int32_t *oyc;              // [k_max][ld]: 8 j + min(count, 7) of that observation, -1 = none
     const int32_t *obs_off, *obs_k;
     const float *obs_p;
-    float *tv, *ts;                  // tape: speed of step k, loss seed of step k+1
-    float *mom[4];                   // Adam moments of dp, dv: m_dp, v_dp, m_dv, v_dv
+    float4 *tape_a, *tape_b;         // tape [k_max][ld]: (Av, Adp, Adv, w0n), (w0n v, fa, frd, seed of step k+1)
+    float *tape_d;                   // [k_max][ld]: frdl (delta gradient only)
+    float4 *mom;                     // [k_max][ld]: Adam moments (m_dp, v_dp, m_dv, v_dv)
     float *thm, *thv;                // Adam moments of the parameters, [5][N]
     float *P, *V, *A;
     double *loss;                    // loss_out (LOSS_GRAD) or loss_hist (FIT)
@@ -232,9 +237,21 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ float *slot(float *sm, int c, int arr, int u, int lane)
+__device__ __forceinline__ void cp16(void *dst, const void *src)
 {
-    return sm + ((size_t)((c % S) * NA + arr) * U + u) * 32 + lane;
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+
+// Slot of (chunk c, step u, lane) in float4 region r (0..2) or in the float2
+// region of the chunk's stage.
+__device__ __forceinline__ float4 *slot4(float *sm, int c, int r, int u, int lane)
+{
+    return reinterpret_cast<float4 *>(sm + (size_t)(c % S) * STAGE) + ((size_t)r * U + u) * 32 + lane;
+}
+__device__ __forceinline__ float2 *slot2(float *sm, int c, int u, int lane)
+{
+    return reinterpret_cast<float2 *>(sm + (size_t)(c % S) * STAGE + 3 * 4 * U * 32) + (size_t)u * 32 + lane;
 }
 
 __device__ __forceinline__ double warp_sum(double x)
@@ -250,11 +267,12 @@ struct MetricAcc {
 };
 
 // Forward over the Ki steps of trajectory i (Kw = the warp's largest Ki).
-// Returns the loss sum (LOSS_GRAD, FIT).
-template <int MODE, bool D4>
-__device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, bool act, int Ki, int Kw, float *sm, int lane,
-                            MetricAcc &ma, float len_inv)
+// Returns the loss sum (LOSS_GRAD, FIT), which also write the tape.
+template <int MODE, bool D4, bool WD>
+__device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, bool act, int Ki, int Kw, float *sm,
+                                            int lane, MetricAcc &ma, float len_inv)
 {
+    constexpr bool TAPE = MODE == LOSS_GRAD || MODE == FIT;
     const int nch = (Kw + U - 1) / U;
     const size_t ld = (size_t)a.ld;
     auto issue = [&](int c) {
@@ -264,11 +282,12 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
                 const int k = c * U + u;
                 if (k < Ki) {
                     const size_t o = (size_t)k * ld + i;
-                    cp4(slot(sm, c, 0, u, lane), a.dp + o);
-                    cp4(slot(sm, c, 1, u, lane), a.dv + o);
+                    float *d = reinterpret_cast<float *>(slot4(sm, c, 0, u, lane));
+                    cp4(d, a.dp + o);
+                    cp4(d + 1, a.dv + o);
                     if (MODE != FWD_OUT) {
-                        cp4(slot(sm, c, 2, u, lane), a.oyy + o);
-                        cp4(slot(sm, c, 3, u, lane), a.oyc + o);
+                        cp4(d + 2, a.oyy + o);
+                        cp4(d + 3, a.oyc + o);
                     }
                 }
             }
@@ -294,11 +313,15 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
         for (int u = 0; u < U; ++u) {
             const int k = c * U + u;
             const bool valid = k < Ki;
-            const float dp = *slot(sm, c, 0, u, lane), dv = *slot(sm, c, 1, u, lane);
+            const float4 row = *slot4(sm, c, 0, u, lane);     // dp, dv, observed position, observation code
+            const float dp = row.x, dv = row.y;
             const float gap_inv = rcp_approx(fmaxf(dp, IDM_GAP_FLOOR));
             const float uu = fmaf(dv, q.c, q.T);
             float as;
             const float vn = speed_step<D4>(v, gap_inv, uu, q, dt, inv_dt, a_min, as);
+            // the adjoint's partials at this step, beside the serial chain
+            Jac1 J;
+            if (TAPE) J = jac1<D4, WD>(v, dp, dv, q, inv_dt, a_min);
             float phn = ph, pln = pl;
             euler_pos(phn, pln, v, dt);
             const float v_k = v;
@@ -315,9 +338,9 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
             } else {
                 // observations at step k+1: the staged first one, then any
                 // further ones from the CSR
-                const int code = valid ? __float_as_int(*slot(sm, c, 3, u, lane)) : -1;
+                const int code = valid ? __float_as_int(row.w) : -1;
                 const bool has = code >= 0;
-                float r = (ph - *slot(sm, c, 2, u, lane)) + pl;
+                float r = (ph - row.z) + pl;
                 float seed = has ? sgn(r) : 0.0f;
                 Lc += has ? fabsf(r) : 0.0f;
                 if (MODE == METRICS && has) {
@@ -337,9 +360,10 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
                         }
                     }
                 }
-                if ((MODE == LOSS_GRAD || MODE == FIT) && valid) {
-                    a.tv[o] = v_k;
-                    a.ts[o] = seed;
+                if (TAPE && valid) {
+                    a.tape_a[o] = make_float4(J.Av, J.Adp, J.Adv, J.w0n);
+                    a.tape_b[o] = make_float4(J.w0n * v_k, J.fa, J.frd, seed);
+                    if (WD) a.tape_d[o] = J.frdl;
                 }
                 if (MODE == METRICS && valid) {
                     const double aa = fabs((double)as);
@@ -379,13 +403,14 @@ __device__ __forceinline__ float adam1(float x, float g, float &m, float &w, flo
     return fmaf(-a1 * m, rcp_approx(fmaf(sw, isb2, 1e-8f)), x);
 }
 
-// Reverse pass over the Ki steps of trajectory i.  lambda_p and lambda_v are
-// the adjoints of the position and speed; the seed of step k+1 enters
-// lambda_p before step k is reversed.  Returns the parameter sums A[6]
-// (gradients assembled by the caller), lambda_p(0) and lambda_v(0).
-template <int MODE, bool D4, bool WD>
-__device__ __forceinline__ void adj_phase(const Args &a, const Par &q, int i, int Ki, int Kw, float *sm, int lane, float a1,
-                          float isb2, float (&Acc)[6], float &lp_out, float &lv_out)
+// Reverse pass over the Ki steps of trajectory i on the tape of the forward.
+// lambda_p and lambda_v are the adjoints of the position and speed; the seed
+// of step k+1 enters lambda_p before step k is reversed.  Returns the
+// parameter sums A[6] (gradients assembled by the caller), lambda_p(0) and
+// lambda_v(0).
+template <int MODE, bool WD>
+__device__ __forceinline__ void adj_phase(const Args &a, int i, int Ki, int Kw, float *sm, int lane, float a1,
+                                          float isb2, float (&Acc)[6], float &lp_out, float &lv_out)
 {
     const int nch = (Kw + U - 1) / U;
     const size_t ld = (size_t)a.ld;
@@ -396,14 +421,13 @@ __device__ __forceinline__ void adj_phase(const Args &a, const Par &q, int i, in
                 const int k = Kw - 1 - (c * U + u);
                 if (k >= 0 && k < Ki) {
                     const size_t o = (size_t)k * ld + i;
-                    cp4(slot(sm, c, 0, u, lane), a.tv + o);
-                    cp4(slot(sm, c, 1, u, lane), a.ts + o);
-                    cp4(slot(sm, c, 2, u, lane), a.dp + o);
-                    cp4(slot(sm, c, 3, u, lane), a.dv + o);
-                    if (MODE == FIT) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) cp4(slot(sm, c, 4 + m, u, lane), a.mom[m] + o);
-                    }
+                    cp16(slot4(sm, c, 0, u, lane), a.tape_a + o);
+                    cp16(slot4(sm, c, 1, u, lane), a.tape_b + o);
+                    if (MODE == FIT) cp16(slot4(sm, c, 2, u, lane), a.mom + o);
+                    if (WD) cp4(reinterpret_cast<float *>(slot4(sm, c, 2, u, lane)), a.tape_d + o);
+                    float *d = reinterpret_cast<float *>(slot2(sm, c, u, lane));
+                    cp4(d, a.dp + o);
+                    cp4(d + 1, a.dv + o);
                 }
             }
         }
@@ -412,41 +436,32 @@ __device__ __forceinline__ void adj_phase(const Args &a, const Par &q, int i, in
 #pragma unroll
     for (int c = 0; c < S - 1; ++c) issue(c);
 
-    const float dt = a.dt, inv_dt = a.inv_dt, a_min = a.a_min;
+    const float dt = a.dt;
     float lp = 0.0f, lv = 0.0f;
 #pragma unroll
     for (int r = 0; r < 6; ++r) Acc[r] = 0.0f;
     for (int c = 0; c < nch; ++c) {
         issue(c + S - 1);
         cp_wait<S - 1>();
-        // The partials of the U steps are independent of the adjoint state:
-        // all of them first (they overlap), then the serial lambda_p,
-        // lambda_v and sums, updated by selects for the lane's valid steps
-        // (a lane past its horizon computes on stale staged values).
-        Jac1 J[U];
-        float vk[U], dpk[U], dvk[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            vk[u] = *slot(sm, c, 0, u, lane);
-            dpk[u] = *slot(sm, c, 2, u, lane);
-            dvk[u] = *slot(sm, c, 3, u, lane);
-            J[u] = jac1<D4, WD>(vk[u], dpk[u], dvk[u], q, inv_dt, a_min);
-        }
+        // Branch-free: a lane past its horizon reads stale staged values and
+        // keeps its state (selects, predicated stores).
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = Kw - 1 - (c * U + u);
             const bool valid = k >= 0 && k < Ki;
-            const float lpn = lp + *slot(sm, c, 1, u, lane);             // lambda_p(k+1)
-            const float mu = dt * lv;                                    // dt lambda_v(k+1)
-            const float lvn = fmaf(mu, J[u].Av, fmaf(dt, lpn, lv));      // lambda_v(k)
-            const float gdp = mu * J[u].Adp, gdv = mu * J[u].Adv;
-            const float wv = J[u].w0n * vk[u];
-            Acc[0] = valid ? fmaf(mu, J[u].w0n, Acc[0]) : Acc[0];
-            Acc[1] = valid ? fmaf(mu, wv, Acc[1]) : Acc[1];
-            Acc[2] = valid ? fmaf(mu, wv * dvk[u], Acc[2]) : Acc[2];
-            Acc[3] = valid ? fmaf(mu, J[u].fa, Acc[3]) : Acc[3];
-            Acc[4] = valid ? fmaf(mu, J[u].frd, Acc[4]) : Acc[4];
-            if (WD) Acc[5] = valid ? fmaf(mu, J[u].frdl, Acc[5]) : Acc[5];
+            const float4 ta = *slot4(sm, c, 0, u, lane);     // Av, Adp, Adv, w0n
+            const float4 tb = *slot4(sm, c, 1, u, lane);     // w0n v, fa, frd, seed of step k+1
+            const float2 pv = *slot2(sm, c, u, lane);        // dp, dv
+            const float lpn = lp + tb.w;                     // lambda_p(k+1)
+            const float mu = dt * lv;                        // dt lambda_v(k+1)
+            const float lvn = fmaf(mu, ta.x, fmaf(dt, lpn, lv));   // lambda_v(k)
+            const float gdp = mu * ta.y, gdv = mu * ta.z;
+            Acc[0] = valid ? fmaf(mu, ta.w, Acc[0]) : Acc[0];
+            Acc[1] = valid ? fmaf(mu, tb.x, Acc[1]) : Acc[1];
+            Acc[2] = valid ? fmaf(mu, tb.x * pv.y, Acc[2]) : Acc[2];
+            Acc[3] = valid ? fmaf(mu, tb.y, Acc[3]) : Acc[3];
+            Acc[4] = valid ? fmaf(mu, tb.z, Acc[4]) : Acc[4];
+            if (WD) Acc[5] = valid ? fmaf(mu, slot4(sm, c, 2, u, lane)->x, Acc[5]) : Acc[5];
             lp = valid ? lpn : lp;
             lv = valid ? lvn : lv;
             const size_t o = (size_t)k * ld + i;
@@ -454,17 +469,13 @@ __device__ __forceinline__ void adj_phase(const Args &a, const Par &q, int i, in
                 if (valid && a.g_dp) a.g_dp[o] = gdp;
                 if (valid && a.g_dv) a.g_dv[o] = gdv;
             } else if (MODE == FIT) {
-                float m0 = *slot(sm, c, 4, u, lane), w0 = *slot(sm, c, 5, u, lane);
-                float m1 = *slot(sm, c, 6, u, lane), w1 = *slot(sm, c, 7, u, lane);
-                const float dpn = adam1(dpk[u], gdp, m0, w0, a1, isb2);
-                const float dvn = adam1(dvk[u], gdv, m1, w1, a1, isb2);
+                float4 m = *slot4(sm, c, 2, u, lane);
+                const float dpn = adam1(pv.x, gdp, m.x, m.y, a1, isb2);
+                const float dvn = adam1(pv.y, gdv, m.z, m.w, a1, isb2);
                 if (valid) {
                     a.dp[o] = dpn;
                     a.dv[o] = dvn;
-                    a.mom[0][o] = m0;
-                    a.mom[1][o] = w0;
-                    a.mom[2][o] = m1;
-                    a.mom[3][o] = w1;
+                    a.mom[o] = m;
                 }
             }
         }
@@ -521,7 +532,9 @@ __device__ __forceinline__ void run_single(const Args &a, int i, bool act, int K
         }
     }
     const Par q = act ? load_par(a, i) : make_par(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 4.0f);
-    const double L = fwd_phase<MODE, D4>(a, q, i, act, Ki, Kw, sm, lane, ma, len_inv);
+    const bool wd = MODE == LOSS_GRAD && a.g6[5] != nullptr;
+    const double L = wd ? fwd_phase<MODE, D4, true>(a, q, i, act, Ki, Kw, sm, lane, ma, len_inv)
+                        : fwd_phase<MODE, D4, false>(a, q, i, act, Ki, Kw, sm, lane, ma, len_inv);
     if (MODE == METRICS) {
         if (len_inv == 0.0f) {
             ma.pos = 0.0;
@@ -540,11 +553,10 @@ __device__ __forceinline__ void run_single(const Args &a, int i, bool act, int K
         if (lane == 0 && a.loss) atomicAdd(a.loss, s);
         __threadfence_block();  // the tape written above is read back by this thread's copies
         float A[6], lp, lv, gr[6];
-        const bool wd = a.g6[5] != nullptr;
         if (wd)
-            adj_phase<LOSS_GRAD, D4, true>(a, q, i, Ki, Kw, sm, lane, 0.0f, 0.0f, A, lp, lv);
+            adj_phase<LOSS_GRAD, true>(a, i, Ki, Kw, sm, lane, 0.0f, 0.0f, A, lp, lv);
         else
-            adj_phase<LOSS_GRAD, D4, false>(a, q, i, Ki, Kw, sm, lane, 0.0f, 0.0f, A, lp, lv);
+            adj_phase<LOSS_GRAD, false>(a, i, Ki, Kw, sm, lane, 0.0f, 0.0f, A, lp, lv);
         if (!act) return;
         param_grads(q, A, gr);
         bool bad = !isfinite(lp) || !isfinite(lv);
@@ -590,7 +602,7 @@ __device__ __forceinline__ void fit_warp(const Args &a, int i, bool act, int Ki,
     bool bad = false;
     MetricAcc ma;
     for (int it = 0; it < a.n_iter; ++it) {
-        const double L = fwd_phase<FIT, D4>(a, q, i, act, Ki, Kw, sm, lane, ma, 0.0f);
+        const double L = fwd_phase<FIT, D4, false>(a, q, i, act, Ki, Kw, sm, lane, ma, 0.0f);
         const double s = warp_sum(L);
         if (lane == 0 && a.loss) atomicAdd(a.loss + it, s);
         __threadfence_block();  // tape and updated dp, dv are read back by this thread's copies
@@ -599,7 +611,7 @@ __device__ __forceinline__ void fit_warp(const Args &a, int i, bool act, int Ki,
         const float bc1 = 1.0f - __powf(0.9f, (float)t), bc2 = 1.0f - __powf(0.999f, (float)t);
         const float a1 = lr / bc1, isb2 = 1.0f / sqrtf(bc2);
         float A[6], lp, lv, gr[6];
-        adj_phase<FIT, D4, false>(a, q, i, Ki, Kw, sm, lane, a1, isb2, A, lp, lv);
+        adj_phase<FIT, false>(a, i, Ki, Kw, sm, lane, a1, isb2, A, lp, lv);
         __threadfence_block();
         if (act) {
             param_grads(q, A, gr);
@@ -812,9 +824,10 @@ int ensure_tape(idm_ctx *c, const idm_recon_t *r, rec::Args &a)
 {
     const size_t rows = (size_t)r->k_max * r->ld;
     int rc;
-    if ((rc = ensure(c, c->rec_tape, sizeof(float) * 2 * rows, "adjoint tape"))) return rc;
-    a.tv = (float *)c->rec_tape.p;
-    a.ts = a.tv + rows;
+    if ((rc = ensure(c, c->rec_tape, sizeof(float) * 9 * rows, "adjoint tape"))) return rc;
+    a.tape_a = (float4 *)c->rec_tape.p;
+    a.tape_b = a.tape_a + rows;
+    a.tape_d = (float *)(a.tape_b + rows);
     return IDM_OK;
 }
 
@@ -932,7 +945,7 @@ extern "C" int idm_recon_fit(idm_ctx_t *c, const idm_recon_t *r, idm_params_t *p
         return rc;
     IDM_CK(cudaMemsetAsync(c->rec_mom.p, 0, sizeof(float) * 4 * rows, st));
     IDM_CK(cudaMemsetAsync(c->rec_thm.p, 0, sizeof(float) * 10 * std::max<size_t>(N, 1), st));
-    for (int m = 0; m < 4; ++m) a.mom[m] = (float *)c->rec_mom.p + m * rows;
+    a.mom = (float4 *)c->rec_mom.p;
     a.thm = (float *)c->rec_thm.p;
     a.thv = a.thm + 5 * N;
     a.loss = loss_hist;
