@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "../../include/idm.h"
 #include "../../include/idm_recon.h"
@@ -303,12 +304,13 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
     float Ls = 0.0f, Lcomp = 0.0f;   // loss: per-thread Kahan sum of the chunk sums
     const int j_end =
         (MODE == LOSS_GRAD || MODE == FIT || MODE == METRICS) && Ki > 0 ? min(a.obs_off[i + 1], a.n_obs) : 0;
-    for (int c = 0; c < nch; ++c) {
-        issue(c + S - 1);
-        cp_wait<S - 1>();
+    // One chunk of U steps.  MULTI: some step of the chunk has several
+    // observations (rare); without it the chunk is one branch-free block, so
+    // the compiler can overlap a step's partials, position and observation
+    // work with the next step's serial chain.
+    auto chunk = [&](int c, auto multi_tag) {
+        constexpr bool MULTI = decltype(multi_tag)::value;
         float Lc = 0.0f;
-        // Branch-free over the chunk: a lane past its horizon computes on
-        // stale staged values and keeps its state (selects, predicated stores).
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = c * U + u;
@@ -336,8 +338,8 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
                     if (a.A) a.A[o] = as;
                 }
             } else {
-                // observations at step k+1: the staged first one, then any
-                // further ones from the CSR
+                // observations at step k+1: the staged first one, then (MULTI)
+                // any further ones from the CSR
                 const int code = valid ? __float_as_int(row.w) : -1;
                 const bool has = code >= 0;
                 float r = (ph - row.z) + pl;
@@ -347,7 +349,7 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
                     ma.pos += fabs((double)r) * len_inv;
                     ++ma.n_pos;
                 }
-                if (has && (code & 7) > 1) {
+                if (MULTI && has && (code & 7) > 1) {
                     const int cnt = code & 7, j0 = code >> 3;
                     for (int j = j0 + 1; j < j_end; ++j) {
                         if (cnt < 7 ? j >= j0 + cnt : a.obs_k[j] != k + 1) break;
@@ -374,6 +376,22 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
                 }
             }
         }
+        return Lc;
+    };
+    for (int c = 0; c < nch; ++c) {
+        issue(c + S - 1);
+        cp_wait<S - 1>();
+        // Branch-free over the chunk: a lane past its horizon computes on
+        // stale staged values and keeps its state (selects, predicated stores).
+        bool multi = false;
+        if (MODE != FWD_OUT) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int code = __float_as_int(slot4(sm, c, 0, u, lane)->w);
+                multi |= (c * U + u < Ki) && code >= 0 && (code & 7) > 1;
+            }
+        }
+        const float Lc = __any_sync(FULL, multi) ? chunk(c, std::true_type{}) : chunk(c, std::false_type{});
         kahan(Ls, Lcomp, Lc);
     }
     const double L = (double)Ls - (double)Lcomp;

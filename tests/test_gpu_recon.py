@@ -353,3 +353,39 @@ def test_full_size_reconstruction_workload(api):
     grad_close(gdp_g.double().cpu().numpy()[:, ok], gdp[:, ok], what="dp")
     grad_close(gdv_g.double().cpu().numpy()[:, ok], gdv[:, ok], what="dv")
     assert api.default_context().check_status() == 0
+
+
+def test_padded_row_stride(api):
+    """Per-step arrays with a row stride larger than the trajectory count
+    (ld > N): the same loss and gradients as the packed layout."""
+    from paper_2412_16750_gb300 import lib
+    case = make_case(51, 45, (3.0, 25.0), 0.1, 0.1, 1.0)
+    obs_k, K, p0, v0 = oracle_setup(case)
+    rng = np.random.default_rng(510)
+    k_max, n = int(K.max()), 45
+    dp, dv = leader_vars(rng, k_max, n)
+    th = param_vars(rng, n)
+    case, obs_k = drop_ambiguous(case, obs_k, K, th, dp, dv, p0, v0)
+    K = R.horizons(case["off"], obs_k)
+    dp, dv = dp[:int(K.max())], dv[:int(K.max())]
+    g = GpuCase(api, case, p0, v0).r
+    loss_a, gth_a, gdp_a, gdv_a, _, _ = g.loss_grad(cuda(th), cuda(dp), cuda(dv))
+    ld = 77
+    dp_p = np.full((g.k_max, ld), np.nan, np.float32)
+    dv_p = np.full((g.k_max, ld), np.nan, np.float32)
+    dp_p[:, :n], dv_p[:, :n] = dp, dv
+    rec = g.c()
+    rec.ld = ld
+    loss = torch.zeros((), device="cuda", dtype=torch.float64)
+    gth = torch.empty((6, n), device="cuda")
+    gdp = torch.full((g.k_max, ld), 7.0, device="cuda")
+    gdv = torch.full((g.k_max, ld), 7.0, device="cuda")
+    dpt, dvt, tht = cuda(dp_p), cuda(dv_p), cuda(th)
+    lib.idm_recon_loss_grad(g.ctx.handle, rec, lib.make_params(tht), dpt, dvt, loss, lib.make_params(gth), gdp, gdv)
+    torch.cuda.synchronize()
+    assert loss.item() == loss_a.item()
+    np.testing.assert_array_equal(gth.cpu().numpy(), gth_a.cpu().numpy())
+    np.testing.assert_array_equal(gdp.cpu().numpy()[:, :n], gdp_a.cpu().numpy())
+    np.testing.assert_array_equal(gdv.cpu().numpy()[:, :n], gdv_a.cpu().numpy())
+    assert np.all(gdp.cpu().numpy()[:, n:] == 7.0)          # the padding is not written
+    assert api.default_context().check_status() == 0
