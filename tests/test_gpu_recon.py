@@ -383,7 +383,7 @@ def test_padded_row_stride(api):
     dpt, dvt, tht = cuda(dp_p), cuda(dv_p), cuda(th)
     lib.idm_recon_loss_grad(g.ctx.handle, rec, lib.make_params(tht), dpt, dvt, loss, lib.make_params(gth), gdp, gdv)
     torch.cuda.synchronize()
-    assert loss.item() == loss_a.item()
+    assert abs(loss.item() - loss_a.item()) <= 1e-12 * abs(loss_a.item())   # warp sums added in any order
     np.testing.assert_array_equal(gth.cpu().numpy(), gth_a.cpu().numpy())
     np.testing.assert_array_equal(gdp.cpu().numpy()[:, :n], gdp_a.cpu().numpy())
     np.testing.assert_array_equal(gdv.cpu().numpy()[:, :n], gdv_a.cpu().numpy())
