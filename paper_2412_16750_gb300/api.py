@@ -383,9 +383,12 @@ RECON_DV0 = 0.0
 class Recon:
     """Observed trajectories (CSR over trajectories) prepared for the
     reconstruction mode: nearest steps, horizons K and initial states come
-    from idm_recon_prepare.  Per-step tensors are time-major (k_max, N)."""
+    from idm_recon_prepare.  Per-step arrays are time-major with k_max rows
+    and a row stride ld = N rounded up to 32 (so that rows can be staged
+    with 16-byte copies); the methods accept (k_max, N) or (k_max, ld)
+    tensors and return (.., N) views."""
 
-    def __init__(self, obs_off, obs_t, obs_p, dt, a_min=-10.0, ctx=None):
+    def __init__(self, obs_off, obs_t, obs_p, dt, a_min=-10.0, ctx=None, ld=None):
         self.ctx = ctx or default_context()
         self.obs_off = obs_off.to(device="cuda", dtype=torch.int32).contiguous()
         self.obs_t = _f32(obs_t)
@@ -400,7 +403,8 @@ class Recon:
         km = lib.idm_recon_prepare(self.ctx.handle, self.N, self.n_obs, self.obs_off, self.obs_t, self.obs_p,
                                    self.dt, self.obs_k, self.K, self.p_init, self.v_init, True, _stream())
         self.k_max = max(int(km), 1)
-        self.ld = max(self.N, 1)
+        self.ld = ld if ld is not None else max(32, -(-self.N // 32) * 32)
+        assert self.ld >= self.N
 
     def c(self):
         return lib.idm_recon_t(self.N, self.k_max, self.ld, self.n_obs, lib.ptr(self.obs_off).value,
@@ -408,8 +412,18 @@ class Recon:
                                lib.ptr(self.K).value, lib.ptr(self.p_init).value, lib.ptr(self.v_init).value,
                                self.dt, self.a_min)
 
+    def _rows(self, x):
+        """A (k_max, N) or (k_max, ld) per-step tensor as (k_max, ld) float32 contiguous."""
+        x = _f32(x)
+        assert x.shape[0] == self.k_max, "per-step arrays need k_max rows"
+        if x.shape[1] == self.ld:
+            return x
+        y = torch.zeros((self.k_max, self.ld), device="cuda", dtype=torch.float32)
+        y[:, :x.shape[1]] = x
+        return y
+
     def init_vars(self):
-        """(theta (6, N), dp, dv (k_max, N)) at the paper's starting point."""
+        """(theta (6, N), dp, dv (k_max, ld)) at the paper's starting point."""
         theta = torch.tensor(RECON_INIT, dtype=torch.float32, device="cuda")[:, None].repeat(1, self.N).contiguous()
         dp = torch.full((self.k_max, self.ld), RECON_DP0, device="cuda", dtype=torch.float32)
         dv = torch.full((self.k_max, self.ld), RECON_DV0, device="cuda", dtype=torch.float32)
@@ -417,39 +431,47 @@ class Recon:
 
     def forward(self, theta, dp, dv):
         """(P, V (k_max+1, N), A (k_max, N))."""
-        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        theta, dp, dv = _f32(theta), self._rows(dp), self._rows(dv)
         P = torch.empty((self.k_max + 1, self.ld), device="cuda", dtype=torch.float32)
         V = torch.empty_like(P)
         A = torch.empty((self.k_max, self.ld), device="cuda", dtype=torch.float32)
         lib.idm_recon_forward(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, P, V, A, _stream())
-        return P, V, A
+        n = self.N
+        return P[:, :n], V[:, :n], A[:, :n]
 
     def loss_grad(self, theta, dp, dv):
         """(loss float64 0-d, g_theta (6, N), g_dp, g_dv (k_max, N), g_p_init, g_v_init)."""
-        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        theta, dp, dv = _f32(theta), self._rows(dp), self._rows(dv)
         loss = torch.zeros((), device="cuda", dtype=torch.float64)
-        g = torch.empty((6, self.ld), device="cuda", dtype=torch.float32)
+        g = torch.empty((6, max(self.N, 1)), device="cuda", dtype=torch.float32)
         gdp = torch.empty((self.k_max, self.ld), device="cuda", dtype=torch.float32)
         gdv = torch.empty_like(gdp)
-        gp = torch.empty(self.ld, device="cuda", dtype=torch.float32)
-        gv = torch.empty(self.ld, device="cuda", dtype=torch.float32)
+        gp = torch.empty(max(self.N, 1), device="cuda", dtype=torch.float32)
+        gv = torch.empty(max(self.N, 1), device="cuda", dtype=torch.float32)
         lib.idm_recon_loss_grad(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, loss,
                                 lib.make_params(g), gdp, gdv, gp, gv, _stream())
-        return loss, g, gdp, gdv, gp, gv
+        n = self.N
+        return loss, g[:, :n], gdp[:, :n], gdv[:, :n], gp[:n], gv[:n]
 
     def fit(self, theta, dp, dv, n_iter=500, lr0=0.1, lr1=0.01, box_lo=RECON_BOX_LO, box_hi=RECON_BOX_HI):
-        """Adam fit in place on theta (6, N), dp, dv (k_max, N), float32 CUDA
-        contiguous; returns the float64 loss history (n_iter,)."""
+        """Adam fit in place on theta (6, N) and dp, dv ((k_max, N) or
+        (k_max, ld)), float32 CUDA contiguous; returns the float64 loss
+        history (n_iter,)."""
         for t in (theta, dp, dv):
             assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        dpw, dvw = self._rows(dp), self._rows(dv)
         hist = torch.zeros(max(n_iter, 1), device="cuda", dtype=torch.float64)
-        lib.idm_recon_fit(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, n_iter, lr0, lr1, box_lo,
+        lib.idm_recon_fit(self.ctx.handle, self.c(), lib.make_params(theta), dpw, dvw, n_iter, lr0, lr1, box_lo,
                           box_hi, hist, _stream())
+        if dpw.data_ptr() != dp.data_ptr():
+            dp.copy_(dpw[:, :dp.shape[1]])
+        if dvw.data_ptr() != dv.data_ptr():
+            dv.copy_(dvw[:, :dv.shape[1]])
         return hist[:n_iter]
 
     def metrics(self, theta, dp, dv):
         """float64 (4,): Pos. (fraction), mean |a*|, std |a*|, Imp. (fraction)."""
-        theta, dp, dv = _f32(theta), _f32(dp), _f32(dv)
+        theta, dp, dv = _f32(theta), self._rows(dp), self._rows(dv)
         out = torch.zeros(4, device="cuda", dtype=torch.float64)
         lib.idm_recon_metrics(self.ctx.handle, self.c(), lib.make_params(theta), dp, dv, out, _stream())
         return out

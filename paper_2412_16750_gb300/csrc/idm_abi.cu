@@ -414,7 +414,7 @@ int idm_ctx_destroy(idm_ctx_t *c)
                    &c->loss_part, &c->loss_tmp,  &c->adam_m,       &c->adam_v,       &c->lay_counts,
                    &c->lay_cursor, &c->eval_part, &c->sub_ckpt,    &c->scen_tab,     &c->scen_seg_off,
                    &c->scen_seg_idx, &c->lane_off_dev, &c->rec_oyy, &c->rec_oyc,    &c->rec_tape,
-                   &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax};
+                   &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax,     &c->rec_multi};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -48,7 +48,7 @@ struct idm_ctx {
     int wpb = 8;
     idm::abi::Buf seg, ctl, status, g0, ckpt, loss_part, loss_tmp, adam_m, adam_v, lay_counts, lay_cursor, eval_part, sub_ckpt;
     idm::abi::Buf scen_tab, scen_seg_off, scen_seg_idx, lane_off_dev;  // batched scenarios
-    idm::abi::Buf rec_oyy, rec_oyc, rec_tape, rec_mom, rec_thm, rec_acc, rec_kmax;  // reconstruction mode
+    idm::abi::Buf rec_oyy, rec_oyc, rec_multi, rec_tape, rec_mom, rec_thm, rec_acc, rec_kmax;  // reconstruction mode
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t fit_exec = nullptr;
     unsigned char fit_key[640] = {0};  // arguments the cached fit graph was captured with

@@ -58,6 +58,8 @@ struct Args {
     float *dp, *dv;
     const float *oyy;                // [k_max][ld]: first observed position of step k+1
     const int32_t *oyc;              // [k_max][ld]: 8 j + min(count, 7) of that observation, -1 = none
+    const int32_t *multi;            // [N]: 1 if some step of the trajectory has several observations
+    int wide_ok;                     // dp, dv and the observation rows allow 16-byte row copies (ld % 4 == 0, aligned)
     const int32_t *obs_off, *obs_k;
     const float *obs_p;
     float4 *tape_a, *tape_b;         // tape [k_max][ld]: (Av, Adp, Adv, w0n), (w0n v, fa, frd, seed of step k+1)
@@ -244,15 +246,47 @@ __device__ __forceinline__ void cp16(void *dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
 }
 
-// Slot of (chunk c, step u, lane) in float4 region r (0..2) or in the float2
-// region of the chunk's stage.
+// Slot of (chunk c, step u, lane) in float4 region r (0..2) of the chunk's
+// stage, and the row-major float rows of the stage: row (r, u) holds the 32
+// columns of array r at step u.  Float region 0 overlays float4 region 0
+// (forward: dp, dv, observed position, observation code); float region 1
+// lies after the three float4 regions (adjoint: dp, dv).
 __device__ __forceinline__ float4 *slot4(float *sm, int c, int r, int u, int lane)
 {
     return reinterpret_cast<float4 *>(sm + (size_t)(c % S) * STAGE) + ((size_t)r * U + u) * 32 + lane;
 }
-__device__ __forceinline__ float2 *slot2(float *sm, int c, int u, int lane)
+__device__ __forceinline__ float *rows_fwd(float *sm, int c) { return sm + (size_t)(c % S) * STAGE; }
+__device__ __forceinline__ float *rows_adj(float *sm, int c) { return sm + (size_t)(c % S) * STAGE + 3 * 4 * U * 32; }
+
+// Stage NR time-major rows per step (arrays src[0..NR), steps k(u), u < U)
+// of the warp's 32 columns starting at column i0 into rows[(r U + u) 32 +
+// col].  wide: 16-byte copies shared by the warp (eight per 128-byte row
+// segment; needs ld % 4 == 0, 16-byte aligned arrays and i0 + 32 <= ld);
+// otherwise each lane copies its own column.  Rows with k(u) < 0 or k(u) >=
+// kmax_lane (per lane, or Kw for the wide copies) are skipped.
+template <int NR, typename KOF>
+__device__ __forceinline__ void stage_rows(float *rows, const float *const (&src)[NR], size_t ld, int i0, int lane,
+                                           bool wide, int k_lim, int k_lim_lane, KOF k_of)
 {
-    return reinterpret_cast<float2 *>(sm + (size_t)(c % S) * STAGE + 3 * 4 * U * 32) + (size_t)u * 32 + lane;
+    if (wide) {
+#pragma unroll
+        for (int m = 0; m < NR * U * 8 / 32; ++m) {
+            const int q = lane + 32 * m;               // segment: 8 per row
+            const int row = q >> 3, seg = q & 7;
+            const int r = row / U, u = row % U;
+            const int k = k_of(u);
+            if (k >= 0 && k < k_lim) cp16(rows + (size_t)row * 32 + seg * 4, src[r] + (size_t)k * ld + i0 + seg * 4);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k_of(u);
+            if (k >= 0 && k < k_lim_lane) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) cp4(rows + (size_t)(r * U + u) * 32 + lane, src[r] + (size_t)k * ld + i0 + lane);
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double x)
@@ -276,21 +310,17 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
     constexpr bool TAPE = MODE == LOSS_GRAD || MODE == FIT;
     const int nch = (Kw + U - 1) / U;
     const size_t ld = (size_t)a.ld;
+    const int i0 = i - lane;
+    const bool wide = a.wide_ok && i0 + 32 <= a.ld;   // warp-uniform
     auto issue = [&](int c) {
         if (c < nch) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int k = c * U + u;
-                if (k < Ki) {
-                    const size_t o = (size_t)k * ld + i;
-                    float *d = reinterpret_cast<float *>(slot4(sm, c, 0, u, lane));
-                    cp4(d, a.dp + o);
-                    cp4(d + 1, a.dv + o);
-                    if (MODE != FWD_OUT) {
-                        cp4(d + 2, a.oyy + o);
-                        cp4(d + 3, a.oyc + o);
-                    }
-                }
+            auto k_of = [c](int u) { return c * U + u; };
+            if (MODE == FWD_OUT) {
+                const float *const src[2] = {a.dp, a.dv};
+                stage_rows<2>(rows_fwd(sm, c), src, ld, i0, lane, wide, Kw, Ki, k_of);
+            } else {
+                const float *const src[4] = {a.dp, a.dv, a.oyy, reinterpret_cast<const float *>(a.oyc)};
+                stage_rows<4>(rows_fwd(sm, c), src, ld, i0, lane, wide, Kw, Ki, k_of);
             }
         }
         cp_commit();
@@ -315,8 +345,10 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
         for (int u = 0; u < U; ++u) {
             const int k = c * U + u;
             const bool valid = k < Ki;
-            const float4 row = *slot4(sm, c, 0, u, lane);     // dp, dv, observed position, observation code
-            const float dp = row.x, dv = row.y;
+            const float *rw = rows_fwd(sm, c) + u * 32 + lane;
+            const float dp = rw[0], dv = rw[U * 32];
+            const float y_obs = MODE != FWD_OUT ? rw[2 * U * 32] : 0.0f;
+            const float code_f = MODE != FWD_OUT ? rw[3 * U * 32] : 0.0f;
             const float gap_inv = rcp_approx(fmaxf(dp, IDM_GAP_FLOOR));
             const float uu = fmaf(dv, q.c, q.T);
             float as;
@@ -340,9 +372,9 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
             } else {
                 // observations at step k+1: the staged first one, then (MULTI)
                 // any further ones from the CSR
-                const int code = valid ? __float_as_int(row.w) : -1;
+                const int code = valid ? __float_as_int(code_f) : -1;
                 const bool has = code >= 0;
-                float r = (ph - row.z) + pl;
+                float r = (ph - y_obs) + pl;
                 float seed = has ? sgn(r) : 0.0f;
                 Lc += has ? fabsf(r) : 0.0f;
                 if (MODE == METRICS && has) {
@@ -378,20 +410,15 @@ __device__ __forceinline__ double fwd_phase(const Args &a, const Par &q, int i, 
         }
         return Lc;
     };
+    // several observations at one step: decided once per warp
+    const bool multi = MODE != FWD_OUT && __any_sync(FULL, act && Ki > 0 && a.multi[i] != 0);
     for (int c = 0; c < nch; ++c) {
         issue(c + S - 1);
         cp_wait<S - 1>();
+        if (wide) __syncwarp();   // rows copied by other lanes
         // Branch-free over the chunk: a lane past its horizon computes on
         // stale staged values and keeps its state (selects, predicated stores).
-        bool multi = false;
-        if (MODE != FWD_OUT) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int code = __float_as_int(slot4(sm, c, 0, u, lane)->w);
-                multi |= (c * U + u < Ki) && code >= 0 && (code & 7) > 1;
-            }
-        }
-        const float Lc = __any_sync(FULL, multi) ? chunk(c, std::true_type{}) : chunk(c, std::false_type{});
+        const float Lc = multi ? chunk(c, std::true_type{}) : chunk(c, std::false_type{});
         kahan(Ls, Lcomp, Lc);
     }
     const double L = (double)Ls - (double)Lcomp;
@@ -432,6 +459,8 @@ __device__ __forceinline__ void adj_phase(const Args &a, int i, int Ki, int Kw, 
 {
     const int nch = (Kw + U - 1) / U;
     const size_t ld = (size_t)a.ld;
+    const int i0 = i - lane;
+    const bool wide = a.wide_ok && i0 + 32 <= a.ld;   // warp-uniform
     auto issue = [&](int c) {
         if (c < nch) {
 #pragma unroll
@@ -443,11 +472,10 @@ __device__ __forceinline__ void adj_phase(const Args &a, int i, int Ki, int Kw, 
                     cp16(slot4(sm, c, 1, u, lane), a.tape_b + o);
                     if (MODE == FIT) cp16(slot4(sm, c, 2, u, lane), a.mom + o);
                     if (WD) cp4(reinterpret_cast<float *>(slot4(sm, c, 2, u, lane)), a.tape_d + o);
-                    float *d = reinterpret_cast<float *>(slot2(sm, c, u, lane));
-                    cp4(d, a.dp + o);
-                    cp4(d + 1, a.dv + o);
                 }
             }
+            const float *const src[2] = {a.dp, a.dv};
+            stage_rows<2>(rows_adj(sm, c), src, ld, i0, lane, wide, Kw, Ki, [c, Kw](int u) { return Kw - 1 - (c * U + u); });
         }
         cp_commit();
     };
@@ -461,6 +489,7 @@ __device__ __forceinline__ void adj_phase(const Args &a, int i, int Ki, int Kw, 
     for (int c = 0; c < nch; ++c) {
         issue(c + S - 1);
         cp_wait<S - 1>();
+        if (wide) __syncwarp();   // rows copied by other lanes
         // Branch-free: a lane past its horizon reads stale staged values and
         // keeps its state (selects, predicated stores).
 #pragma unroll
@@ -469,7 +498,7 @@ __device__ __forceinline__ void adj_phase(const Args &a, int i, int Ki, int Kw, 
             const bool valid = k >= 0 && k < Ki;
             const float4 ta = *slot4(sm, c, 0, u, lane);     // Av, Adp, Adv, w0n
             const float4 tb = *slot4(sm, c, 1, u, lane);     // w0n v, fa, frd, seed of step k+1
-            const float2 pv = *slot2(sm, c, u, lane);        // dp, dv
+            const float2 pv = make_float2(rows_adj(sm, c)[u * 32 + lane], rows_adj(sm, c)[(U + u) * 32 + lane]);   // dp, dv
             const float lpn = lp + tb.w;                     // lambda_p(k+1)
             const float mu = dt * lv;                        // dt lambda_v(k+1)
             const float lvn = fmaf(mu, ta.x, fmaf(dt, lpn, lv));   // lambda_v(k)
@@ -725,7 +754,7 @@ __global__ void traj_init_kernel(int N, int n_obs, const int32_t *off, const flo
 // Time-major observation index: row k of trajectory i names the first
 // observation at step k+1 (its position and 8 j + min(count, 7)).
 __global__ void obs_rows_kernel(int N, int n_obs, int k_max, int ld, const int32_t *off, const int32_t *obs_k,
-                                const float *p, float *oyy, int32_t *oyc, unsigned *status)
+                                const float *p, float *oyy, int32_t *oyc, int32_t *multi, unsigned *status)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_obs) return;
@@ -743,6 +772,7 @@ __global__ void obs_rows_kernel(int N, int n_obs, int k_max, int ld, const int32
     const size_t o = (size_t)(s - 1) * ld + i;
     oyy[o] = p[j];
     oyc[o] = j * 8 + cnt;
+    if (cnt > 1) multi[i] = 1;
 }
 
 __global__ void metrics_final_kernel(const double *acc, int n_traj, double *out)
@@ -815,6 +845,9 @@ rec::Args base_args(idm_ctx *c, const idm_recon_t *r, const idm_params_t *p, con
     a.obs_k = r->obs_k;
     a.obs_p = r->obs_p;
     a.status = (unsigned *)c->status.p;
+    // 16-byte row copies need 16-byte aligned rows of every staged array (the
+    // observation rows share ld and are the context's own allocations)
+    a.wide_ok = (r->ld % 4 == 0) && ((uintptr_t)dp % 16 == 0) && ((uintptr_t)dv % 16 == 0);
     return a;
 }
 
@@ -825,16 +858,20 @@ int build_obs_rows(idm_ctx *c, const idm_recon_t *r, rec::Args &a, cudaStream_t 
     int rc;
     if ((rc = ensure(c, c->rec_oyy, sizeof(float) * rows, "observation rows"))) return rc;
     if ((rc = ensure(c, c->rec_oyc, sizeof(int32_t) * rows, "observation codes"))) return rc;
+    if ((rc = ensure(c, c->rec_multi, sizeof(int32_t) * std::max<size_t>(r->ld, 1), "observation flags"))) return rc;
     IDM_CK(cudaMemsetAsync(c->rec_oyc.p, 0xff, sizeof(int32_t) * rows, st));
+    IDM_CK(cudaMemsetAsync(c->rec_multi.p, 0, sizeof(int32_t) * std::max<size_t>(r->ld, 1), st));
     if (r->n_obs > 0 && r->n_traj > 0) {
         const int n = (int)r->n_obs;
         rec::obs_rows_kernel<<<(n + 255) / 256, 256, 0, st>>>(r->n_traj, n, r->k_max, r->ld, r->obs_off, r->obs_k,
                                                               r->obs_p, (float *)c->rec_oyy.p,
-                                                              (int32_t *)c->rec_oyc.p, a.status);
+                                                              (int32_t *)c->rec_oyc.p, (int32_t *)c->rec_multi.p,
+                                                              a.status);
         IDM_CK(cudaGetLastError());
     }
     a.oyy = (const float *)c->rec_oyy.p;
     a.oyc = (const int32_t *)c->rec_oyc.p;
+    a.multi = (const int32_t *)c->rec_multi.p;
     return IDM_OK;
 }
 
