@@ -202,7 +202,7 @@ def test_predict_params_maps_into_the_box(api):
 def test_learned_init_beats_plain(api):
     """Train the network on simulated prefixes, then fit a held-out scene from
     the learned and from the plain initial guess with the same Adam schedule;
-    the FP64 oracle judges both fits against the noise-free truth."""
+    the FP64 oracle scores both fits against the noise-free truth."""
     # training set: 300K vehicles, 20-step noisy prefixes, shuffled
     rng = np.random.default_rng(60)
     tr = synth.make_scene([100] * 3000, rng)
