@@ -389,3 +389,72 @@ def test_padded_row_stride(api):
     np.testing.assert_array_equal(gdv.cpu().numpy()[:, :n], gdv_a.cpu().numpy())
     assert np.all(gdp.cpu().numpy()[:, n:] == 7.0)          # the padding is not written
     assert api.default_context().check_status() == 0
+
+
+def test_edge_trajectories(api):
+    """Degenerate and extreme trajectories in one call: no observation, a
+    single observation (K = 0), several observations at step 0 only, every
+    observation at one step (a step with 9 observations), a long trajectory
+    (K = 3,000 at dt = 0.1 s), and a count (33) that leaves a one-lane tail
+    warp: loss and every gradient against the oracle (the long trajectory
+    with tolerances scaled to its FP32 drift)."""
+    dt = F32(0.1)
+    rng = np.random.default_rng(61)
+    ts, ps, off = [], [], [0]
+
+    def add(t, p):
+        ts.append(np.asarray(t, np.float64)); ps.append(np.asarray(p, np.float64)); off.append(off[-1] + len(t))
+
+    add([], [])                                            # no observation
+    add([0.0], [5.0])                                      # a single observation
+    add([0.0, 0.01, 0.02], [1.0, 1.2, 1.3])                # several at step 0 only
+    add([0.0] + [0.96 + 0.01 * j for j in range(9)], [0.0] + list(8.0 + rng.uniform(-3, 3, 9)))   # 9 at step 10
+    long_t = np.append(np.arange(0.0, 299.5, 0.7), 300.0)
+    add(long_t, 12.0 * long_t + rng.normal(0, 2.0, len(long_t)))   # K = 3000
+    for _ in range(28):
+        T = rng.uniform(2.0, 8.0)
+        t = np.arange(0.0, T, 0.3)
+        add(t, rng.uniform(0, 50) + rng.uniform(5, 20) * t + rng.normal(0, 1.0, len(t)))
+    case = dict(off=np.array(off, np.int32), t=synth.f32(np.concatenate(ts)), p=synth.f32(np.concatenate(ps)), dt=dt)
+    n = len(off) - 1
+    assert n == 33
+    obs_k, K, p0, v0 = oracle_setup(case)
+    assert K[0] == 0 and K[1] == 0 and K[2] == 0 and K[3] == 10 and K[4] == 3000
+    k_max = int(K.max())
+    dp, dv = leader_vars(rng, k_max, n)
+    th = param_vars(rng, n)
+    case, obs_k = drop_ambiguous(case, obs_k, K, th, dp, dv, p0, v0)
+    K = R.horizons(case["off"], obs_k)
+    assert K[4] == 3000 and K[3] == 10
+    P, V, _ = R.forward(K, dp, dv, th, p0, v0, case["dt"], A_MIN)
+    L, gP = R.mae_seed(K, case["off"], obs_k, case["p"], P)
+    gr, gdp, gdv, gp0, gv0 = R.adjoint(K, dp, dv, th, case["dt"], V, gP, A_MIN)
+    g = GpuCase(api, case, p0, v0).r
+    np.testing.assert_array_equal(g.K.cpu().numpy()[:n], K)
+    loss, gth, gdp_g, gdv_g, gp_g, gv_g = g.loss_grad(cuda(th), cuda(dp), cuda(dv))
+    Pg, _, _ = g.forward(cuda(th), cuda(dp), cuda(dv))
+    torch.cuda.synchronize()
+    # positions: 1e-3 m over the first 100 steps; over 3,000 steps the FP32
+    # speed drifts, bounded here by 1e-2 m (the loss moves by at most the
+    # number of observations times that)
+    Pg = Pg.double().cpu().numpy()
+    assert np.max(np.abs(Pg[:101] - P[:101])) <= 1e-3
+    drift = np.max(np.abs(Pg - P))
+    assert drift <= 1e-2, drift
+    n_obs_long = int(np.sum(obs_k[case["off"][4]:case["off"][5]] > 0))
+    assert abs(loss.item() - L) <= 1e-6 * L + n_obs_long * drift
+    gth = gth.double().cpu().numpy()
+    short = np.array([i for i in range(n) if i != 4])
+    for q in range(6):
+        grad_close(gth[q][short], gr[q][short], what="param %d" % q)
+        assert abs(gth[q][4] - gr[q][4]) <= 1e-3 * abs(gr[q][4]) + 1e-6, q    # the 3,000-step trajectory
+    grad_close(gdp_g.double().cpu().numpy()[:, short], gdp[:, short], what="dp")
+    grad_close(gdv_g.double().cpu().numpy()[:, short], gdv[:, short], what="dv")
+    for gg, rr in ((gdp_g, gdp), (gdv_g, gdv)):
+        col = gg.double().cpu().numpy()[:, 4]
+        assert np.linalg.norm(col - rr[:, 4]) <= 1e-3 * np.linalg.norm(rr[:, 4])
+    grad_close(gv_g.double().cpu().numpy()[short], gv0[short], what="v_init")
+    # trajectories without steps have zero gradients everywhere
+    for i in (0, 1, 2):
+        assert np.all(gth[:, i] == 0.0)
+    assert api.default_context().check_status() == 0
