@@ -548,14 +548,16 @@ def displacement(px, py, tx, ty, miss_m=2.0, ctx=None):
 
 
 def predict_rollout(lanes, x_hist, y_hist, lane_lo, lane_hi, dt, n_fut, n_iter=500, lr0=0.1, lr1=0.01,
-                    box_lo=PRED_BOX_LO, box_hi=PRED_BOX_HI, theta0=RECON_INIT, a_min=-10.0, ctx=None):
+                    box_lo=PRED_BOX_LO, box_hi=PRED_BOX_HI, theta0=RECON_INIT, a_min=-10.0, ctx=None, tune=False):
     """Training-free prediction (Sec. IV-B, V-C): assign every agent to the
     nearest candidate lane at the last history frame, project its history
     onto that lane, order the agents lane by lane (head first), fit the IDM
     parameters to the H - 1 history steps, roll out n_fut steps from the last
     history frame and project the rollout back onto the lane centre lines.
     x_hist, y_hist: (H, N).  Returns a dict (agents in the fitted order given
-    by perm): perm, lane, theta, loss history, s_hist (H, N), x, y (n_fut, N)."""
+    by perm): perm, lane, theta, loss history, s_hist (H, N), x, y (n_fut, N).
+    tune: pick the fit's kernel shape with the autotuner (cached per GPU and
+    problem signature) before fitting."""
     ctx = ctx or default_context()
     st = _stream()
     x_hist, y_hist = _f32(x_hist), _f32(y_hist)
@@ -571,6 +573,11 @@ def predict_rollout(lanes, x_hist, y_hist, lane_lo, lane_hi, dt, n_fut, n_iter=5
     scene = Scene.from_lane_off(lane_off, torch.full((N,), PRED_LENGTH, device="cuda", dtype=torch.float32))
     p0, v0 = rollout_state(s_sorted, 0, 1, dt, ctx=ctx)
     theta = torch.tensor(theta0, dtype=torch.float32, device="cuda")[:, None].repeat(1, N).contiguous()
+    if tune:
+        from . import tune as _tune
+        sig = _tune.signature(scene.max_lane, N, H - 1, 1, kind="predict")
+        _tune.tuned(ctx, lambda c: loss_grad(theta, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, a_min, ctx=c),
+                    scene.max_lane, sig)
     hist = fit(theta, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, n_iter, lr0, lr1, box_lo, box_hi, a_min, ctx=ctx)
     pr, vr = rollout_state(s_sorted, H - 2, H - 1, dt, ctx=ctx)
     traj = simulate(theta, pr, vr, scene, n_fut, dt, a_min, ctx=ctx)

@@ -104,7 +104,7 @@ inline Part partials(float v, float gap, float vh, const Veh &q, float inv_dt, f
     o.dth[2] = -w;
     o.dth[3] = sig2 * fa + w * v * dvel * q.c / (2.0f * q.am);
     o.dth[4] = w * v * dvel * q.c / (2.0f * q.b);
-    o.dth[5] = (rd > 0.0f) ? -sig2 * q.am * rd * logf(r) : 0.0f;
+    o.dth[5] = (r > 0.0f && rd > 0.0f) ? -sig2 * q.am * rd * logf(r) : 0.0f;   // r -> 0+ limit near rest
     return o;
 }
 

@@ -284,7 +284,11 @@ __device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const V
     if (WANT_DELTA) {
         const f2 lnr = mul2(lg2(r), F2(LN2));
         const f2 t = mul2(J.frd, lnr);
-        J.frdl = make_float2(rd.x > 0.0f ? t.x : 0.0f, rd.y > 0.0f ? t.y : 0.0f);
+        // r^delta ln r -> 0 as r -> 0+.  Near rest the a_lb = -v/dt branch
+        // leaves v + dt a* within rounding of 0: a speed a few ulps below 0,
+        // or a denormal that the flush-to-zero logarithm reads as 0, also
+        // take the limit (r^delta has underflowed to 0 there)
+        J.frdl = make_float2(r.x > 0.0f && rd.x > 0.0f ? t.x : 0.0f, r.y > 0.0f && rd.y > 0.0f ? t.y : 0.0f);
     } else {
         J.frdl = F2(0.0f);
     }

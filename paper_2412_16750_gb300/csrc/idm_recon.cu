@@ -178,7 +178,7 @@ __device__ __forceinline__ Jac1 jac1(float v, float dp, float dv, const Par &q, 
     J.frd = sig2 * rd;
     if (WD) {
         const float t = J.frd * (lg2_approx(r) * LN2);
-        J.frdl = rd > 0.0f ? t : 0.0f;
+        J.frdl = r > 0.0f && rd > 0.0f ? t : 0.0f;   // the r -> 0+ limit (also for a speed rounded to <= 0 or a denormal)
     } else {
         J.frdl = 0.0f;
     }

@@ -108,3 +108,28 @@ def test_argument_errors(cpu):
         cpu.idm_cpu_forward(th, sc["p_init"], sc["v_init"], s, 0, DT)
     with pytest.raises(cpu.CpuError):
         cpu.idm_cpu_loss_grad(th, sc["p_init"], sc["v_init"], s, 10, DT, np.zeros((10, 7)), 0)
+
+
+def test_braking_to_rest_delta_gradient(cpu):
+    # a creeping follower a few centimetres behind a stopped leader: its next
+    # speed rounds below 0; the delta gradient must stay finite (r -> 0+ limit)
+    rng = np.random.default_rng(81)
+    p, v = [], []
+    for _ in range(20):
+        g1 = rng.uniform(0.02, 0.5)
+        p += [0.0, -(5.0 + g1)]
+        v += [0.0, rng.uniform(0.05, 0.9)]
+    lane_off = synth.lane_offsets([2] * 20)
+    length = np.full(40, 5.0)
+    th = synth.plain_init(40)
+    K = 30
+    P, V = oracle.forward(lane_off, length, th, p, v, K, DT, A_MIN)
+    Y = synth.f32(P[1:] + np.random.default_rng(82).normal(0, 0.5, size=(K, 40)))
+    s = cpu.Scene(lane_off, length)
+    L, g, gp, gv = cpu.idm_cpu_loss_grad(th, synth.f32(p), synth.f32(v), s, K, DT, Y, 1, A_MIN)
+    assert np.isfinite(g).all()
+    P, V = oracle.forward(lane_off, length, th, synth.f32(p), synth.f32(v), K, DT, A_MIN)
+    Lr, gP = oracle.mse_seed(P, Y, 1)
+    gr, _, _ = oracle.adjoint(lane_off, length, th, K, DT, P, V, gP, None, A_MIN)
+    assert abs(L - Lr) <= 1e-5 * Lr
+    grad_close(g, gr)

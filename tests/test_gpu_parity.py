@@ -443,3 +443,33 @@ def test_full_size_sampled_lanes(api):
         P, _ = oracle.forward(np.array([0, e - a], dtype=np.int32), sc["length"][a:e], theta[:, a:e],
                               sc["p_init"][a:e], sc["v_init"][a:e], K, DT, A_MIN)
         assert np.max(np.abs(traj[:, a:e].double().cpu().numpy() - P)) <= 5e-3
+
+
+def braking_scene(seed, n_lanes=30):
+    """Lanes of three: a stopped leader, a follower creeping (v < 1 m/s, so
+    the -v/dt bound is active) a few centimetres behind it, a third vehicle
+    behind that.  The follower's next speed rounds to a few ulps below 0."""
+    rng = np.random.default_rng(seed)
+    p, v, L = [], [], []
+    for _ in range(n_lanes):
+        g1, g2 = rng.uniform(0.02, 0.5), rng.uniform(0.5, 3.0)
+        p += [0.0, -(5.0 + g1), -(10.0 + g1 + g2)]
+        v += [0.0, rng.uniform(0.05, 0.9), rng.uniform(0.0, 0.9)]
+        L += [5.0, 5.0, 5.0]
+    N = 3 * n_lanes
+    th = np.vstack([rng.uniform(lo, hi, N) for lo, hi in synth.TRUE_RANGES] + [np.full(N, 4.0)])
+    return dict(lane_off=synth.lane_offsets([3] * n_lanes), length=synth.f32(L), p_init=synth.f32(p),
+                v_init=synth.f32(v), theta_true=synth.f32(th))
+
+
+def test_braking_to_rest_delta_gradient(api):
+    sc = braking_scene(71)
+    K, s = 30, 1
+    Y = noisy_targets(sc, K, s, np.random.default_rng(72))
+    th = synth.plain_init(len(sc["length"]))
+    L, g_ref, gp_ref, gv_ref, _ = oracle_loss_grad(sc, th, Y, K, s)
+    loss, g, gp, gv = run_loss_grad(api, sc, th, Y, K, s)
+    assert np.isfinite(g).all() and np.isfinite(gp).all() and np.isfinite(gv).all()
+    assert abs(loss - L) <= 1e-5 * L
+    grad_close(g, g_ref)
+    assert api.default_context().check_status() == 0
