@@ -649,6 +649,12 @@ def reconstruction(a, dev):
             "paper_s_per_trajectory": paper_s,
             "trajectory_steps_per_s": steps * a.recon_iters / (ms * 1e-3),
             "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+            "roofline": {"kernel": "recon_fit_kernel (all iterations in one launch)", "bound": "hbm",
+                         "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                         "bytes_per_trajectory_step": RECON_BYTES_PER_STEP,
+                         "note": "one serial chain per trajectory: with few trajectories (filtering) the kernel is "
+                                 "latency-bound below this roof"},
             "us_per_step_of_longest": ms * 1e3 / (a.recon_iters * r.k_max),
             "gpu_launches": 1,
             "loss": {"initial": float(h[0]), "final": float(h[-1])},
@@ -726,6 +732,7 @@ def prediction(a, dev):
     cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
     stream = torch.cuda.current_stream(dev)
     sc = synth.prediction_scenes(a.pred_scen, np.random.default_rng(synth.SEED_BASE + 70))
+    peaks, _ = measured_peaks()
     H, Fn = sc["n_hist"], sc["n_fut"]
     N = sc["x"].shape[1]
     ctx = api.Context()
@@ -763,6 +770,14 @@ def prediction(a, dev):
            "pipeline_ms": total_ms, "ms_per_scenario": total_ms / a.pred_scen,
            "projection_ms": proj_ms, "projection_segments": seg_assign + seg_proj,
            "projection_segments_per_s": (seg_assign + seg_proj) / (proj_ms * 1e-3),
+           "projection_roofline": {"kernel": "project_kernel", "bound": "alu",
+                                   "achieved": 15.0 * (seg_assign + seg_proj) / (proj_ms * 1e-3) / 1e9,
+                                   "peak": alu_peak_ginst(peaks.get("sm_max_mhz", 2070.0),
+                                                          torch.cuda.get_device_properties(dev).multi_processor_count),
+                                   "unit": "Ginstr/s (FP32 pipe)",
+                                   "ops_per_segment": 15,
+                                   "note": "FP32 operations of one segment distance (direction, clamped parameter, "
+                                           "foot point, squared distance, compare); two projection launches"},
            "ade_m": float(sums[0] / N), "fde_m": float(sums[1] / N), "miss_rate_2m": float(sums[2] / N),
            "final_loss": float(out["loss"][-1].item()), "fit_shape": list(ctx.tuning),
            "paper": "WOMD validation: minADE 7.862 m, minFDE 15.668 m, miss rate 0.586 (Table II)"}
