@@ -196,13 +196,49 @@ def test_fit_reduces_loss_and_is_stationary_at_the_truth():
 
 def test_metrics_hand_made():
     K = np.array([4, 4], np.int32)
-    P = np.array([[0.0, 0.0], [1.0, 2.0], [2.0, 4.0], [3.0, 6.0], [4.0, 8.0]])
-    A = np.array([[1.0, -2.0], [1.0, 12.0], [-1.0, 2.0], [1.0, -2.0]])
+    P = np.array([[3.0, 0.0], [4.0, 2.0], [5.0, 4.0], [6.0, 6.0], [7.0, 8.0]])
+    A = np.array([[1.0, -2.0], [5.0, 12.0], [-1.0, 2.0], [1.0, -2.0]])
     off = np.array([0, 2, 4], np.int32)
     ks = np.array([0, 4, 0, 4], np.int32)
-    ys = np.array([0.0, 4.4, 0.0, 8.0])             # trajectory 0: error 0.4 at k=4 over length 4.4
+    ys = np.array([3.0, 7.4, 0.0, 8.0])             # trajectory 0: error 0.4 at k=4 over length 4.4
     pos, mean, std, imp = R.metrics(K, off, ks, ys, P, A)
     assert abs(pos - (0.4 / 4.4) / 4) < 1e-12
     absa = np.abs(A).ravel()
     assert abs(mean - absa.mean()) < 1e-12 and abs(std - absa.std()) < 1e-12
-    assert imp == 0.5
+    assert imp == 0.5                                # |a*| = 5 in trajectory 0 is not implausible
+
+
+def test_mae_several_observations_per_step():
+    # two observations at one step: both enter the loss, the seed is the sum
+    # of their signs (here one on each side of the position: seed 0)
+    K = np.array([3], np.int32)
+    P = np.array([[0.0], [1.0], [2.0], [3.0]])
+    off = np.array([0, 4], np.int32)
+    ks = np.array([0, 2, 2, 3], np.int32)
+    ys = np.array([0.0, 3.0, -1.0, 5.0])
+    L, gP = R.mae_seed(K, off, ks, ys, P)
+    assert L == 1.0 + 3.0 + 2.0
+    np.testing.assert_array_equal(gP[:, 0], [0.0, 0.0, 0.0, -1.0])
+    L, gP = R.mae_seed(K, off, np.array([0, 2, 2, 2], np.int32), np.array([0.0, 3.0, 4.0, -1.0]), P)
+    assert L == 1.0 + 2.0 + 3.0 and gP[2, 0] == -1.0
+
+
+def test_gap_floor_has_zero_derivative():
+    # virtual-leader gaps below the floor: the loss does not depend on them
+    K, th, dp, dv, p0, v0, off, ks, ys = _toy(9)
+    dp = dp.copy()
+    dp[2:6, :] = 0.05
+    P, V, _ = R.forward(K, dp, dv, th, p0, v0, DT, A_MIN)
+    _, gP = R.mae_seed(K, off, ks, ys, P)
+    _, gdp, _, _, _ = R.adjoint(K, dp, dv, th, DT, V, gP, A_MIN)
+    assert np.all(gdp[2:6, :] == 0.0)
+    L0 = _loss(K, th, dp, dv, p0, v0, off, ks, ys)
+    d2 = dp.copy()
+    d2[3, 1] = 0.07
+    assert _loss(K, th, d2, dv, p0, v0, off, ks, ys) == L0
+    # the same steps with their original (above-floor) gaps do have a derivative
+    K, th, dp0, dv, p0, v0, off, ks, ys = _toy(9)
+    P, V, _ = R.forward(K, dp0, dv, th, p0, v0, DT, A_MIN)
+    _, gP = R.mae_seed(K, off, ks, ys, P)
+    _, gdp0, _, _, _ = R.adjoint(K, dp0, dv, th, DT, V, gP, A_MIN)
+    assert np.any(gdp0[2:6, :] != 0.0)
