@@ -6,11 +6,13 @@
 //
 // One thread per trajectory, one warp per block.  Every per-step array is
 // time-major, so at step k a warp touches one 128-byte row segment per array.
-// Rows are staged into shared memory with cp.async, S chunks of U steps
+// Rows are staged into shared memory with cp.async, S - 1 chunks of U steps
 // ahead of use, so the forward's serial chain (the speed of step k+1 needs the
-// whole model evaluation of step k) does not wait on memory.  A lane reads
-// only the shared-memory column it copied itself, so its own
-// cp.async.wait_group is the only synchronisation.
+// whole model evaluation of step k) does not wait on memory: rows of the
+// caller's arrays with 16-byte copies shared by the warp (then __syncwarp), or
+// with 4-byte copies of each lane's own column when the row stride is not a
+// multiple of four; the tape and the Adam moments with one 16-byte copy per
+// lane of its own data.
 //
 // Forward: integrates the state and, while its serial chain (one model
 // evaluation per step) leaves most issue slots idle, evaluates the adjoint's
@@ -41,9 +43,10 @@ namespace rec {
 
 constexpr int U = 8;                       // steps per staged chunk
 constexpr int S = 3;                       // chunks in flight
-// A stage holds, per step and lane: three float4 slots (forward: dp, dv and
-// the observation row; adjoint: the two tape halves and the Adam moments or
-// the delta factor) and one float2 slot (adjoint: dp, dv).
+// A stage holds, per step and lane: three float4 slots (forward: the rows of
+// dp, dv, the observed position and the observation code, overlaid as four
+// float rows; adjoint: the two tape halves and the Adam moments or the delta
+// factor) and two float rows (adjoint: dp, dv).
 constexpr int STAGE = (3 * 4 + 2) * U * 32;   // floats per chunk
 constexpr int SMEM = (int)sizeof(float) * S * STAGE;
 
@@ -262,8 +265,9 @@ __device__ __forceinline__ float *rows_adj(float *sm, int c) { return sm + (size
 // of the warp's 32 columns starting at column i0 into rows[(r U + u) 32 +
 // col].  wide: 16-byte copies shared by the warp (eight per 128-byte row
 // segment; needs ld % 4 == 0, 16-byte aligned arrays and i0 + 32 <= ld);
-// otherwise each lane copies its own column.  Rows with k(u) < 0 or k(u) >=
-// kmax_lane (per lane, or Kw for the wide copies) are skipped.
+// otherwise each lane copies its own column.  Rows with k(u) < 0, or k(u) >=
+// k_lim_lane (the lane's horizon, own-column copies) or k_lim (the warp's
+// largest horizon, wide copies) are skipped.
 template <int NR, typename KOF>
 __device__ __forceinline__ void stage_rows(float *rows, const float *const (&src)[NR], size_t ld, int i0, int lane,
                                            bool wide, int k_lim, int k_lim_lane, KOF k_of)
