@@ -193,3 +193,57 @@ def test_bad_lane_index_sets_status(api):
     rc, flags = ctx.status()
     assert rc == lib.IDM_ERR_LANES and flags & lib.IDM_STATUS_BAD_LANES
     assert ctx.status()[0] == lib.IDM_OK
+
+
+def test_full_size_prediction_sampled_lanes(api):
+    """The prediction workload of the benchmark (10,000 scenarios) through
+    the GPU pipeline; 40 sampled lanes (every agent on them) re-run by the
+    oracle's pipeline: assignment, projected history, fitted parameters (5
+    Adam iterations), rollout positions.  Lanes whose agents have near-tied
+    nearest lanes are not sampled."""
+    sc = synth.prediction_scenes(10000, np.random.default_rng(synth.SEED_BASE + 70))
+    H, Fn = sc["n_hist"], sc["n_fut"]
+    N = sc["x"].shape[1]
+    n_iter = 5
+    L = lanes_of(api, sc)
+    out = api.predict_rollout(L, cuda(sc["x"][:H]), cuda(sc["y"][:H]), cuda(sc["lane_lo"], torch.int32),
+                              cuda(sc["lane_hi"], torch.int32), sc["dt"], Fn, n_iter)
+    torch.cuda.synchronize()
+    perm = out["perm"].cpu().numpy()
+    lane_off = out["lane_off"].cpu().numpy()
+    s_g = out["s_hist"].cpu().numpy()
+    th_g = out["theta"].double().cpu().numpy()
+    x_g, y_g = out["x"].cpu().numpy(), out["y"].cpu().numpy()
+    polys = polylines(sc)
+    rng = np.random.default_rng(90)
+    used = np.where(np.diff(lane_off) > 0)[0]
+    checked = 0
+    for l in rng.permutation(used):
+        a0, a1 = lane_off[l], lane_off[l + 1]
+        agents = perm[a0:a1]
+        asg = oracle_assign(sc, polys, H - 1, agents)
+        if min(x[3] for x in asg) < 1e-2 or any(x[0] != l for x in asg):
+            continue
+        # oracle pipeline on this lane alone (lanes do not interact)
+        s_hist = np.array([[G.project(polys[l], (float(sc["x"][f, i]), float(sc["y"][f, i])))[0] for i in agents]
+                           for f in range(H)])
+        sub_perm, sub_off = oracle.layout(np.zeros(len(agents), np.int32), s_hist[0], 1)
+        np.testing.assert_array_equal(agents[sub_perm], agents)      # the GPU's lane order
+        np.testing.assert_allclose(s_g[:, a0:a1], s_hist, rtol=0, atol=1e-3)
+        n = len(agents)
+        p0, v0 = G.rollout_state(s_hist, 0, 1, sc["dt"])
+        th0 = np.array(api.RECON_INIT)[:, None].repeat(n, 1)
+        th, _ = oracle.fit(np.array([0, n], np.int32), np.full(n, api.PRED_LENGTH), th0, p0, v0, H - 1, sc["dt"],
+                           s_hist[1:], 1, n_iter, 0.1, 0.01, api.PRED_BOX_LO, api.PRED_BOX_HI, A_MIN)
+        np.testing.assert_allclose(th_g[:, a0:a1], th, rtol=1e-4, atol=1e-4)
+        pr, vr = G.rollout_state(s_hist, H - 2, H - 1, sc["dt"])
+        P, _ = oracle.forward(np.array([0, n], np.int32), np.full(n, api.PRED_LENGTH), th, pr, vr, Fn, sc["dt"], A_MIN)
+        for j in range(n):
+            for f in (0, Fn // 2, Fn - 1):
+                p = G.unproject(polys[l], P[f + 1, j])
+                assert abs(x_g[f, a0 + j] - p[0]) < 2e-2 and abs(y_g[f, a0 + j] - p[1]) < 2e-2
+        checked += 1
+        if checked == 40:
+            break
+    assert checked == 40
+    assert api.default_context().check_status() == 0
