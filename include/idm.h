@@ -127,6 +127,19 @@ int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
  * adjoint's 4 x 4). */
 int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_interval, int warps_per_block);
 
+/* How idm_fit runs its iterations (see idm_fit).  IDM_FIT_AUTO (default):
+ * the single launch when K <= ckpt_interval (then the forward runs in the
+ * first iteration only: its one checkpoint is the initial state) or N * K <=
+ * 2^22 vehicle-steps, where the per-iteration launch boundary is a sizeable
+ * share of an iteration; else the graph, whose forward runs at its own,
+ * higher occupancy.  The graph is always used by idm_fit_eval and while profiling
+ * is on (idm_set_profiling times every launch of the graph).  Returns
+ * IDM_ERR_ARG for another value. */
+#define IDM_FIT_AUTO 0
+#define IDM_FIT_GRAPH 1
+#define IDM_FIT_SINGLE_LAUNCH 2
+int idm_set_fit_mode(idm_ctx_t *ctx, int mode);
+
 /* Longest lane the library can simulate (vehicles): 32 * 8 * 8 = 2048. */
 int idm_max_lane_supported(void);
 
@@ -207,9 +220,19 @@ int idm_loss_grad(idm_ctx_t *ctx, const idm_scene_t *scene, const idm_params_t *
  * a_max, b), projection onto [box_lo[q], box_hi[q]]}; delta is not changed.
  * The learning rate of iteration t (0-based) is lr0 + (lr1 - lr0) t /
  * (n_iter - 1); Adam uses beta1 0.9, beta2 0.999, eps 1e-8, zero initial
- * moments.  The n_iter iterations (1 <= n_iter <= 100000) are captured once
- * into a CUDA graph, cached on the context for calls with identical
- * arguments, and launched on `stream` as one graph.
+ * moments.  The n_iter iterations (1 <= n_iter <= 100000) run in one of two
+ * forms with identical results (idm_set_fit_mode):
+ *   - graph: one forward and one adjoint launch per iteration (the forward
+ *     in the first iteration only when K <= ckpt_interval), captured once
+ *     into a CUDA graph, cached on the context for calls with identical
+ *     arguments, and launched on `stream` as one graph;
+ *   - single launch: one persistent kernel in which each group of warps
+ *     carries its lane segments through all n_iter iterations (lanes never
+ *     interact, so no iteration waits for the rest of the scene), plus one
+ *     reduction of the loss history.
+ * Workspace of the single launch: 8 * n_iter * min(n_lanes, 2 * ceil(N /
+ * cap) + 1024) * warps_per_segment bytes of loss partials (cap = 32 * vpt *
+ * warps_per_segment).
  *   params (device, in/out): initial guess in, fitted values out.
  *   box_lo, box_hi (HOST, [5], order v0, T, s0, a_max, b).
  *   loss_hist (device out, double [n_iter], may be NULL): loss at the

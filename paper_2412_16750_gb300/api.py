@@ -29,6 +29,14 @@ class Context:
         lib.idm_set_tuning(self.handle, vpt, warps_per_segment, ckpt_interval, warps_per_block)
         self.tuning = (vpt, warps_per_segment, ckpt_interval, warps_per_block)
 
+    def set_fit_mode(self, mode):
+        """How idm_fit runs its iterations: "auto", "graph" (one forward and
+        one adjoint launch per iteration in a CUDA graph) or "single" (every
+        iteration in one persistent launch); the results are identical."""
+        code = {"auto": lib.IDM_FIT_AUTO, "graph": lib.IDM_FIT_GRAPH, "single": lib.IDM_FIT_SINGLE_LAUNCH}[mode]
+        lib.idm_set_fit_mode(self.handle, code)
+        self.fit_mode = mode
+
     def status(self, stream=None):
         rc, flags = lib.idm_status(self.handle, stream or torch.cuda.current_stream())
         return rc, flags

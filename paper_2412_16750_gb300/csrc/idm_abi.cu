@@ -191,6 +191,7 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     CK(idm::launch_build_segments(sc->lane_off, L, nullptr, 0, 32 * P->vpt * G, N, (Seg *)c->seg.p,
                                   (int *)c->ctl.p + CTL_NSEG, a.status, st));
     P->loss_per_seg = G;
+    P->k_max = sim->K;
     return forward_grid(c, P, L);
 }
 
@@ -294,7 +295,7 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     // The graph depends on every launch argument; reuse it when they repeat.
     struct Key {
         SimArgs a;
-        int vpt, G, grid_f, grid_b, wpb, wpb_b, n_iter, profiling, loss_per_seg;
+        int vpt, G, grid_f, grid_b, wpb, wpb_b, n_iter, profiling, loss_per_seg, fwd_once;
         const double *hist;
         const float *eval_targets;
         const double *eval_hist;
@@ -304,6 +305,11 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     key.a = a;
     key.vpt = P.vpt * 16 + P.vpt_f; key.G = P.G * 16 + P.G_f; key.grid_f = P.grid_f; key.grid_b = P.grid_b; key.wpb = P.wpb_f;
     key.wpb_b = P.wpb_b; key.n_iter = n_iter; key.profiling = c->profiling; key.loss_per_seg = P.loss_per_seg;
+    // With every horizon within one checkpoint interval the only checkpoint
+    // is the initial state, which no iteration changes: the forward runs in
+    // the first iteration only (the adjoint recomputes the steps itself).
+    const bool fwd_once = !eval && P.k_max <= c->C;
+    key.fwd_once = fwd_once;
     key.hist = loss_hist;
     key.eval_targets = eval ? eval_targets : nullptr;
     key.eval_hist = eval ? eval_hist : nullptr;
@@ -326,9 +332,11 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
         if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, cs);
         for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
             a.iter = it;
-            e = cudaMemsetAsync((int *)c->ctl.p + CTL_WORK_F, 0, sizeof(int) * 2, cs);
+            const bool run_fwd = !fwd_once || it == 0;
+            e = cudaMemsetAsync((int *)c->ctl.p + (run_fwd ? CTL_WORK_F : CTL_WORK_B), 0,
+                                sizeof(int) * (run_fwd ? 2 : 1), cs);
             if (e == cudaSuccess && c->profiling) e = cudaEventRecordWithFlags(c->ev[4 * it], cs, cudaEventRecordExternal);
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && run_fwd) {
                 SimArgs af = a;
                 af.work = (int *)c->ctl.p + CTL_WORK_F;
                 if (eval) {
@@ -365,6 +373,43 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
         c->ev_used = c->profiling ? n_iter : 0;
     }
     CK(cudaGraphLaunch(c->fit_exec, st));
+    return IDM_OK;
+}
+
+// The fit as one persistent launch (idm_fused.cuh) for a single scene:
+// clear the Adam moments and the work counter, run every iteration of every
+// segment, then reduce the loss partials of all iterations.  The partials
+// are sized for the most segments the packing can produce: next-fit packing
+// inside each of the builder's 1024 lane chunks closes a segment only when
+// the next lane would overflow it, so two consecutive segments of a chunk
+// hold more than `cap` vehicles and a chunk of n vehicles gives at most
+// 2n/cap + 1 segments.
+int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const float *box_lo, const float *box_hi,
+                   float lr0, float lr1, double *loss_hist, cudaStream_t st)
+{
+    int rc;
+    if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
+    if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
+    const long long cap = 32LL * P.vpt * P.G;
+    const long long seg_bound = std::min<long long>(n_lanes, 2 * (((long long)N + cap - 1) / cap) + 1024);
+    const long long stride = std::max<long long>(1, seg_bound * P.G);
+    if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
+        return rc;
+    SimArgs &a = P.a;
+    a.adam_m = (float *)c->adam_m.p;
+    a.adam_v = (float *)c->adam_v.p;
+    a.n_iter = n_iter;
+    a.lr0 = lr0;
+    a.lr1 = lr1;
+    for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
+    a.loss_part = (double *)c->fit_part.p;
+    a.work = (int *)c->ctl.p + CTL_WORK_B;
+    CK(cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, st));
+    CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
+    CK(cudaMemsetAsync(a.work, 0, sizeof(int), st));
+    CK(idm::launch_fit_fused(P.vpt, P.G, a, stride, P.grid_b, P.wpb_b, st));
+    if (loss_hist)
+        CK(idm::launch_loss_finalize_iters(a.loss_part, stride, a.n_seg, P.loss_per_seg, n_iter, loss_hist, st));
     return IDM_OK;
 }
 
@@ -414,7 +459,8 @@ int idm_ctx_destroy(idm_ctx_t *c)
                    &c->loss_part, &c->loss_tmp,  &c->adam_m,       &c->adam_v,       &c->lay_counts,
                    &c->lay_cursor, &c->eval_part, &c->sub_ckpt,    &c->scen_tab,     &c->scen_seg_off,
                    &c->scen_seg_idx, &c->lane_off_dev, &c->rec_oyy, &c->rec_oyc,    &c->rec_tape,
-                   &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax,     &c->rec_multi};
+                   &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax,     &c->rec_multi,
+                   &c->fit_part};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -438,6 +484,15 @@ int idm_set_tuning(idm_ctx_t *c, int vpt, int warps_per_segment, int ckpt_interv
     c->G_req = warps_per_segment;
     c->C = ckpt_interval;
     c->wpb = warps_per_block;
+    return IDM_OK;
+}
+
+int idm_set_fit_mode(idm_ctx_t *c, int mode)
+{
+    if (!c) return IDM_ERR_ARG;
+    if (mode != IDM_FIT_AUTO && mode != IDM_FIT_GRAPH && mode != IDM_FIT_SINGLE_LAUNCH)
+        return fail(c, IDM_ERR_ARG, "fit mode must be IDM_FIT_AUTO, IDM_FIT_GRAPH or IDM_FIT_SINGLE_LAUNCH");
+    c->fit_mode = mode;
     return IDM_OK;
 }
 
@@ -611,6 +666,14 @@ int idm_fit_eval(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, c
     if ((rc = prepare(c, scene, params, p_init, v_init, sim, true, true, obs_stride, &P, st))) return rc;
     if ((rc = backward_grid(c, &P, false, true, false, scene->n_lanes))) return rc;
     P.a.targets = targets;
+    const double vehicle_steps = (double)scene->n_vehicles * (double)sim->K;
+    const bool single = !eval_targets && !c->profiling &&
+                        (c->fit_mode == IDM_FIT_SINGLE_LAUNCH ||
+                         (c->fit_mode == IDM_FIT_AUTO &&
+                          (sim->K <= c->C || vehicle_steps <= IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS)));
+    if (single)
+        return run_fit_single(c, P, n_iter, (size_t)scene->n_vehicles, scene->n_lanes, box_lo, box_hi, lr0, lr1,
+                              loss_hist, st);
     return run_fit_graph(c, P, n_iter, (size_t)scene->n_vehicles, box_lo, box_hi, lr0, lr1, loss_hist, nullptr, 0,
                          st, single_finalize, eval_targets, eval_hist);
 }

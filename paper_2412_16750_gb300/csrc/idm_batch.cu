@@ -319,6 +319,7 @@ int idm_batch_fit(idm_ctx_t *c, const idm_batch_t *b, idm_params_t *params, cons
     if ((rc = prepare_batch(c, b, params, p_init, v_init, true, &P, BP, st))) return rc;
     if ((rc = backward_grid(c, &P, false, true, false, (int)std::max<size_t>(BP.seg.size(), 1)))) return rc;
     P.a.targets = targets;
+    P.k_max = BP.max_K;
     g_bfin = BatchFinalize{b->n_scen, scen_loss};
     struct {
         int S;

@@ -1,0 +1,97 @@
+// The forward pass over one warp segment (Eq. 1-3 with the Sec. III-C
+// bounds, arXiv 2412.16750): K Euler steps with checkpoints every C steps,
+// optional trajectory / speed output and an optional squared error against
+// a second target set.  Used by the forward kernel (idm_sim.cu) and by the
+// single-launch fit (idm_fused.cuh).
+#pragma once
+#include "idm_sim_common.cuh"
+
+namespace idm {
+
+// ---------------------------------------------------------------------------
+// Forward: K steps per segment, optional trajectory / speed output,
+// checkpoints every C steps.  (The squared-error loss is accumulated by the
+// adjoint's recompute, which evaluates the residuals anyway.)
+// ---------------------------------------------------------------------------
+struct FwdFlags {
+    bool traj, vtraj, ckpt, eval;
+};
+
+template <int NP, bool D4>
+__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
+                                                const VehConst2 (&kc)[NP], State2 (&st)[NP], const bool (&vx)[NP],
+                                                const bool (&vy)[NP], FwdFlags f)
+{
+    const int lane = g.lane;
+    const int Ns = sc.n_veh;
+    const int wl = lb + g.w * 64 * NP;  // scenario-local index of this warp's first slot
+    int next_ck = 0, ck_idx = 0;
+    int xp = 0;
+    int obs_k = sc.obs_stride, obs_row = 0;  // next observed step and its target row (eval)
+    float esum = 0.0f, ecomp = 0.0f;         // squared residuals (eval), Kahan over observed steps
+    for (int k = 0;; ++k) {
+        if (f.ckpt && k == next_ck && k < sc.K) {
+            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                store_pair(base, q, st[p].ph, vx[p], vy[p]);
+                store_pair(base + (size_t)Ns, q, st[p].pl, vx[p], vy[p]);
+                store_pair(base + 2 * (size_t)Ns, q, st[p].v, vx[p], vy[p]);
+                store_pair(base + 3 * (size_t)Ns, q, st[p].gap, vx[p], vy[p]);
+            }
+            next_ck += a.C;
+            ++ck_idx;
+        }
+        if (f.traj || f.vtraj) {
+            const size_t row = sc.traj_off + (size_t)k * Ns + wl;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int q = 64 * p + 2 * lane;
+                if (f.traj) store_pair(a.traj + row, q, position2(st[p]), vx[p], vy[p]);
+                if (f.vtraj) store_pair(a.vtraj + row, q, st[p].v, vx[p], vy[p]);
+            }
+        }
+        if (f.eval && k == obs_k) {
+            if (obs_row < sc.n_obs) {
+                const float *y = a.eval_targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
+                f2 e = F2(0.0f);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    f2 r = residual2(st[p], load_pair(y, 64 * p + 2 * lane, vx[p], vy[p]));
+                    r.x = vx[p] ? r.x : 0.0f;
+                    r.y = vy[p] ? r.y : 0.0f;
+                    e = fma2(r, r, e);
+                }
+                kahan_add(esum, ecomp, __fadd_rn(e.x, e.y));
+            }
+            obs_k += sc.obs_stride;
+            ++obs_row;
+        }
+        if (k == sc.K) break;
+
+        f2 vcur[NP], vh[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
+        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
+        leader_vals2<NP>(vcur, vh, lane, lead_in);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+            euler2(st[p], as, vh[p], sc.dt);
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (vx[p] && !(isfinite(st[p].v.x) && isfinite(st[p].ph.x))) bad = true;
+        if (vy[p] && !(isfinite(st[p].v.y) && isfinite(st[p].ph.y))) bad = true;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (f.eval) {
+        const double part = warp_sum_double((double)esum - (double)ecomp) * (double)sc.inv_nobs;
+        if (lane == 0) a.eval_part[(size_t)s_idx * g.G + g.w] = part;
+    }
+}
+
+}  // namespace idm

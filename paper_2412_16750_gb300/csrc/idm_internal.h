@@ -90,6 +90,17 @@ int backward_max_warps(int vpt, int G);
 // Adjoint warps per SM the register budgets allow for a shape.
 int backward_resident_warps(int vpt, int G);
 cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st);
+// Single-launch fit (idm_fused.cuh): every Adam iteration of every segment
+// in one persistent launch of the adjoint's shape (vpt, G, wpb, tape depth
+// and prefetch of `a`); loss partial of iteration it at
+// loss_part[it * part_stride + ...].  The grid is capped at the resident
+// blocks.
+cudaError_t launch_fit_fused(int vpt, int G, const SimArgs &a, long long part_stride, int grid, int wpb,
+                             cudaStream_t st);
+// Losses of iterations 0..n_iter-1 of a single-launch fit into out[n_iter],
+// each summed in the order of launch_loss_finalize.
+cudaError_t launch_loss_finalize_iters(const double *loss_part, long long stride, const int *n_seg, int per_seg,
+                                       int n_iter, double *out, cudaStream_t st);
 int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem,
                      bool sub = false);
 // Adjoint kernel variants (idm_adjoint{2,4,8}.cu): dense or target seeds,
@@ -98,6 +109,11 @@ int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, 
 void *backward_fn_vpt2(bool dense, bool adam, bool wd, bool big, bool sub);
 void *backward_fn_vpt4(bool dense, bool adam, bool wd, bool big, bool sub);
 void *backward_fn_vpt8(bool dense, bool adam, bool wd, bool big, bool sub);
+// Single-launch fit variants (idm_fused{2,4,8}.cu): 8-warp block form (4
+// vehicles/thread only), tape blocks with sub-checkpoints.
+void *fused_fn_vpt2(bool big, bool sub);
+void *fused_fn_vpt4(bool big, bool sub);
+void *fused_fn_vpt8(bool big, bool sub);
 
 // Layout (idm_layout.cu).
 cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,

@@ -16,7 +16,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "idm_sim_common.cuh"
+#include "idm_forward.cuh"
 
 namespace idm {
 
@@ -138,92 +138,6 @@ cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *s
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Forward: K steps per segment, optional trajectory / speed output,
-// checkpoints every C steps.  (The squared-error loss is accumulated by the
-// adjoint's recompute, which evaluates the residuals anyway.)
-// ---------------------------------------------------------------------------
-struct FwdFlags {
-    bool traj, vtraj, ckpt, eval;
-};
-
-template <int NP, bool D4>
-__device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
-                                                const VehConst2 (&kc)[NP], State2 (&st)[NP], const bool (&vx)[NP],
-                                                const bool (&vy)[NP], FwdFlags f)
-{
-    const int lane = g.lane;
-    const int Ns = sc.n_veh;
-    const int wl = lb + g.w * 64 * NP;  // scenario-local index of this warp's first slot
-    int next_ck = 0, ck_idx = 0;
-    int xp = 0;
-    int obs_k = sc.obs_stride, obs_row = 0;  // next observed step and its target row (eval)
-    float esum = 0.0f, ecomp = 0.0f;         // squared residuals (eval), Kahan over observed steps
-    for (int k = 0;; ++k) {
-        if (f.ckpt && k == next_ck && k < sc.K) {
-            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int q = 64 * p + 2 * lane;
-                store_pair(base, q, st[p].ph, vx[p], vy[p]);
-                store_pair(base + (size_t)Ns, q, st[p].pl, vx[p], vy[p]);
-                store_pair(base + 2 * (size_t)Ns, q, st[p].v, vx[p], vy[p]);
-                store_pair(base + 3 * (size_t)Ns, q, st[p].gap, vx[p], vy[p]);
-            }
-            next_ck += a.C;
-            ++ck_idx;
-        }
-        if (f.traj || f.vtraj) {
-            const size_t row = sc.traj_off + (size_t)k * Ns + wl;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int q = 64 * p + 2 * lane;
-                if (f.traj) store_pair(a.traj + row, q, position2(st[p]), vx[p], vy[p]);
-                if (f.vtraj) store_pair(a.vtraj + row, q, st[p].v, vx[p], vy[p]);
-            }
-        }
-        if (f.eval && k == obs_k) {
-            if (obs_row < sc.n_obs) {
-                const float *y = a.eval_targets + sc.tgt_off + (size_t)obs_row * Ns + wl;
-                f2 e = F2(0.0f);
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    f2 r = residual2(st[p], load_pair(y, 64 * p + 2 * lane, vx[p], vy[p]));
-                    r.x = vx[p] ? r.x : 0.0f;
-                    r.y = vy[p] ? r.y : 0.0f;
-                    e = fma2(r, r, e);
-                }
-                kahan_add(esum, ecomp, __fadd_rn(e.x, e.y));
-            }
-            obs_k += sc.obs_stride;
-            ++obs_row;
-        }
-        if (k == sc.K) break;
-
-        f2 vcur[NP], vh[NP];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
-        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
-        leader_vals2<NP>(vcur, vh, lane, lead_in);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
-            euler2(st[p], as, vh[p], sc.dt);
-        }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        if (vx[p] && !(isfinite(st[p].v.x) && isfinite(st[p].ph.x))) bad = true;
-        if (vy[p] && !(isfinite(st[p].v.y) && isfinite(st[p].ph.y))) bad = true;
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
-    if (f.eval) {
-        const double part = warp_sum_double((double)esum - (double)ecomp) * (double)sc.inv_nobs;
-        if (lane == 0) a.eval_part[(size_t)s_idx * g.G + g.w] = part;
-    }
-}
-
 template <int VPT>
 __global__ void __launch_bounds__(512)
 forward_kernel(SimArgs a, FwdFlags f)
@@ -275,6 +189,38 @@ loss_finalize_kernel(const double *part, const int *n_seg, int per_seg, double *
 cudaError_t launch_loss_finalize(const double *loss_part, const int *n_seg, int per_seg, double *out, cudaStream_t st)
 {
     loss_finalize_kernel<<<1, 1024, 0, st>>>(loss_part, n_seg, per_seg, out);
+    return cudaGetLastError();
+}
+
+// The losses of all iterations of a single-launch fit: block it sums the
+// partials of iteration it in the order of loss_finalize_kernel, so each
+// value equals that of the per-iteration reduction.
+__global__ void __launch_bounds__(1024)
+loss_finalize_iters_kernel(const double *part, long long stride, const int *n_seg, int per_seg, double *out)
+{
+    __shared__ double sh[1024];
+    const long long n = (long long)*n_seg * per_seg;
+    if (n > stride) {  // flagged by the fit kernel
+        if (threadIdx.x == 0) out[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const double *pi = part + (size_t)blockIdx.x * (size_t)stride;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += pi[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_loss_finalize_iters(const double *loss_part, long long stride, const int *n_seg, int per_seg,
+                                       int n_iter, double *out, cudaStream_t st)
+{
+    if (n_iter < 1) return cudaSuccess;
+    loss_finalize_iters_kernel<<<n_iter, 1024, 0, st>>>(loss_part, stride, n_seg, per_seg, out);
     return cudaGetLastError();
 }
 
@@ -348,6 +294,40 @@ cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool wan
     args.G = G;
     void *params[] = {&args};
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
+}
+
+// Single-launch fit kernels live in idm_fused{2,4,8}.cu.
+static void *fused_fn_v(int vpt, int wpb, bool sub)
+{
+    switch (vpt) {
+    case 2: return fused_fn_vpt2(false, sub);
+    case 4: return fused_fn_vpt4(wpb > 4, sub);
+    case 8: return fused_fn_vpt8(false, sub);
+    }
+    return nullptr;
+}
+
+cudaError_t launch_fit_fused(int vpt, int G, const SimArgs &a, long long part_stride, int grid, int wpb,
+                             cudaStream_t st)
+{
+    if (wpb > backward_max_warps(vpt, G) || wpb % G) return cudaErrorInvalidValue;
+    void *fn = fused_fn_v(vpt, wpb, a.tape_T < a.C);
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = backward_smem_bytes(vpt, false, a.tape_T, G, wpb, a.bwd_pf != 0);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * wpb, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int cap = n_sm * (occ > 0 ? occ : 1);
+    SimArgs args = a;
+    args.G = G;
+    long long stride = part_stride;
+    void *params[] = {&args, &stride};
+    return cudaLaunchKernel(fn, dim3(grid < cap ? grid : cap), dim3(32 * wpb), params, smem, st);
 }
 
 int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool want_delta, int wpb, size_t smem,

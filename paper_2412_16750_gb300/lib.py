@@ -27,6 +27,10 @@ IDM_STATUS_TIMEOUT = 8
 IDM_STATUS_BAD_OBS = 16
 IDM_STATUS_BAD_LANES = 32
 
+IDM_FIT_AUTO = 0
+IDM_FIT_GRAPH = 1
+IDM_FIT_SINGLE_LAUNCH = 2
+
 IDM_MLP_IN = 80
 IDM_MLP_HIDDEN = 256
 IDM_MLP_OUT = 5
@@ -90,6 +94,7 @@ _SIGS = {
                                      ctypes.POINTER(idm_params_t), _vp, _vp, _vp]),
     "idm_gather_rows": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp]),
     "idm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "idm_set_fit_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
     "idm_phase_times": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int32)]),
     "idm_batch_sizes": (ctypes.c_int, [ctypes.POINTER(idm_batch_t), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
@@ -262,6 +267,10 @@ def idm_gather_rows(ctx, N, n_rows, perm, src, dst, stream=None):
 
 def idm_set_profiling(ctx, on):
     return check(ctx, load().idm_set_profiling(ctx, 1 if on else 0))
+
+
+def idm_set_fit_mode(ctx, mode):
+    return check(ctx, load().idm_set_fit_mode(ctx, int(mode)))
 
 
 def idm_phase_times(ctx, stream=None):

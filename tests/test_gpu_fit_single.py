@@ -1,0 +1,170 @@
+"""The Adam fit (Sec. IV-A, V-B) as one persistent launch
+(IDM_FIT_SINGLE_LAUNCH) against the per-iteration CUDA graph
+(IDM_FIT_GRAPH).  Both run the same forward and adjoint arithmetic per
+segment and iteration, and the loss history is reduced in the same fixed
+order, so parameters and history must agree BIT FOR BIT: across kernel
+shapes (2, 4 and 8 vehicles per thread; 1 to 8 warps per segment, including
+the 8-warp block form), a tape shallower than the checkpoint interval (tape
+blocks restarted from sub-checkpoints), ragged and empty lanes, delta != 4
+in some segments, an observation stride, K not a multiple of the interval,
+and more segments than resident warp groups.  The single launch is also
+compared with the FP64 oracle's fit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_16750_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = float(np.float32(0.1))
+A_MIN = -10.0
+EDGE_COUNTS = [1, 2, 3, 33, 0, 17, 31, 32, 1, 5, 0, 63, 64, 7]   # up to the 64 slots of 2 x 1 warp
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_16750_gb300 import api as _api
+    return _api
+
+
+def cuda(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def targets(sc, K, s, rng):
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    n_obs = K // s
+    return synth.f32(P[s::s][:n_obs] + rng.normal(0, 0.5, size=(n_obs, P.shape[1])))
+
+
+def fit_both(api, sc, th0, Y, K, s, n_iter, tuning):
+    out = {}
+    for mode in ("graph", "single"):
+        ctx = api.Context(*tuning)
+        ctx.set_fit_mode(mode)
+        th = cuda(th0)
+        scn = api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+        hist = api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT, cuda(Y), s, n_iter, 0.1, 0.01,
+                       synth.BOX_LO, synth.BOX_HI, A_MIN, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.check_status() == 0
+        out[mode] = (th.cpu().numpy(), hist.cpu().numpy())
+    return out
+
+
+def mixed_delta(sc, rng):
+    """theta_true with delta != 4 in a few lanes (segments take the general
+    power; the others keep the delta = 4 specialisation)."""
+    th = sc["theta_true"].copy()
+    lo = sc["lane_off"]
+    for l in rng.choice(len(lo) - 1, size=3, replace=False):
+        th[5, lo[l]:lo[l + 1]] = 3.5
+    return th
+
+
+# (workspace cap, vpt, warps per segment, checkpoint interval, warps per block)
+SHAPES = [
+    (0, 2, 1, 1, 8),
+    (0, 2, 2, 7, 8),
+    (0, 4, 1, 8, 4),
+    (0, 4, 4, 16, 8),
+    (0, 4, 8, 5, 8),    # 8-warp block form
+    (0, 8, 2, 3, 8),
+    (0, 8, 8, 8, 8),
+    (0, 0, 0, 64, 8),   # tape shallower than the interval: sub-checkpoints
+]
+
+
+@pytest.mark.parametrize("tuning", SHAPES)
+def test_single_launch_equals_graph(api, tuning):
+    rng = np.random.default_rng(300)
+    sc = synth.make_scene(EDGE_COUNTS, rng)
+    N = int(sc["lane_off"][-1])
+    th0 = mixed_delta(sc, rng) * np.r_[rng.uniform(0.8, 1.2, size=(5, N)), np.ones((1, N))]
+    th0 = synth.f32(th0)
+    K, s, n_iter = 37, 3, 6
+    Y = targets(sc, K, s, rng)
+    out = fit_both(api, sc, th0, Y, K, s, n_iter, tuning)
+    np.testing.assert_array_equal(out["single"][0], out["graph"][0])
+    np.testing.assert_array_equal(out["single"][1], out["graph"][1])
+    assert not np.array_equal(out["single"][0], th0)  # the fit moved the parameters
+
+
+def test_single_launch_many_segments(api):
+    """5,000 one-lane segments (lanes of 40 vehicles, 64-slot segments) for
+    at most 2,432 resident single-warp groups: groups take several segments,
+    each through all iterations."""
+    rng = np.random.default_rng(301)
+    sc = synth.make_scene([40] * 5000, rng)
+    th0 = synth.plain_init(int(sc["lane_off"][-1]))
+    K, s, n_iter = 20, 1, 4
+    Y = targets(sc, K, s, rng)
+    out = fit_both(api, sc, th0, Y, K, s, n_iter, (0, 2, 1, 8, 8))
+    np.testing.assert_array_equal(out["single"][0], out["graph"][0])
+    np.testing.assert_array_equal(out["single"][1], out["graph"][1])
+
+
+def test_single_launch_against_oracle(api):
+    rng = np.random.default_rng(302)
+    sc = synth.make_scene(EDGE_COUNTS, rng)
+    N = int(sc["lane_off"][-1])
+    th0 = synth.f32(mixed_delta(sc, rng))
+    th0[:5] = synth.plain_init(N)[:5]
+    K, s, n_iter = 41, 2, 5
+    Y = targets(sc, K, s, rng)
+    th_ref, hist_ref = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, DT, Y, s, n_iter,
+                                  0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    ctx = api.Context(vpt=4, warps_per_segment=2, ckpt_interval=6)
+    ctx.set_fit_mode("single")
+    th = cuda(th0)
+    scn = api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+    hist = api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT, cuda(Y), s, n_iter, 0.1, 0.01,
+                   synth.BOX_LO, synth.BOX_HI, A_MIN, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.check_status() == 0
+    np.testing.assert_allclose(hist.cpu().numpy(), hist_ref, rtol=1e-5)
+    np.testing.assert_allclose(th.double().cpu().numpy(), th_ref, rtol=1e-4, atol=1e-5)
+
+
+def test_fit_mode_argument(api):
+    from paper_2412_16750_gb300 import lib
+    ctx = api.Context()
+    with pytest.raises(lib.IdmError):
+        lib.idm_set_fit_mode(ctx.handle, 7)
+    ctx.set_fit_mode("auto")
+
+
+@pytest.mark.parametrize("mode", ["graph", "single"])
+def test_horizon_within_one_interval_skips_forward(api, mode):
+    """K <= C: after the first iteration the forward is skipped (its only
+    checkpoint is the initial state).  idm_fit_eval always runs the forward
+    (it scores every iterate), so equal parameters and history show the skip
+    changes nothing; and the fit agrees with the oracle."""
+    rng = np.random.default_rng(303)
+    sc = synth.make_scene(EDGE_COUNTS, rng)
+    N = int(sc["lane_off"][-1])
+    th0 = synth.plain_init(N)
+    K, s, n_iter = 12, 1, 6
+    Y = targets(sc, K, s, rng)
+    scn = api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+    res = []
+    for ev in (None, cuda(Y)):
+        ctx = api.Context(0, 2, 2, 16, 8)
+        ctx.set_fit_mode(mode)
+        th = cuda(th0)
+        out = api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT, cuda(Y), s, n_iter, 0.1, 0.01,
+                      synth.BOX_LO, synth.BOX_HI, A_MIN, ctx=ctx, eval_targets=ev)
+        hist = out if ev is None else out[0]
+        torch.cuda.synchronize()
+        assert ctx.check_status() == 0
+        res.append((th.cpu().numpy(), hist.cpu().numpy()))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    th_ref, hist_ref = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, DT, Y, s, n_iter,
+                                  0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    np.testing.assert_allclose(res[0][1], hist_ref, rtol=1e-5)
+    np.testing.assert_allclose(res[0][0], th_ref, rtol=1e-4, atol=1e-5)
