@@ -399,6 +399,7 @@ def time_to_fit(a, dev):
         th_buf.copy_(plain)
         _, fit_ms = timed(lambda: api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx))
     ms_iter = fit_ms / a.fit_iters
+    fit_form = ctx.last_fit_form()
 
     def first_below(ev_hist):
         rmse = np.sqrt(ev_hist.cpu().numpy() / N)
@@ -426,7 +427,7 @@ def time_to_fit(a, dev):
     wall = lambda it, extra: (extra + it * ms_iter) / 1e3 if it is not None else None
     out["fit"] = {"workload": "2000 lanes x 100 vehicles (200K), 100 steps, every step observed, noise 0.5 m; "
                               "Adam %d iterations, lr 0.1 -> 0.01" % a.fit_iters,
-                  "rmse_target_m": a.rmse_target, "ms_per_iteration": ms_iter,
+                  "rmse_target_m": a.rmse_target, "ms_per_iteration": ms_iter, "fit_form": fit_form,
                   "shape": {"vpt": shape[0], "warps_per_segment": shape[1], "ckpt_interval": shape[2],
                             "warps_per_block": shape[3], "source": shape_src},
                   "plain": {"iterations": it_plain, "seconds": wall(it_plain, 0.0),
@@ -780,6 +781,7 @@ def prediction(a, dev):
                                            "foot point, squared distance, compare); two projection launches"},
            "ade_m": float(sums[0] / N), "fde_m": float(sums[1] / N), "miss_rate_2m": float(sums[2] / N),
            "final_loss": float(out["loss"][-1].item()), "fit_shape": list(ctx.tuning),
+           "fit_form": ctx.last_fit_form(),
            "paper": "WOMD validation: minADE 7.862 m, minFDE 15.668 m, miss rate 0.586 (Table II)"}
     ctx.close()
     return res

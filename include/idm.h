@@ -140,6 +140,11 @@ int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_inte
 #define IDM_FIT_SINGLE_LAUNCH 2
 int idm_set_fit_mode(idm_ctx_t *ctx, int mode);
 
+/* The form the last idm_fit / idm_fit_eval on this context ran in
+ * (IDM_FIT_GRAPH or IDM_FIT_SINGLE_LAUNCH); 0 before the first fit or for a
+ * NULL context. */
+int idm_last_fit_form(const idm_ctx_t *ctx);
+
 /* Longest lane the library can simulate (vehicles): 32 * 8 * 8 = 2048. */
 int idm_max_lane_supported(void);
 

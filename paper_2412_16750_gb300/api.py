@@ -37,6 +37,11 @@ class Context:
         lib.idm_set_fit_mode(self.handle, code)
         self.fit_mode = mode
 
+    def last_fit_form(self):
+        """"graph" or "single" for the last fit on this context (None before one)."""
+        return {lib.IDM_FIT_GRAPH: "graph", lib.IDM_FIT_SINGLE_LAUNCH: "single"}.get(
+            lib.idm_last_fit_form(self.handle))
+
     def status(self, stream=None):
         rc, flags = lib.idm_status(self.handle, stream or torch.cuda.current_stream())
         return rc, flags
@@ -582,10 +587,13 @@ def predict_rollout(lanes, x_hist, y_hist, lane_lo, lane_hi, dt, n_fut, n_iter=5
     p0, v0 = rollout_state(s_sorted, 0, 1, dt, ctx=ctx)
     theta = torch.tensor(theta0, dtype=torch.float32, device="cuda")[:, None].repeat(1, N).contiguous()
     if tune:
+        # time what runs: a short fit (the shape decides its form and tape
+        # depth as well as the per-step cost), on a scratch copy
         from . import tune as _tune
-        sig = _tune.signature(scene.max_lane, N, H - 1, 1, kind="predict")
-        _tune.tuned(ctx, lambda c: loss_grad(theta, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, a_min, ctx=c),
-                    scene.max_lane, sig)
+        sig = _tune.signature(scene.max_lane, N, H - 1, 1, kind="predict-fit")
+        scratch = theta.clone()
+        _tune.tuned(ctx, lambda c: fit(scratch, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, 20, lr0, lr1, box_lo,
+                                       box_hi, a_min, ctx=c), scene.max_lane, sig)
     hist = fit(theta, p0, v0, scene, H - 1, dt, s_sorted[1:], 1, n_iter, lr0, lr1, box_lo, box_hi, a_min, ctx=ctx)
     pr, vr = rollout_state(s_sorted, H - 2, H - 1, dt, ctx=ctx)
     traj = simulate(theta, pr, vr, scene, n_fut, dt, a_min, ctx=ctx)

@@ -155,7 +155,10 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     if ((rc = ensure(c, c->g0, sizeof(float) * (size_t)N, "initial gaps"))) return rc;
     if ((rc = ensure(c, c->loss_part, sizeof(double) * (size_t)L * G, "loss partials"))) return rc;
     if ((rc = ensure(c, c->loss_tmp, sizeof(double) * 2, "loss scalar"))) return rc;
-    const int n_ck = (sim->K + c->C - 1) / c->C;
+    // an interval longer than the horizon gives the same single checkpoint
+    // segment; clamping it lets the adjoint's tape be only K steps deep
+    const int C = std::min(c->C, sim->K);
+    const int n_ck = (sim->K + C - 1) / C;
     if (need_ckpt && (rc = ensure(c, c->ckpt, sizeof(float) * 4 * (size_t)n_ck * N, "checkpoints"))) return rc;
 
     SimArgs &a = P->a;
@@ -180,7 +183,7 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     a.v_init = v_init;
     a.loss_part = (double *)c->loss_part.p;
     a.ckpt = (float *)c->ckpt.p;
-    a.C = c->C;
+    a.C = C;
     a.status = (unsigned *)c->status.p;
     a.N_total = N;
     a.G = G;
@@ -239,7 +242,8 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     // tape depth: the checkpoint interval, or less when a deeper tape would
     // cost resident groups (blocks inside a checkpoint segment then restart
     // from sub-checkpoints written by an extra forward pass)
-    int T = c->C;
+    const int C = P->a.C;  // the call's checkpoint interval (at most its longest horizon)
+    int T = C;
     const size_t want = std::min(reg_cap, std::max<size_t>(groups_per_sm(1, false), 1));
     while (T > 1 && groups_per_sm(T, false) < want) --T;
     if (groups_per_sm(T, false) == 0)
@@ -249,8 +253,8 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     const bool pf = groups_per_sm(T, true) >= std::min(reg_cap, groups_per_sm(T, false));
     P->a.bwd_pf = pf ? 1 : 0;
     P->a.tape_T = T;
-    if (T < c->C) {
-        const size_t rows = (size_t)((c->C + T - 1) / T - 1);
+    if (T < C) {
+        const size_t rows = (size_t)((C + T - 1) / T - 1);
         int rc;
         if ((rc = ensure(c, c->sub_ckpt, sizeof(float) * 4 * rows * (size_t)std::max(P->a.N_total, 1),
                          "sub-checkpoints")))
@@ -264,7 +268,7 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     groups = std::max(1, std::min(groups, idm::backward_max_warps(P->vpt, G) / G));
     P->wpb_b = groups * G;
     size_t smem = per_group * groups;
-    int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem, T < c->C);
+    int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem, T < C);
     int blocks_needed = (L * G + P->wpb_b - 1) / P->wpb_b;
     P->grid_b = std::min(blocks_needed, c->n_sm * occ_b);
     P->grid_b = P->grid_b < 1 ? 1 : P->grid_b;
@@ -308,7 +312,7 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     // With every horizon within one checkpoint interval the only checkpoint
     // is the initial state, which no iteration changes: the forward runs in
     // the first iteration only (the adjoint recomputes the steps itself).
-    const bool fwd_once = !eval && P.k_max <= c->C;
+    const bool fwd_once = !eval && P.k_max <= P.a.C;
     key.fwd_once = fwd_once;
     key.hist = loss_hist;
     key.eval_targets = eval ? eval_targets : nullptr;
@@ -496,14 +500,17 @@ int idm_set_fit_mode(idm_ctx_t *c, int mode)
     return IDM_OK;
 }
 
+int idm_last_fit_form(const idm_ctx_t *c) { return c ? c->last_fit_form : 0; }
+
 size_t idm_workspace_bytes(const idm_ctx_t *c, const idm_scene_t *s, const idm_sim_t *sim)
 {
     if (!c || !s || !sim || sim->K < 1) return 0;
     size_t N = (size_t)s->n_vehicles, L = (size_t)s->n_lanes;
-    size_t n_ck = (size_t)((sim->K + c->C - 1) / c->C);
+    const int C = std::min(c->C, sim->K);
+    size_t n_ck = (size_t)((sim->K + C - 1) / C);
     // sub-checkpoints when the adjoint's tape is shallower than the interval
     // (at most ceil(C/2) - 1 rows; typically none for C <= 8)
-    const size_t sub = c->C > 8 ? (size_t)((c->C + 1) / 2 - 1) : 0;
+    const size_t sub = C > 8 ? (size_t)((C + 1) / 2 - 1) : 0;
     return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + 16 * n_ck * N + 16 * sub * N;
 }
 
@@ -671,6 +678,7 @@ int idm_fit_eval(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, c
                         (c->fit_mode == IDM_FIT_SINGLE_LAUNCH ||
                          (c->fit_mode == IDM_FIT_AUTO &&
                           (sim->K <= c->C || vehicle_steps <= IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS)));
+    c->last_fit_form = single ? IDM_FIT_SINGLE_LAUNCH : IDM_FIT_GRAPH;
     if (single)
         return run_fit_single(c, P, n_iter, (size_t)scene->n_vehicles, scene->n_lanes, box_lo, box_hi, lr0, lr1,
                               loss_hist, st);

@@ -18,6 +18,95 @@ namespace idm {
 // The six factored gradient sums of each slot accumulate in registers over
 // all steps.
 // ---------------------------------------------------------------------------
+// Epilogue of a segment: the parameter gradients from the six factored
+// sums, then either their output or (fit) the Adam update with the box
+// projection in place.  Adam is taken in the reordered form of Kingma & Ba
+// (2015, Sec. 2): with alpha_t = lr sqrt(1 - beta2^t) / (1 - beta1^t) and
+// eps_t = eps sqrt(1 - beta2^t), theta -= alpha_t m / (sqrt(v) + eps_t) is
+// the bias-corrected step with its per-iteration factors computed once per
+// thread.  Every load of a slot is issued before the slot's stores: the
+// parameter and moment arrays may alias as far as the compiler knows, so a
+// store would otherwise hold back each later load for a full memory round
+// trip (this epilogue was half of a short-horizon fit iteration).
+template <int NP, bool ADAM, bool WD>
+__device__ __forceinline__ void segment_epilogue(const SimArgs &a, const Seg &sg, int lane, int wb,
+                                                 const VehConst2 (&kc)[NP], const f2 (&sacc)[6][NP],
+                                                 const f2 (&lp)[NP], const f2 (&lv)[NP], const bool (&vx)[NP],
+                                                 const bool (&vy)[NP])
+{
+    float step_t = 0.0f, eps_t = 0.0f;
+    if (ADAM) {
+        const int it = a.iter;
+        const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
+        const float bc1 = 1.0f - powf(0.9f, (float)(it + 1)), bc2 = 1.0f - powf(0.999f, (float)(it + 1));
+        const float sb2 = sqrtf(bc2);
+        step_t = lr * sb2 / bc1;
+        eps_t = 1e-8f * sb2;
+    }
+    float *const th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
+                          const_cast<float *>(a.am), const_cast<float *>(a.b)};
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(c ? vy[p] : vx[p])) continue;
+            const int gi = sg.veh_begin + wb + 64 * p + 2 * lane + c;
+            // this slot's loads, all ahead of its stores
+            float tv[5], mm[5], vm[5];
+            if (ADAM) {
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const size_t mi = (size_t)r * a.N_total + gi;
+                    tv[r] = th[r][gi];
+                    mm[r] = a.adam_m[mi];
+                    vm[r] = a.adam_v[mi];
+                }
+            } else {
+                tv[0] = a.v0[gi];
+                tv[4] = a.b[gi];
+            }
+            const float v0 = tv[0], b = tv[4];
+            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
+            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
+            const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
+            const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
+            const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
+            float gr[6];
+            gr[0] = am * dl * A4 / v0;                 // v0
+            gr[1] = -A1;                               // T
+            gr[2] = -A0;                               // s0
+            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
+            gr[4] = A2 * cc / (2.0f * b);              // b
+            gr[5] = -am * A5;                          // delta
+#pragma unroll
+            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
+            if (ADAM) {
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const size_t mi = (size_t)r * a.N_total + gi;
+                    const float m = 0.9f * mm[r] + 0.1f * gr[r];
+                    const float vv = 0.999f * vm[r] + 0.001f * gr[r] * gr[r];
+                    a.adam_m[mi] = m;
+                    a.adam_v[mi] = vv;
+                    const float x = tv[r] - step_t * m / (sqrtf(vv) + eps_t);
+                    th[r][gi] = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
+                }
+            } else {
+                if (a.g_v0) a.g_v0[gi] = gr[0];
+                if (a.g_T) a.g_T[gi] = gr[1];
+                if (a.g_s0) a.g_s0[gi] = gr[2];
+                if (a.g_am) a.g_am[gi] = gr[3];
+                if (a.g_b) a.g_b[gi] = gr[4];
+                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
+                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
+                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
+            }
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+}
+
 template <int NP, bool DENSE, bool ADAM, bool WD, bool D4>
 __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDesc &sc, const Seg &sg, int s_idx, int lb,
                                                  Grp &g, float *tv, const VehConst2 (&kc)[NP], State2 (&st)[NP],
@@ -247,60 +336,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         grp_sync(g);  // the tape may be overwritten by the next segment
     }
 
-    // epilogue: parameter gradients from the factored sums
-    bool bad = false;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!(c ? vy[p] : vx[p])) continue;
-            const int q = wb + 64 * p + 2 * lane + c;
-            const int gi = sg.veh_begin + q;
-            const float v0 = a.v0[gi], b = a.b[gi];
-            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
-            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
-            const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
-            const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
-            const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
-            float gr[6];
-            gr[0] = am * dl * A4 / v0;                 // v0
-            gr[1] = -A1;                               // T
-            gr[2] = -A0;                               // s0
-            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
-            gr[4] = A2 * cc / (2.0f * b);              // b
-            gr[5] = -am * A5;                          // delta
-            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
-            if (ADAM) {
-                const int it = a.iter;
-                const int t = it + 1;
-                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
-                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
-                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
-                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
-#pragma unroll
-                for (int r = 0; r < 5; ++r) {
-                    const size_t mi = (size_t)r * a.N_total + gi;
-                    float m = 0.9f * a.adam_m[mi] + 0.1f * gr[r];
-                    float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[r] * gr[r];
-                    a.adam_m[mi] = m;
-                    a.adam_v[mi] = vv;
-                    float x = th[r][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
-                    x = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
-                    th[r][gi] = x;
-                }
-            } else {
-                if (a.g_v0) a.g_v0[gi] = gr[0];
-                if (a.g_T) a.g_T[gi] = gr[1];
-                if (a.g_s0) a.g_s0[gi] = gr[2];
-                if (a.g_am) a.g_am[gi] = gr[3];
-                if (a.g_b) a.g_b[gi] = gr[4];
-                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
-                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
-                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
-            }
-        }
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {
         const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
         if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
@@ -615,60 +651,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
       }
     }
 
-    // epilogue: parameter gradients from the factored sums
-    bool bad = false;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!(c ? vy[p] : vx[p])) continue;
-            const int q = wb + 64 * p + 2 * lane + c;
-            const int gi = sg.veh_begin + q;
-            const float v0 = a.v0[gi], b = a.b[gi];
-            const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
-            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
-            const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
-            const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
-            const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
-            float gr[6];
-            gr[0] = am * dl * A4 / v0;                 // v0
-            gr[1] = -A1;                               // T
-            gr[2] = -A0;                               // s0
-            gr[3] = A3 + A2 * cc / (2.0f * am);        // a_max
-            gr[4] = A2 * cc / (2.0f * b);              // b
-            gr[5] = -am * A5;                          // delta
-            for (int r = 0; r < 6; ++r) bad |= !isfinite(gr[r]);
-            if (ADAM) {
-                const int it = a.iter;
-                const int t = it + 1;
-                const float lr = a.n_iter > 1 ? a.lr0 + (a.lr1 - a.lr0) * (float)it / (float)(a.n_iter - 1) : a.lr0;
-                const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
-                float *th[5] = {const_cast<float *>(a.v0), const_cast<float *>(a.T), const_cast<float *>(a.s0),
-                                const_cast<float *>(a.am), const_cast<float *>(a.b)};
-#pragma unroll
-                for (int r = 0; r < 5; ++r) {
-                    const size_t mi = (size_t)r * a.N_total + gi;
-                    float m = 0.9f * a.adam_m[mi] + 0.1f * gr[r];
-                    float vv = 0.999f * a.adam_v[mi] + 0.001f * gr[r] * gr[r];
-                    a.adam_m[mi] = m;
-                    a.adam_v[mi] = vv;
-                    float x = th[r][gi] - lr * (m / bc1) / (sqrtf(vv / bc2) + 1e-8f);
-                    x = fminf(fmaxf(x, a.lo[r]), a.hi[r]);
-                    th[r][gi] = x;
-                }
-            } else {
-                if (a.g_v0) a.g_v0[gi] = gr[0];
-                if (a.g_T) a.g_T[gi] = gr[1];
-                if (a.g_s0) a.g_s0[gi] = gr[2];
-                if (a.g_am) a.g_am[gi] = gr[3];
-                if (a.g_b) a.g_b[gi] = gr[4];
-                if (a.g_delta) a.g_delta[gi] = WD ? gr[5] : 0.0f;
-                if (a.g_p_init) a.g_p_init[gi] = c ? lp[p].y : lp[p].x;
-                if (a.g_v_init) a.g_v_init[gi] = c ? lv[p].y : lv[p].x;
-            }
-        }
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {
         const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
         if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;

@@ -142,7 +142,12 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
         return fail(c, IDM_ERR_ARG, "a lane has %d vehicles, more than %d", max_lane, idm_max_lane_supported());
     if ((rc = pick_shape(c, max_lane, &Pp->vpt, &Pp->G))) return rc;
     const int G = Pp->G;
-    plan_batch(b, c->C, 32 * Pp->vpt * G, BP);
+    // the checkpoint interval, at most the longest horizon (same segments,
+    // shallower adjoint tape)
+    int max_K = 1;
+    for (int s = 0; s < b->n_scen; ++s) max_K = std::max(max_K, b->K[s]);
+    const int C = std::min(c->C, max_K);
+    plan_batch(b, C, 32 * Pp->vpt * G, BP);
     const int N = b->n_vehicles, L = b->n_lanes, S = b->n_scen;
     const size_t n_seg = BP.seg.size();
     if ((rc = ensure(c, c->seg, sizeof(Seg) * std::max<size_t>(n_seg, 1), "segments"))) return rc;
@@ -177,7 +182,7 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
     a.v_init = v_init;
     a.loss_part = (double *)c->loss_part.p;
     a.ckpt = (float *)c->ckpt.p;
-    a.C = c->C;
+    a.C = C;
     a.status = (unsigned *)c->status.p;
     a.N_total = N;
     a.G = G;

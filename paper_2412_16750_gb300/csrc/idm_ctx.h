@@ -52,6 +52,7 @@ struct idm_ctx {
     idm::abi::Buf rec_oyy, rec_oyc, rec_multi, rec_tape, rec_mom, rec_thm, rec_acc, rec_kmax;  // reconstruction mode
     idm::abi::Buf fit_part;            // single-launch fit: loss partials of every iteration
     int fit_mode = IDM_FIT_AUTO;
+    int last_fit_form = 0;             // IDM_FIT_GRAPH or IDM_FIT_SINGLE_LAUNCH of the last idm_fit (0: none)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t fit_exec = nullptr;
     unsigned char fit_key[640] = {0};  // arguments the cached fit graph was captured with

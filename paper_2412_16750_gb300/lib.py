@@ -95,6 +95,7 @@ _SIGS = {
     "idm_gather_rows": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp]),
     "idm_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "idm_set_fit_mode": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "idm_last_fit_form": (ctypes.c_int, [_vp]),
     "idm_phase_times": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int32)]),
     "idm_batch_sizes": (ctypes.c_int, [ctypes.POINTER(idm_batch_t), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
@@ -271,6 +272,10 @@ def idm_set_profiling(ctx, on):
 
 def idm_set_fit_mode(ctx, mode):
     return check(ctx, load().idm_set_fit_mode(ctx, int(mode)))
+
+
+def idm_last_fit_form(ctx):
+    return load().idm_last_fit_form(ctx)
 
 
 def idm_phase_times(ctx, stream=None):

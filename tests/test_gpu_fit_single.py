@@ -168,3 +168,23 @@ def test_horizon_within_one_interval_skips_forward(api, mode):
                                   0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
     np.testing.assert_allclose(res[0][1], hist_ref, rtol=1e-5)
     np.testing.assert_allclose(res[0][0], th_ref, rtol=1e-4, atol=1e-5)
+
+
+def test_last_fit_form(api):
+    """The auto rule: K <= C or N * K <= 2^22 runs the single launch."""
+    rng = np.random.default_rng(304)
+    sc = synth.make_scene([5, 7], rng)
+    N = int(sc["lane_off"][-1])
+    scn = api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+    ctx = api.Context(0, 0, 0, 8, 8)
+    assert ctx.last_fit_form() is None
+    for K, mode, form in ((12, "auto", "single"), (12, "graph", "graph"), (6, "auto", "single")):
+        ctx.set_fit_mode(mode)
+        Y = targets(sc, K, 1, rng)
+        api.fit(cuda(synth.plain_init(N)), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT, cuda(Y), 1, 2,
+                ctx=ctx)
+        assert ctx.last_fit_form() == form
+    Y = targets(sc, 12, 1, rng)
+    api.fit(cuda(synth.plain_init(N)), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 12, DT, cuda(Y), 1, 2,
+            ctx=ctx, eval_targets=cuda(Y))
+    assert ctx.last_fit_form() == "graph"   # the eval variant always runs the graph
