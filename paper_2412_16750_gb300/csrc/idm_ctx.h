@@ -85,12 +85,12 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
 int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const float *box_lo, const float *box_hi,
                    float lr0, float lr1, double *loss_hist, cudaStream_t st);
 // IDM_FIT_AUTO picks the single launch when K fits one checkpoint interval
-// (its forward then runs once, so it never does more work than the graph)
-// or up to this many vehicle-steps per iteration (N * K), where the graph's
-// per-iteration launch boundary outweighs running the forward at the
-// adjoint's occupancy (measured on GB300: 1.2-1.6x faster at 1.7M
-// vehicle-steps, 7% slower at 20M).
-constexpr double IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS = 4194304.0;
+// (its forward then runs once) or up to this many vehicle-steps per
+// iteration (N * K).  Measured on GB300, single launch over graph: 1.5x at
+// 2e6-4e6 vehicle-steps, 1.2x at 2e7, 1.06x at 2e8, 1.01x at 6e8, 1.00x at
+// 2e9 (where the graph's forward kernel, at its own higher occupancy, makes
+// up for the launch boundaries).
+constexpr double IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS = 1073741824.0;
 int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
                   float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
                   cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t),

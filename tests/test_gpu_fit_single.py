@@ -188,3 +188,46 @@ def test_last_fit_form(api):
     api.fit(cuda(synth.plain_init(N)), cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 12, DT, cuda(Y), 1, 2,
             ctx=ctx, eval_targets=cuda(Y))
     assert ctx.last_fit_form() == "graph"   # the eval variant always runs the graph
+
+
+@pytest.mark.parametrize("mode", ["graph", "single"])
+def test_fit_lane_too_long_status(api, mode):
+    """A lane longer than the segment capacity behind an understated
+    max_lane: the device flags it, that lane is not simulated (its
+    parameters stay as given), the other lane is fitted as alone."""
+    from paper_2412_16750_gb300 import lib
+    rng = np.random.default_rng(305)
+    sc = synth.make_scene([70, 3], rng)
+    N = int(sc["lane_off"][-1])
+    K, n_iter = 8, 3
+    Y = targets(sc, K, 1, rng)
+    th0 = synth.plain_init(N)
+    ctx = api.Context(0, 2, 1, 8, 8)
+    ctx.set_fit_mode(mode)
+    scn = api.Scene(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]), 32)  # understated max_lane
+    th = cuda(th0)
+    api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scn, K, DT, cuda(Y), 1, n_iter, 0.1, 0.01,
+            synth.BOX_LO, synth.BOX_HI, A_MIN, ctx=ctx)
+    torch.cuda.synchronize()
+    rc, flags = ctx.status()
+    assert rc == lib.IDM_ERR_LANE and flags & lib.IDM_STATUS_LANE_TOO_LONG
+    th = th.double().cpu().numpy()
+    np.testing.assert_array_equal(th[:, :70], th0[:, :70])
+    short = {k: sc[k][70:] for k in ("length", "p_init", "v_init")}
+    th_ref, _ = oracle.fit(np.array([0, 3], np.int32), short["length"], th0[:, 70:], short["p_init"],
+                           short["v_init"], K, DT, Y[:, 70:], 1, n_iter, 0.1, 0.01, synth.BOX_LO, synth.BOX_HI, A_MIN)
+    np.testing.assert_allclose(th[:, 70:], th_ref, rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("n_iter", [1, 2000])
+def test_single_launch_iteration_counts(api, n_iter):
+    """One iteration, and 2,000 iterations of a small scene (loss partials
+    of every iteration in one buffer): equal to the graph bit for bit."""
+    rng = np.random.default_rng(306)
+    sc = synth.make_scene([3, 9, 1], rng)
+    K = 15
+    Y = targets(sc, K, 1, rng)
+    out = fit_both(api, sc, synth.plain_init(int(sc["lane_off"][-1])), Y, K, 1, n_iter, (0, 2, 1, 8, 8))
+    np.testing.assert_array_equal(out["single"][0], out["graph"][0])
+    np.testing.assert_array_equal(out["single"][1], out["graph"][1])
+    assert np.all(np.isfinite(out["single"][1]))
