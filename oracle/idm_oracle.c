@@ -28,7 +28,8 @@
  *   - a_lb = -v/dt when -v/dt > a_min strictly; a tie takes a_min (derivative 0).
  *   - Loss: sum over vehicles of that vehicle's mean squared error over the
  *     observed steps k = s, 2s, ..., <= K (step 0 never observed).  The paper
- *     sums per-trajectory losses; BASELINE's workloads use squared error.
+ *     sums per-trajectory losses; the multi-vehicle fits here use the squared
+ *     error (the single-trajectory absolute error is recon_oracle.c).
  *   - Parameter order used everywhere in this file:
  *       0 v0 (= v_targ), 1 T (= T_pref), 2 s0 (= s_min), 3 a_max,
  *       4 b (= a_pref), 5 delta.
