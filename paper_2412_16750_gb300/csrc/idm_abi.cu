@@ -384,7 +384,7 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
 // clear the Adam moments and the work counter, run every iteration of every
 // segment, then reduce the loss partials of all iterations.  The partials
 // are sized for the most segments the packing can produce: next-fit packing
-// inside each of the builder's 1024 lane chunks closes a segment only when
+// inside each of the builder's lane chunks closes a segment only when
 // the next lane would overflow it, so two consecutive segments of a chunk
 // hold more than `cap` vehicles and a chunk of n vehicles gives at most
 // 2n/cap + 1 segments.
@@ -395,7 +395,8 @@ int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const
     if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
     if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
     const long long cap = 32LL * P.vpt * P.G;
-    const long long seg_bound = std::min<long long>(n_lanes, 2 * (((long long)N + cap - 1) / cap) + 1024);
+    const long long seg_bound =
+        std::min<long long>(n_lanes, 2 * (((long long)N + cap - 1) / cap) + idm::SEG_BUILD_CHUNKS);
     const long long stride = std::max<long long>(1, seg_bound * P.G);
     if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
         return rc;

@@ -23,6 +23,11 @@ struct ScenDesc {
     long long ckpt_off;  // element offset of the checkpoints
 };
 
+// The segment builder packs lanes in this many contiguous chunks (one
+// thread each, next-fit inside a chunk), so n vehicles in lanes no longer
+// than the capacity give at most 2 n / cap + SEG_BUILD_CHUNKS segments.
+constexpr int SEG_BUILD_CHUNKS = 1024;
+
 // One warp segment: whole lanes packed into at most 32*VPT slots.
 struct Seg {
     int veh_begin;  // global index of slot 0

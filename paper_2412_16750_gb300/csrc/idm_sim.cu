@@ -57,7 +57,7 @@ cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_ini
 // boundary); a block scan places the chunks' segments.  A lane longer than
 // cap is skipped and flagged.
 // ---------------------------------------------------------------------------
-constexpr int BUILD_THREADS = 1024;
+constexpr int BUILD_THREADS = SEG_BUILD_CHUNKS;
 
 template <bool EMIT>
 __device__ int pack_lanes(const int *lane_off, int l0, int l1, const int *scen_lane_off, int n_scen, int cap,
