@@ -130,8 +130,9 @@ int idm_set_tuning(idm_ctx_t *ctx, int vpt, int warps_per_segment, int ckpt_inte
 /* How idm_fit runs its iterations (see idm_fit).  IDM_FIT_AUTO (default):
  * the single launch when K <= ckpt_interval (then the forward runs in the
  * first iteration only: its one checkpoint is the initial state) or N * K <=
- * 2^30 vehicle-steps; else the graph (at that size the two take the same
- * time: the graph's forward kernel runs at its own, higher occupancy).  The graph is always used by idm_fit_eval and while profiling
+ * 2^30 vehicle-steps, provided its loss partials (see idm_fit) fit in 256
+ * MB; else the graph (at 2^30 vehicle-steps the two take the same time: the
+ * graph's forward kernel runs at its own, higher occupancy).  The graph is always used by idm_fit_eval and while profiling
  * is on (idm_set_profiling times every launch of the graph).  Returns
  * IDM_ERR_ARG for another value. */
 #define IDM_FIT_AUTO 0

@@ -380,6 +380,16 @@ int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo
     return IDM_OK;
 }
 
+// Loss partials per iteration of the single launch: one per warp of the
+// most segments the packing can produce (see run_fit_single).
+long long single_launch_stride(const Prep &P, size_t N, int n_lanes)
+{
+    const long long cap = 32LL * P.vpt * P.G;
+    const long long seg_bound =
+        std::min<long long>(n_lanes, 2 * (((long long)N + cap - 1) / cap) + idm::SEG_BUILD_CHUNKS);
+    return std::max<long long>(1, seg_bound * P.G);
+}
+
 // The fit as one persistent launch (idm_fused.cuh) for a single scene:
 // clear the Adam moments and the work counter, run every iteration of every
 // segment, then reduce the loss partials of all iterations.  The partials
@@ -394,10 +404,7 @@ int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const
     int rc;
     if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
     if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
-    const long long cap = 32LL * P.vpt * P.G;
-    const long long seg_bound =
-        std::min<long long>(n_lanes, 2 * (((long long)N + cap - 1) / cap) + idm::SEG_BUILD_CHUNKS);
-    const long long stride = std::max<long long>(1, seg_bound * P.G);
+    const long long stride = single_launch_stride(P, N, n_lanes);
     if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
         return rc;
     SimArgs &a = P.a;
@@ -675,9 +682,11 @@ int idm_fit_eval(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, c
     if ((rc = backward_grid(c, &P, false, true, false, scene->n_lanes))) return rc;
     P.a.targets = targets;
     const double vehicle_steps = (double)scene->n_vehicles * (double)sim->K;
+    const double partial_bytes =
+        8.0 * (double)n_iter * (double)single_launch_stride(P, (size_t)scene->n_vehicles, scene->n_lanes);
     const bool single = !eval_targets && !c->profiling &&
                         (c->fit_mode == IDM_FIT_SINGLE_LAUNCH ||
-                         (c->fit_mode == IDM_FIT_AUTO &&
+                         (c->fit_mode == IDM_FIT_AUTO && partial_bytes <= IDM_SINGLE_LAUNCH_MAX_PARTIAL_BYTES &&
                           (sim->K <= c->C || vehicle_steps <= IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS)));
     c->last_fit_form = single ? IDM_FIT_SINGLE_LAUNCH : IDM_FIT_GRAPH;
     if (single)

@@ -91,6 +91,10 @@ int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const
 // 2e9 (where the graph's forward kernel, at its own higher occupancy, makes
 // up for the launch boundaries).
 constexpr double IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS = 1073741824.0;
+// ... and only while its loss partials (8 bytes per warp segment and
+// iteration) stay within this much workspace.
+constexpr double IDM_SINGLE_LAUNCH_MAX_PARTIAL_BYTES = 268435456.0;
+long long single_launch_stride(const Prep &P, size_t N, int n_lanes);
 int run_fit_graph(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
                   float lr1, double *loss_hist, const void *extra_key, size_t extra_len, cudaStream_t st,
                   cudaError_t (*finalize)(idm_ctx *, const Prep &, int, double *, cudaStream_t),
