@@ -85,7 +85,8 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
     if ((rc = pick_shape(&c, sc->max_lane, &P.vpt, &P.G))) return rc;
     const size_t N = (size_t)sc->n_vehicles, L = (size_t)sc->n_lanes;
     const int G = P.G;
-    const size_t n_ck = (size_t)((sim->K + c.C - 1) / c.C);
+    const int C = std::min(c.C, sim->K);  // as idm_loss_grad: at most the horizon
+    const size_t n_ck = (size_t)((sim->K + C - 1) / C);
 
     // scratch layout (256-byte aligned pieces)
     size_t off = 0;
@@ -125,7 +126,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
     a.targets = targets;
     a.loss_part = (double *)(base + o_part);
     a.ckpt = (float *)(base + o_ckpt);
-    a.C = c.C;
+    a.C = C;
     a.status = status;
     a.N_total = (int)N;
     a.G = G;
@@ -133,7 +134,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
     const bool want_delta = grad && grad->delta;
     if ((rc = forward_grid(&c, &P, (int)L))) return rc;
     if ((rc = backward_grid(&c, &P, false, false, want_delta, (int)L))) return rc;
-    if (P.a.tape_T != c.C) return IDM_ERR_WORKSPACE;  // would need sub-checkpoint scratch
+    if (P.a.tape_T != C) return IDM_ERR_WORKSPACE;  // would need sub-checkpoint scratch
 
     // the array keeps the previous call's contents: clear counters and status
     if (cudaMemsetAsync(base, 0, o_seg, st) != cudaSuccess) return IDM_ERR_CUDA;
