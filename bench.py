@@ -563,6 +563,7 @@ def batched(a, dev):
         e1.record(stream)
         torch.cuda.synchronize()
     ms_iter = e0.elapsed_time(e1) / a.batch_iters
+    fit_form = ctx.last_fit_form()
     rc, flags = ctx.status()
     if rc != 0:
         raise RuntimeError("batched status %d flags %d" % (rc, flags))
@@ -570,7 +571,8 @@ def batched(a, dev):
     _, tot0, _, _, _ = api.batch_loss_grad(plain, p0, v0, b, clean, ctx=ctx)
     out = {"workload": sc["name"], "vehicles": N, "lanes": int(sc["scen_lane_off"][-1]),
            "vehicle_steps_per_iteration": units, "iterations": a.batch_iters, "ms_per_iteration": ms_iter,
-           "vehicle_steps_per_s": units / (ms_iter * 1e-3), "launches_per_iteration": 3,
+           "vehicle_steps_per_s": units / (ms_iter * 1e-3), "fit_form": fit_form,
+           "launches_per_iteration": 3 if fit_form == "graph" else None,
            "shape": {"vpt": shape[0], "warps_per_segment": shape[1], "ckpt_interval": shape[2],
                      "warps_per_block": shape[3], "source": how, "candidates_timed": len(timings)},
            "rmse_vs_clean_m": {"initial": math.sqrt(float(tot0.item()) / N),

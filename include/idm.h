@@ -306,7 +306,9 @@ int idm_batch_loss_grad(idm_ctx_t *ctx, const idm_batch_t *batch, const idm_para
                         void *stream);
 
 /* idm_fit over a batch: n_iter Adam iterations on the sum of the scenario
- * losses, the whole fit captured as one CUDA graph.  loss_hist (device
+ * losses, the whole fit one CUDA graph or one persistent launch (the rule of
+ * idm_set_fit_mode with N * K the batch's sum over scenarios and K its
+ * longest horizon; identical results).  loss_hist (device
  * double [n_iter], may be NULL) receives the summed loss before each update,
  * scen_loss (device double [n_scen], may be NULL) the per-scenario losses of
  * the last iteration. */

@@ -218,6 +218,24 @@ __global__ void scen_total_kernel(const double *part, int per_seg, const int *se
     *total = t;
 }
 
+// Summed loss of every iteration of a single-launch batch fit: thread it
+// sums iteration it's partials in the order of scen_total_kernel.
+__global__ void scen_total_iters_kernel(const double *part, long long stride, int per_seg, const int *seg_off,
+                                        const int *seg_idx, int S, int n_iter, double *hist)
+{
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_iter) return;
+    const double *pi = part + (size_t)it * (size_t)stride;
+    double t = 0.0;
+    for (int s = 0; s < S; ++s) {
+        double acc = 0.0;
+        for (int i = seg_off[s]; i < seg_off[s + 1]; ++i)
+            for (int w = 0; w < per_seg; ++w) acc += pi[(size_t)seg_idx[i] * per_seg + w];
+        t += acc;
+    }
+    hist[it] = t;
+}
+
 struct BatchFinalize {
     int S;
     double *scen_loss;  // per-scenario output of the last iteration (may be NULL)
@@ -325,6 +343,48 @@ int idm_batch_fit(idm_ctx_t *c, const idm_batch_t *b, idm_params_t *params, cons
     if ((rc = backward_grid(c, &P, false, true, false, (int)std::max<size_t>(BP.seg.size(), 1)))) return rc;
     P.a.targets = targets;
     P.k_max = BP.max_K;
+    // the form (see idm_set_fit_mode): the single launch needs the partials
+    // of every iteration, one per warp of every segment (their number is
+    // known here)
+    const int S = b->n_scen;
+    const long long stride = std::max<long long>(1, (long long)BP.seg.size() * P.G);
+    double vehicle_steps = 0.0;
+    for (int q = 0; q < S; ++q) vehicle_steps += (double)BP.scen[q].n_veh * (double)BP.scen[q].K;
+    const bool single = !c->profiling &&
+                        (c->fit_mode == IDM_FIT_SINGLE_LAUNCH ||
+                         (c->fit_mode == IDM_FIT_AUTO &&
+                          8.0 * (double)stride * (double)n_iter <= IDM_SINGLE_LAUNCH_MAX_PARTIAL_BYTES &&
+                          (BP.max_K <= c->C || vehicle_steps <= IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS)));
+    c->last_fit_form = single ? IDM_FIT_SINGLE_LAUNCH : IDM_FIT_GRAPH;
+    if (single) {
+        const size_t N = (size_t)b->n_vehicles;
+        if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
+        if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
+        if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
+            return rc;
+        SimArgs &a = P.a;
+        a.adam_m = (float *)c->adam_m.p;
+        a.adam_v = (float *)c->adam_v.p;
+        a.n_iter = n_iter;
+        a.lr0 = lr0;
+        a.lr1 = lr1;
+        for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
+        a.loss_part = (double *)c->fit_part.p;
+        a.work = (int *)c->ctl.p + CTL_WORK_B;
+        CK(cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, st));
+        CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
+        CK(cudaMemsetAsync(a.work, 0, sizeof(int), st));
+        CK(idm::launch_fit_fused(P.vpt, P.G, a, stride, P.grid_b, P.wpb_b, st));
+        const int *seg_off = (const int *)c->scen_seg_off.p, *seg_idx = (const int *)c->scen_seg_idx.p;
+        if (loss_hist)
+            scen_total_iters_kernel<<<(n_iter + 127) / 128, 128, 0, st>>>(a.loss_part, stride, P.loss_per_seg,
+                                                                          seg_off, seg_idx, S, n_iter, loss_hist);
+        if (scen_loss)
+            scen_loss_kernel<<<(S + 255) / 256, 256, 0, st>>>(a.loss_part + (size_t)(n_iter - 1) * (size_t)stride,
+                                                              P.loss_per_seg, seg_off, seg_idx, S, scen_loss, nullptr);
+        CK(cudaGetLastError());
+        return IDM_OK;
+    }
     g_bfin = BatchFinalize{b->n_scen, scen_loss};
     struct {
         int S;

@@ -202,3 +202,27 @@ def test_autotuned_shape_keeps_parity(api, tmp_path):
     np.testing.assert_allclose(gn, g2n, rtol=0, atol=1e-4 * np.abs(g2n).max())
     shape2, how2, _ = tune.tuned(api.Context(), run, max_lane, sig, path=path)
     assert how2 == "cache" and tuple(shape2) == tuple(shape)
+
+
+@pytest.mark.parametrize("shape", [(0, 2, 1, 3, 8), (0, 4, 2, 8, 8), (0, 8, 2, 5, 8), (0, 0, 0, 64, 8)])
+def test_batch_fit_single_launch_equals_graph(api, shape):
+    """The batched fit as one persistent launch (scenarios with their own K,
+    observation stride and segments, the forward skipped where a scenario's
+    K fits the interval) against the per-iteration graph: loss history and
+    per-scenario losses and parameters bit for bit."""
+    sc, rng = small_batch(207, n_scen=9)
+    Y = targets_for(sc, rng)
+    N = int(sc["lane_off"][-1])
+    th0 = synth.f32(sc["theta_true"] * np.r_[rng.uniform(0.8, 1.2, size=(5, N)), np.ones((1, N))])
+    b = batch_of(api, sc)
+    out = {}
+    for mode in ("graph", "single"):
+        ctx = api.Context(*shape)
+        ctx.set_fit_mode(mode)
+        th = cuda(th0)
+        hist, sl = api.batch_fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), b, cuda(Y), 5, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ctx.check_status() == 0 and ctx.last_fit_form() == mode
+        out[mode] = (th.cpu().numpy(), hist.cpu().numpy(), sl.cpu().numpy())
+    for q in range(3):
+        np.testing.assert_array_equal(out["single"][q], out["graph"][q])
