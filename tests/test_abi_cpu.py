@@ -60,6 +60,8 @@ def test_null_context_is_rejected(libpath):
     assert L.idm_ctx_create(None, 0) == lib.IDM_ERR_ARG
     assert L.idm_ctx_destroy(None) == lib.IDM_OK
     assert L.idm_set_tuning(None, 0, 0, 16, 8) == lib.IDM_ERR_ARG
+    assert L.idm_set_fit_mode(None, lib.IDM_FIT_AUTO) == lib.IDM_ERR_ARG
+    assert L.idm_last_fit_form(None) == 0
 
 
 def test_cpu_backend_exports_its_header():
