@@ -381,10 +381,12 @@ def time_to_fit(a, dev):
     plain = cu(synth.plain_init(N))
     ctx = api.Context()
     th_buf = torch.empty_like(plain)
-    # kernel shape for this problem size (autotuner, cached per GPU)
-    sig = tune.signature(100, N, K, 1, kind="fit")
-    shape, shape_src, _ = tune.tuned(ctx, lambda c: api.loss_grad(plain, p0, v0, scene, K, DT, Y, 1, ctx=c,
-                                                                  want_state_grad=False), 100, sig, repeats=3)
+    # kernel shape for this problem size (autotuner, cached per GPU), timed on
+    # a short fit: the shape also decides the fit's form and tape depth
+    sig = tune.signature(100, N, K, 1, kind="fit-20")
+    scratch = plain.clone()
+    shape, shape_src, _ = tune.tuned(ctx, lambda c: api.fit(scratch, p0, v0, scene, K, DT, Y, 1, 20, ctx=c), 100,
+                                     sig, repeats=3)
 
     def timed(fn):
         e0, e1 = ev(), ev()
