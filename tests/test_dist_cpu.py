@@ -24,6 +24,41 @@ def test_lane_shards_balanced_and_complete():
     assert idm_dist.weak_scaling_value(1e9, 4, 1000.0) == pytest.approx(4e9)
 
 
+def test_lane_shards_more_ranks_than_lanes():
+    lane_off = synth.lane_offsets([4, 9, 2])
+    sh = idm_dist.lane_shards(lane_off, 8)
+    assert len(sh) == 8 and sh[0][0] == 0 and sh[-1][1] == 3
+    assert all(sh[r][1] == sh[r + 1][0] and sh[r][0] <= sh[r][1] for r in range(7))
+    assert sum(b - a for a, b in sh) == 3
+    for a_l, b_l in sh:   # an empty shard has an empty vehicle range and a one-entry CSR
+        a, e, lo = idm_dist.shard_arrays(lane_off, a_l, b_l)
+        assert e - a == int(lane_off[b_l] - lane_off[a_l]) and len(lo) == b_l - a_l + 1 and lo[0] == 0
+
+
+def test_sharded_fit_equals_unsharded():
+    """Lanes never interact and Adam is per vehicle, so fitting each rank's
+    lanes alone (FP64 oracle) reproduces the unsharded fit, and the per-rank
+    loss histories sum to the unsharded history."""
+    import oracle
+    sc = synth.make_scene([7, 12, 3, 9, 15, 4, 1], np.random.default_rng(42))
+    K, dt, n_iter = 20, float(np.float32(0.1)), 4
+    N = int(sc["lane_off"][-1])
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, dt)
+    Y = P[1:] + np.random.default_rng(43).normal(0, 0.5, size=(K, N))
+    th0 = synth.plain_init(N)
+    th_full, h_full = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, dt, Y, 1, n_iter,
+                                 0.1, 0.01, synth.BOX_LO, synth.BOX_HI)
+    for world in (2, 3):
+        h_sum = np.zeros(n_iter)
+        for l0, l1 in idm_dist.lane_shards(sc["lane_off"], world):
+            a, e, lo = idm_dist.shard_arrays(sc["lane_off"], l0, l1)
+            th, h = oracle.fit(lo, sc["length"][a:e], th0[:, a:e], sc["p_init"][a:e], sc["v_init"][a:e], K, dt,
+                               Y[:, a:e], 1, n_iter, 0.1, 0.01, synth.BOX_LO, synth.BOX_HI)
+            np.testing.assert_allclose(th, th_full[:, a:e], rtol=1e-12, atol=1e-13)
+            h_sum += h
+        np.testing.assert_allclose(h_sum, h_full, rtol=1e-12)
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
