@@ -398,13 +398,12 @@ long long single_launch_stride(const Prep &P, size_t N, int n_lanes)
 // the next lane would overflow it, so two consecutive segments of a chunk
 // hold more than `cap` vehicles and a chunk of n vehicles gives at most
 // 2n/cap + 1 segments.
-int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const float *box_lo, const float *box_hi,
-                   float lr0, float lr1, double *loss_hist, cudaStream_t st)
+int launch_single_fit(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
+                      float lr1, long long stride, cudaStream_t st)
 {
     int rc;
     if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
     if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
-    const long long stride = single_launch_stride(P, N, n_lanes);
     if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
         return rc;
     SimArgs &a = P.a;
@@ -420,8 +419,17 @@ int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const
     CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
     CK(cudaMemsetAsync(a.work, 0, sizeof(int), st));
     CK(idm::launch_fit_fused(P.vpt, P.G, a, stride, P.grid_b, P.wpb_b, st));
+    return IDM_OK;
+}
+
+int run_fit_single(idm_ctx *c, Prep &P, int n_iter, size_t N, int n_lanes, const float *box_lo, const float *box_hi,
+                   float lr0, float lr1, double *loss_hist, cudaStream_t st)
+{
+    const long long stride = single_launch_stride(P, N, n_lanes);
+    int rc;
+    if ((rc = launch_single_fit(c, P, n_iter, N, box_lo, box_hi, lr0, lr1, stride, st))) return rc;
     if (loss_hist)
-        CK(idm::launch_loss_finalize_iters(a.loss_part, stride, a.n_seg, P.loss_per_seg, n_iter, loss_hist, st));
+        CK(idm::launch_loss_finalize_iters(P.a.loss_part, stride, P.a.n_seg, P.loss_per_seg, n_iter, loss_hist, st));
     return IDM_OK;
 }
 

@@ -357,24 +357,9 @@ int idm_batch_fit(idm_ctx_t *c, const idm_batch_t *b, idm_params_t *params, cons
                           (BP.max_K <= c->C || vehicle_steps <= IDM_SINGLE_LAUNCH_MAX_VEHICLE_STEPS)));
     c->last_fit_form = single ? IDM_FIT_SINGLE_LAUNCH : IDM_FIT_GRAPH;
     if (single) {
-        const size_t N = (size_t)b->n_vehicles;
-        if ((rc = ensure(c, c->adam_m, sizeof(float) * 5 * N, "Adam m"))) return rc;
-        if ((rc = ensure(c, c->adam_v, sizeof(float) * 5 * N, "Adam v"))) return rc;
-        if ((rc = ensure(c, c->fit_part, sizeof(double) * (size_t)stride * (size_t)n_iter, "fit loss partials")))
+        if ((rc = launch_single_fit(c, P, n_iter, (size_t)b->n_vehicles, box_lo, box_hi, lr0, lr1, stride, st)))
             return rc;
-        SimArgs &a = P.a;
-        a.adam_m = (float *)c->adam_m.p;
-        a.adam_v = (float *)c->adam_v.p;
-        a.n_iter = n_iter;
-        a.lr0 = lr0;
-        a.lr1 = lr1;
-        for (int q = 0; q < 5; ++q) { a.lo[q] = box_lo[q]; a.hi[q] = box_hi[q]; }
-        a.loss_part = (double *)c->fit_part.p;
-        a.work = (int *)c->ctl.p + CTL_WORK_B;
-        CK(cudaMemsetAsync(c->adam_m.p, 0, sizeof(float) * 5 * N, st));
-        CK(cudaMemsetAsync(c->adam_v.p, 0, sizeof(float) * 5 * N, st));
-        CK(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-        CK(idm::launch_fit_fused(P.vpt, P.G, a, stride, P.grid_b, P.wpb_b, st));
+        const SimArgs &a = P.a;
         const int *seg_off = (const int *)c->scen_seg_off.p, *seg_idx = (const int *)c->scen_seg_idx.p;
         if (loss_hist)
             scen_total_iters_kernel<<<(n_iter + 127) / 128, 128, 0, st>>>(a.loss_part, stride, P.loss_per_seg,

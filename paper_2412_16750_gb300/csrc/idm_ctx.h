@@ -79,6 +79,12 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
 // finalize(it, stream) enqueues the loss reduction of iteration it.  With
 // eval_targets and eval_hist set, each iteration's forward also records the
 // loss against eval_targets in eval_hist[it] (single scene only).
+// The single-launch fit of plan P (single scene or batch): Adam state and
+// the [n_iter][stride] loss partials in the workspace, moments and work
+// counter cleared, the persistent kernel launched.  The caller reduces the
+// partials.
+int launch_single_fit(idm_ctx *c, Prep &P, int n_iter, size_t N, const float *box_lo, const float *box_hi, float lr0,
+                      float lr1, long long stride, cudaStream_t st);
 // The fit of a single scene as one persistent launch (no eval targets, no
 // per-launch profiling); same results as run_fit_graph with single-scene
 // loss reduction.
