@@ -80,7 +80,8 @@ typedef struct {
     const float *length;
 } idm_scene_t;
 
-/* Per-vehicle IDM parameters (device, each [n_vehicles]). */
+/* Per-vehicle IDM parameters (device, each [n_vehicles]; may be NULL when
+ * the scene has no vehicles). */
 typedef struct {
     float *v0, *T, *s0, *a_max, *b, *delta;
 } idm_params_t;

@@ -123,9 +123,10 @@ static int check_scene(idm_ctx *c, const idm_scene_t *s)
     return IDM_OK;
 }
 
-int check_params(idm_ctx *c, const idm_params_t *p, bool all)
+int check_params(idm_ctx *c, const idm_params_t *p, bool all, long long n_vehicles)
 {
     if (!p) return fail(c, IDM_ERR_ARG, "params is NULL");
+    if (n_vehicles == 0) return IDM_OK;  // nothing is read or written
     if (!p->v0 || !p->T || !p->s0 || !p->a_max || !p->b || (all && !p->delta))
         return fail(c, IDM_ERR_ARG, "a parameter array is NULL");
     return IDM_OK;
@@ -585,7 +586,7 @@ int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *para
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true, scene->n_vehicles)) || (rc = check_sim(c, sim))) return rc;
     if (scene->n_vehicles > 0 && (!p_init || !v_init)) return fail(c, IDM_ERR_ARG, "p_init and v_init are required");
     cudaStream_t st = (cudaStream_t)stream;
     Prep P;
@@ -603,7 +604,7 @@ int idm_backward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *par
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true, scene->n_vehicles)) || (rc = check_sim(c, sim))) return rc;
     if (scene->n_vehicles > 0 && (!p_init || !v_init || !gP))
         return fail(c, IDM_ERR_ARG, "p_init, v_init and gP are required");
     cudaStream_t st = (cudaStream_t)stream;
@@ -631,7 +632,7 @@ int idm_loss_grad(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *pa
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true, scene->n_vehicles)) || (rc = check_sim(c, sim))) return rc;
     if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
     if (scene->n_vehicles > 0 && (!p_init || !v_init)) return fail(c, IDM_ERR_ARG, "p_init and v_init are required");
     if (sim->K / obs_stride > 0 && scene->n_vehicles > 0 && !targets)
@@ -673,7 +674,7 @@ int idm_fit_eval(idm_ctx_t *c, const idm_scene_t *scene, idm_params_t *params, c
     if ((eval_targets == nullptr) != (eval_hist == nullptr))
         return fail(c, IDM_ERR_ARG, "eval_targets and eval_hist must be given together");
     int rc;
-    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true)) || (rc = check_sim(c, sim))) return rc;
+    if ((rc = check_scene(c, scene)) || (rc = check_params(c, params, true, scene->n_vehicles)) || (rc = check_sim(c, sim))) return rc;
     if (obs_stride < 1) return fail(c, IDM_ERR_ARG, "obs_stride must be >= 1");
     if (n_iter < 0 || n_iter > 100000) return fail(c, IDM_ERR_ARG, "n_iter must be in [0, 100000]");
     if (!box_lo || !box_hi) return fail(c, IDM_ERR_ARG, "box_lo and box_hi (host) are required");

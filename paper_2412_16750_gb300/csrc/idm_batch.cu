@@ -277,7 +277,7 @@ int idm_batch_forward(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *pa
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true))) return rc;
+    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true, b->n_vehicles))) return rc;
     if (b->n_vehicles > 0 && (!p_init || !v_init || !traj))
         return fail(c, IDM_ERR_ARG, "p_init, v_init and traj are required");
     cudaStream_t st = (cudaStream_t)stream;
@@ -296,7 +296,7 @@ int idm_batch_loss_grad(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true))) return rc;
+    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true, b->n_vehicles))) return rc;
     if (b->n_vehicles > 0 && (!p_init || !v_init || !targets))
         return fail(c, IDM_ERR_ARG, "p_init, v_init and targets are required");
     cudaStream_t st = (cudaStream_t)stream;
@@ -327,7 +327,7 @@ int idm_batch_fit(idm_ctx_t *c, const idm_batch_t *b, idm_params_t *params, cons
 {
     if (!c) return IDM_ERR_ARG;
     int rc;
-    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true))) return rc;
+    if ((rc = check_batch(c, b)) || (rc = check_params(c, params, true, b->n_vehicles))) return rc;
     if (n_iter < 0 || n_iter > 100000) return fail(c, IDM_ERR_ARG, "n_iter must be in [0, 100000]");
     if (!box_lo || !box_hi) return fail(c, IDM_ERR_ARG, "box_lo and box_hi (host) are required");
     for (int q = 0; q < 5; ++q)

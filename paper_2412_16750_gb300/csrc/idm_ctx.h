@@ -72,7 +72,8 @@ int ensure_status(idm_ctx *c);
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
 // Forward shape for the segment capacity of the adjoint shape (vpt, G).
 void forward_shape(int vpt, int G, int *vpt_f, int *G_f);
-int check_params(idm_ctx *c, const idm_params_t *p, bool all);
+// Parameter arrays: required unless the scene has no vehicles.
+int check_params(idm_ctx *c, const idm_params_t *p, bool all, long long n_vehicles);
 int forward_grid(idm_ctx *c, Prep *P, int L);
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L);
 // Capture (or reuse) the n_iter-iteration fit graph for plan P and launch it.

@@ -231,3 +231,30 @@ def test_single_launch_iteration_counts(api, n_iter):
     np.testing.assert_array_equal(out["single"][0], out["graph"][0])
     np.testing.assert_array_equal(out["single"][1], out["graph"][1])
     assert np.all(np.isfinite(out["single"][1]))
+
+
+@pytest.mark.parametrize("mode", ["graph", "single"])
+def test_degenerate_fits(api, mode):
+    """An empty scene (one lane, no vehicle) and a fit with no observed step
+    (stride beyond K: no targets, zero loss, zero gradients, so Adam leaves
+    the parameters as given) run in both forms and return zero losses."""
+    ctx = api.Context()
+    ctx.set_fit_mode(mode)
+    empty = api.Scene.from_lane_off(cuda(np.array([0, 0]), torch.int32), cuda(np.zeros(0)))
+    th = torch.zeros((6, 0), device="cuda")
+    hist = api.fit(th, cuda(np.zeros(0)), cuda(np.zeros(0)), empty, 10, DT, cuda(np.zeros((10, 0))), 1, 3, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.check_status() == 0 and ctx.last_fit_form() == mode
+    np.testing.assert_array_equal(hist.cpu().numpy(), np.zeros(3))
+    rng = np.random.default_rng(307)
+    sc = synth.make_scene([5, 0, 3], rng)
+    N = int(sc["lane_off"][-1])
+    scn = api.Scene.from_lane_off(cuda(sc["lane_off"], torch.int32), cuda(sc["length"]))
+    th0 = synth.plain_init(N)
+    th = cuda(th0)
+    hist = api.fit(th, cuda(sc["p_init"]), cuda(sc["v_init"]), scn, 7, DT, torch.zeros((0, N), device="cuda"), 8, 3,
+                   ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.check_status() == 0 and ctx.last_fit_form() == mode
+    np.testing.assert_array_equal(hist.cpu().numpy(), np.zeros(3))
+    np.testing.assert_array_equal(th.cpu().numpy(), synth.f32(th0))
