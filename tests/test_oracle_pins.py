@@ -433,6 +433,37 @@ def test_adam_matches_torch_optim():
     assert oracle.lr_schedule(4, 5, 0.1, 0.01) == pytest.approx(0.01, abs=1e-17)
 
 
+def test_fit_is_the_replay_of_its_steps():
+    """oracle.fit = n_iter rounds of (forward, squared-error seed, adjoint,
+    Adam with bias correction at t = it + 1 and the learning rate
+    lr0 + (lr1 - lr0) it / (n_iter - 1) written here from its definition,
+    projection onto the box), with the loss recorded before each update and
+    delta never changed."""
+    sc = synth.make_scene([6, 3, 9], np.random.default_rng(19))
+    K, s, n_iter, lr0, lr1 = 24, 2, 4, 0.3, 0.05
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, 0.1)
+    N = P.shape[1]
+    Y = P[s::s][:K // s] + np.random.default_rng(20).normal(0, 0.5, size=(K // s, N))
+    th0 = synth.plain_init(N)
+    th0[5, :3] = 3.0
+    lo, hi = np.array(synth.BOX_LO), np.array(synth.BOX_HI)
+    thf, hist = oracle.fit(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, 0.1, Y, s, n_iter,
+                           lr0, lr1, lo, hi)
+    th = th0.copy()
+    m, v = np.zeros((5, N)), np.zeros((5, N))
+    for it in range(n_iter):
+        Pi, Vi = oracle.forward(sc["lane_off"], sc["length"], th, sc["p_init"], sc["v_init"], K, 0.1)
+        L, gP = oracle.mse_seed(Pi, Y, s)
+        g, _, _ = oracle.adjoint(sc["lane_off"], sc["length"], th, K, 0.1, Pi, Vi, gP)
+        assert hist[it] == pytest.approx(L, rel=1e-14)
+        th5 = np.ascontiguousarray(th[:5])
+        oracle.adam_step(th5, np.ascontiguousarray(g[:5]), m, v, it + 1, lr0 + (lr1 - lr0) * it / (n_iter - 1),
+                         lo, hi)
+        th[:5] = th5
+    np.testing.assert_allclose(thf, th, rtol=1e-13, atol=1e-13)
+    np.testing.assert_array_equal(thf[5], th0[5])
+
+
 def test_fit_from_truth_without_noise_is_stationary():
     sc, _, _, K, s = tiny_problem(seed=15)
     th = sc["theta_true"].copy()
