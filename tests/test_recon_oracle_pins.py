@@ -194,6 +194,43 @@ def test_fit_reduces_loss_and_is_stationary_at_the_truth():
     np.testing.assert_array_equal(th2[:5], np.clip(th[:5], np.array(lo)[:, None], np.array(hi)[:, None]))
 
 
+def test_fit_is_the_replay_of_its_steps():
+    """R.fit = n_iter rounds of (forward, absolute-error seed with the loss
+    recorded before the update, adjoint, Adam at t = it + 1 with the learning
+    rate lr0 + (lr1 - lr0) it / (n_iter - 1) on the five parameters, projected
+    onto the box, and unconstrained on every dp_k, dv_k), replayed here with
+    torch.optim.Adam; delta is never changed."""
+    torch = pytest.importorskip("torch")
+    K, th, dp, dv, p0, v0, off, ks, ys = _toy(21)
+    lo, hi = np.array(synth.BOX_LO), np.array(synth.BOX_HI)
+    th0 = synth.plain_init(3)
+    th0[5, 1] = 3.0
+    n_iter, lr0, lr1 = 5, 0.2, 0.02
+    th_f, dp_f, dv_f, hist = R.fit(K, dp, dv, th0, p0, v0, DT, off, ks, ys, n_iter, lr0, lr1, lo, hi, A_MIN)
+    t_th = torch.tensor(th0[:5].copy(), requires_grad=True)
+    t_dp = torch.tensor(dp.copy(), requires_grad=True)
+    t_dv = torch.tensor(dv.copy(), requires_grad=True)
+    opt = torch.optim.Adam([t_th, t_dp, t_dv], lr=lr0, betas=(0.9, 0.999), eps=1e-8)
+    for it in range(n_iter):
+        thi = np.vstack([t_th.detach().numpy(), th0[5:]])
+        dpi, dvi = t_dp.detach().numpy(), t_dv.detach().numpy()
+        P, V, _ = R.forward(K, dpi, dvi, thi, p0, v0, DT, A_MIN)
+        L, gP = R.mae_seed(K, off, ks, ys, P)
+        g, gdp, gdv, _, _ = R.adjoint(K, dpi, dvi, thi, DT, V, gP, A_MIN)
+        assert hist[it] == pytest.approx(L, rel=1e-14)
+        for grp in opt.param_groups:
+            grp["lr"] = lr0 + (lr1 - lr0) * it / (n_iter - 1)
+        t_th.grad, t_dp.grad, t_dv.grad = torch.tensor(g[:5]), torch.tensor(gdp), torch.tensor(gdv)
+        opt.step()
+        with torch.no_grad():
+            t_th.copy_(torch.maximum(torch.minimum(t_th, torch.tensor(hi)[:, None]), torch.tensor(lo)[:, None]))
+    np.testing.assert_allclose(th_f[:5], t_th.detach().numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(th_f[5], th0[5])
+    np.testing.assert_allclose(dp_f, t_dp.detach().numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(dv_f, t_dv.detach().numpy(), rtol=1e-12, atol=1e-12)
+    assert not np.allclose(dp_f, dp)
+
+
 def test_metrics_hand_made():
     K = np.array([4, 4], np.int32)
     P = np.array([[3.0, 0.0], [4.0, 2.0], [5.0, 4.0], [6.0, 6.0], [7.0, 8.0]])
