@@ -202,6 +202,8 @@ def test_fit_is_the_replay_of_its_steps():
     torch.optim.Adam; delta is never changed."""
     torch = pytest.importorskip("torch")
     K, th, dp, dv, p0, v0, off, ks, ys = _toy(21)
+    dv[2:6, 0] = 25.0     # far outside any plausible bound: the virtual-leader
+    dp[3:5, 1] = 400.0    # variables are never boxed
     lo, hi = np.array(synth.BOX_LO), np.array(synth.BOX_HI)
     th0 = synth.plain_init(3)
     th0[5, 1] = 3.0
