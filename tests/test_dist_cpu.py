@@ -1,6 +1,8 @@
-"""Multi-rank path on CPU (gloo, world size 2): lane sharding and the two
-host-side collectives.  The sharded loss equals the unsharded one and every
-rank's gradients equal its slice of the full adjoint (FP64 oracle)."""
+"""Multi-rank path on CPU (gloo): lane and scenario sharding and the host-side
+collectives.  The sharded loss equals the unsharded one and every rank's
+gradients equal its slice of the full adjoint (FP64 oracle); the product
+path dist.fit_sharded, driving libidm_cpu.so on every rank, reproduces the
+unsharded fit of the same library."""
 import os
 import socket
 
@@ -22,6 +24,23 @@ def test_lane_shards_balanced_and_complete():
     sh = idm_dist.lane_shards(synth.lane_offsets([100] * 20), 4)
     assert [b - a for a, b in sh] == [5, 5, 5, 5]
     assert idm_dist.weak_scaling_value(1e9, 4, 1000.0) == pytest.approx(4e9)
+
+
+def test_lane_shards_balance_vehicle_steps():
+    """Weights per lane (vehicles x horizon) move the cuts; scenario shards
+    balance the sum of vehicles x horizon."""
+    lane_off = synth.lane_offsets([10, 10, 10, 10])
+    assert idm_dist.lane_shards(lane_off, 2) == [(0, 2), (2, 4)]
+    assert idm_dist.lane_shards(lane_off, 2, steps=[300, 100, 100, 100]) == [(0, 1), (1, 4)]
+    sh = idm_dist.scenario_shards([100, 50, 50, 100], [100, 200, 200, 100], 2)
+    assert sh == [(0, 2), (2, 4)]
+    rng = np.random.default_rng(5)
+    nv, K = rng.integers(2, 200, 500), rng.integers(50, 500, 500)
+    for world in (2, 3, 8):
+        sh = idm_dist.scenario_shards(nv, K, world)
+        w = [int(np.sum(nv[a:b] * K[a:b])) for a, b in sh]
+        assert sum(w) == int(np.sum(nv * K))
+        assert max(w) - min(w) <= 2 * int(np.max(nv * K))    # within two scenarios of even
 
 
 def test_lane_shards_more_ranks_than_lanes():
@@ -118,5 +137,61 @@ def test_sharded_loss_and_gradients_match_unsharded():
         assert total == pytest.approx(Lf, rel=1e-12)
         assert slowest == 2.0
         np.testing.assert_allclose(g, gf[:, a:e], rtol=1e-12, atol=1e-15)
+        covered[a:e] = True
+    assert covered.all()
+
+
+def _fit_problem(seed=44):
+    import oracle
+    sc = synth.make_scene([7, 12, 3, 9, 15, 4, 1, 20, 6], np.random.default_rng(seed))
+    K, dt = 30, float(np.float32(0.1))
+    N = int(sc["lane_off"][-1])
+    P, _ = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, dt)
+    Y = synth.f32(P[1:] + np.random.default_rng(seed + 1).normal(0, 0.5, size=(K, N)))
+    return sc, K, dt, Y, synth.plain_init(N)
+
+
+def _rank_fit(rank, world, port, out):
+    import torch.distributed as dist
+    from paper_2412_16750_gb300 import build
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    build.build_cpu()
+    sc, K, dt, Y, th0 = _fit_problem()
+    th, (a, e), hist = idm_dist.fit_sharded(sc["lane_off"], sc["length"], th0, sc["p_init"], sc["v_init"], K, dt, Y,
+                                            1, 6, backend="cpu", threads=2)
+    out.put((rank, a, e, th, hist))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_fit_sharded_product_path(world):
+    """dist.fit_sharded on gloo ranks, each fitting its lane range with the
+    CPU backend (libidm_cpu.so): every rank's parameters equal its slice of
+    the unsharded fit bit for bit (lanes never interact), and the all-reduced
+    loss history equals the unsharded one up to the order of the FP64 sum."""
+    import multiprocessing as mp
+    from paper_2412_16750_gb300 import build, cpu
+    build.build_cpu()
+    sc, K, dt, Y, th0 = _fit_problem()
+    th_full = th0.astype(np.float32).copy()
+    h_full = cpu.idm_cpu_fit(th_full, sc["p_init"], sc["v_init"], cpu.Scene(sc["lane_off"], sc["length"]), K, dt, Y,
+                             1, 6, threads=2)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_fit, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=180) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    covered = np.zeros(th0.shape[1], dtype=bool)
+    for rank, a, e, th, hist in res:
+        np.testing.assert_array_equal(th, th_full[:, a:e])
+        np.testing.assert_allclose(hist, h_full, rtol=1e-12)
         covered[a:e] = True
     assert covered.all()
