@@ -61,7 +61,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--vpt", type=int, default=4)
     p.add_argument("--G", type=int, default=4, help="warps per segment")
-    p.add_argument("--ckpt", type=int, default=8)
+    p.add_argument("--ckpt", type=int, default=50, help="checkpoint interval of the timed fit (the stated 50)")
+    p.add_argument("--tuned-ckpt", type=int, default=8,
+                   help="also time the step at this interval (0 = skip); reported as tuned_variant")
+    p.add_argument("--tuned-steps", type=int, default=3)
     p.add_argument("--wpb", type=int, default=8)
     # learned-versus-plain initial guess (time to fit 0.5 m RMSE)
     p.add_argument("--no-init-experiment", action="store_true")
@@ -94,8 +97,9 @@ def parse():
 
 
 def workload_name(a):
-    return ("%d lanes x %d vehicles (%.1fM), %d steps, dt 0.1 s; per step: layout + %d-iteration Adam fit"
-            % (a.lanes, a.per_lane, a.lanes * a.per_lane / 1e6, a.K, a.iters))
+    return ("%d lanes x %d vehicles (%.1fM) per GPU, %d steps, dt 0.1 s, checkpoints every %d steps; per step: "
+            "layout + %d-iteration Adam fit" % (a.lanes, a.per_lane, a.lanes * a.per_lane / 1e6, a.K, a.ckpt,
+                                                a.iters))
 
 
 # ---------------------------------------------------------------------------
@@ -234,40 +238,75 @@ def alu_peak_ginst(sm_mhz, n_sm):
     return n_sm * 128 * sm_mhz * 1e6 / 1e9
 
 
-# Algorithmic instructions per vehicle-step of the adjoint launch, counted
-# from the method's formulas: recompute of the forward step (30 FP32 + 5
-# special-function) + reverse step with gradient accumulation (80 FP32 + 3
-# special-function).
-ADJ_OPS_PER_VS = 118.0
+# Algorithmic work per vehicle-step of the adjoint launch, counted from the
+# method's formulas: FP32 lane operations of the recompute of the forward
+# step (30) and of the reverse step with the gradient accumulation (80), and
+# the special-function operations (exp2 / log2 / reciprocal: 5 in the
+# recompute, 3 in the reverse step) on their own pipe.
+ADJ_FP32_PER_VS = 110.0
+ADJ_SFU_PER_VS = 8.0
+SFU_PER_SM_CLK = 16
 
 
-# Sources of the adjoint kernel: the committed ncu summary records their hash.
+# Sources of the adjoint kernel: a committed ncu summary records their hash.
 ADJOINT_SOURCES = ("idm_adjoint.cuh", "idm_sim_common.cuh", "idm_device.cuh")
 
 
 def adjoint_traffic(n_vehicles, K, ckpt):
-    """DRAM bytes of one adjoint launch from the committed ncu summary
-    (N K a + N b, captured at checkpoint interval 8), or None if absent,
-    taken on a different kernel source or for another interval."""
-    path = os.path.join(ROOT, "profiles", "adjoint_kernel_2M.md")
-    if not os.path.exists(path) or ckpt != 8:
-        return None
+    """DRAM bytes of one adjoint launch (N K a + N b) from the committed ncu
+    summary taken at this checkpoint interval (profiles/adjoint_kernel_*.md
+    with a matching `ckpt_interval:` line), or None if there is none or it
+    was taken on a different kernel source."""
+    import glob
     import hashlib
     src = b""
     for name in ADJOINT_SOURCES:
         src += open(os.path.join(ROOT, "paper_2412_16750_gb300", "csrc", name), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
-    got_sha, per_vs, per_v = None, None, 0.0
-    for line in open(path):
-        if line.startswith("kernel_source_sha256_16:"):
-            got_sha = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_vehicle_step:"):
-            per_vs = float(line.split(":", 1)[1].strip())
-        if line.startswith("dram_bytes_per_vehicle:"):
-            per_v = float(line.split(":", 1)[1].strip())
-    if got_sha != sha or not per_vs:
-        return None
-    return n_vehicles * K * per_vs + n_vehicles * per_v
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "adjoint_kernel_*.md"))):
+        got = {}
+        for line in open(path):
+            for key in ("kernel_source_sha256_16", "ckpt_interval", "dram_bytes_per_vehicle_step",
+                        "dram_bytes_per_vehicle"):
+                if line.startswith(key + ":"):
+                    got[key] = line.split(":", 1)[1].strip()
+        if got.get("kernel_source_sha256_16") != sha or got.get("ckpt_interval") != str(ckpt):
+            continue
+        if "dram_bytes_per_vehicle_step" not in got:
+            continue
+        return n_vehicles * K * float(got["dram_bytes_per_vehicle_step"]) + \
+            n_vehicles * float(got.get("dram_bytes_per_vehicle", 0.0))
+    return None
+
+
+def adjoint_roofline(N, K, ckpt, bwd_avg_ms, n_sm, peaks, peak_kind):
+    """Roofline object of the adjoint launch: bound by the FP32 pipe
+    (algorithmic FP32 lane operations / launch time against 128 FP32 lanes
+    per SM at the maximum SM clock), with the special-function pipe and HBM
+    beside it."""
+    units = N * K
+    t = bwd_avg_ms * 1e-3
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    achieved = ADJ_FP32_PER_VS * units / t / 1e9
+    peak = alu_peak_ginst(sm_mhz, n_sm)
+    sfu_achieved = ADJ_SFU_PER_VS * units / t / 1e9
+    sfu_peak = n_sm * SFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    return {
+        "kernel": "backward_kernel (adjoint with checkpoint recompute + fused Adam)",
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
+        "frac": achieved / peak,
+        "traffic": adjoint_traffic(N, K, ckpt),
+        "peak_source": "nominal: %d SMs x 128 FP32 lanes x %.0f MHz (the maximum SM clock of MEASURED_PEAKS.json, "
+                       "%s; that file has no FP32 figure)" % (n_sm, sm_mhz, peak_kind),
+        "ops_per_vehicle_step": ADJ_FP32_PER_VS,
+        "avg_launch_ms": bwd_avg_ms,
+        "ckpt_interval": ckpt,
+        "sfu": {"ops_per_vehicle_step": ADJ_SFU_PER_VS, "achieved": sfu_achieved, "peak": sfu_peak,
+                "frac": sfu_achieved / sfu_peak, "unit": "G special-function ops/s",
+                "peak_source": "nominal: %d SMs x %d per clock x %.0f MHz" % (n_sm, SFU_PER_SM_CLK, sm_mhz)},
+        "hbm_achieved_gbs": (4.0 + 16.0 / ckpt) * units / t / 1e9,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
 
 
 def run_e2e(a, e2e_steps, step, barrier, max_over_ranks, stream, dev, u_lane, u_p, u_v, u_len, u_th, u_Y, s_th,
@@ -418,6 +457,11 @@ def time_to_fit(a, dev):
             api.mlp_features(scene, p0, v0, K, DT, Y, 1), th_buf))
     _, ev_learned = api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx, eval_targets=clean)
     it_learned, rmse_learned = first_below(ev_learned)
+    ctx.set_event_counting(True)
+    ctx.event_counts()
+    api.simulate(th_buf, p0, v0, scene, K, DT, ctx=ctx)
+    events_learned = ctx.event_counts()
+    ctx.set_event_counting(False)
     # ablation: every vehicle starts at the mean of the training labels (what
     # the network could know without looking at the trajectories)
     lo, hi = np.array(synth.BOX_LO), np.array(synth.BOX_HI)
@@ -439,6 +483,7 @@ def time_to_fit(a, dev):
                               "init_ms": init_ms,
                               "rmse_m_at": {str(i): float(rmse_learned[i])
                                             for i in (0, 10, 50, 100, a.fit_iters - 1) if i < a.fit_iters}},
+                  "events_learned_fit": events_learned,
                   "training_mean_ablation": {"iterations": it_mean, "seconds": wall(it_mean, 0.0),
                                              "rmse_m_at": {str(i): float(rmse_mean[i])
                                                            for i in (0, 10, 50, 100, a.fit_iters - 1)
@@ -486,6 +531,11 @@ def long_horizon(a, dev, net):
         raise RuntimeError("long-horizon status %d flags %d" % (rc, flags))
     peak = torch.cuda.max_memory_allocated(dev)
     ws = lib_workspace(ctx, scene, K_fit)
+    ctx.set_event_counting(True)
+    ctx.event_counts()
+    api.simulate(th, p0, v0, scene, K_all, DT, ctx=ctx)
+    events = ctx.event_counts()
+    ctx.set_event_counting(False)
     err = (pred[K_fit + 1:] - truth[K_fit + 1:]).double()
     rmse_pred = float(torch.sqrt((err * err).mean()).item())
     err_fit = (pred[1:K_fit + 1] - truth[1:K_fit + 1]).double()
@@ -512,6 +562,7 @@ def long_horizon(a, dev, net):
            "rmse_vs_noisy_targets_m": {"before_first_update": math.sqrt(float(hist[0].item()) / N),
                                        "before_last_update": math.sqrt(float(hist[-1].item()) / N)},
            "oracle_check": {"lanes": len(lanes), "max_abs_diff_m": worst, "steps": K_all},
+           "events_fitted": events,
            "peak_hbm_gb": {"torch_allocated": peak / 1e9, "library_workspace": ws / 1e9}}
     ctx.close()
     return out
@@ -569,6 +620,11 @@ def batched(a, dev):
     rc, flags = ctx.status()
     if rc != 0:
         raise RuntimeError("batched status %d flags %d" % (rc, flags))
+    ctx.set_event_counting(True)
+    ctx.event_counts()
+    api.batch_forward(th, p0, v0, b, ctx=ctx)
+    events = ctx.event_counts()
+    ctx.set_event_counting(False)
     _, tot_clean, _, _, _ = api.batch_loss_grad(th, p0, v0, b, clean, ctx=ctx)
     _, tot0, _, _, _ = api.batch_loss_grad(plain, p0, v0, b, clean, ctx=ctx)
     out = {"workload": sc["name"], "vehicles": N, "lanes": int(sc["scen_lane_off"][-1]),
@@ -577,6 +633,7 @@ def batched(a, dev):
            "launches_per_iteration": 3 if fit_form == "graph" else None,
            "shape": {"vpt": shape[0], "warps_per_segment": shape[1], "ckpt_interval": shape[2],
                      "warps_per_block": shape[3], "source": how, "candidates_timed": len(timings)},
+           "events_fitted": events,
            "rmse_vs_clean_m": {"initial": math.sqrt(float(tot0.item()) / N),
                                "after_%d_iterations" % a.batch_iters: math.sqrt(float(tot_clean.item()) / N)}}
     ctx.close()
@@ -829,12 +886,19 @@ def run_gpu(a, rank, world, local_rank):
             print(json.dumps({"time_to_fit": ttf, "long_horizon": long_horizon(a, dev, net)}), flush=True)
         return 0
 
-    # ---- synthetic batch (seeded per rank), unsorted arrival order -------
-    rng = synth.rng_for(1, rank)
-    counts = [a.per_lane] * a.lanes
+    # ---- this rank's share of the job's scene, unsorted arrival order -----
+    # The job's scene has world x --lanes lanes of --per-lane vehicles; lanes
+    # are independent, so each rank takes a contiguous lane range balanced by
+    # vehicles x steps (dist.lane_shards) and the ranks exchange only the FP64
+    # loss history of each step's fit (one all-reduce).
+    from paper_2412_16750_gb300 import dist as idm_dist
+    L_job = a.lanes * world
+    l0, l1 = idm_dist.lane_shards(synth.lane_offsets([a.per_lane] * L_job), world)[rank]
+    rng = synth.rng_for(1, l0)                  # seeded by the shard's first lane
+    counts = [a.per_lane] * (l1 - l0)
     sc = synth.make_scene(counts, rng)
     N = int(sc["lane_off"][-1])
-    L = a.lanes
+    L = l1 - l0
     K = a.K
     ctx = api.Context(vpt=a.vpt, warps_per_segment=a.G, ckpt_interval=a.ckpt, warps_per_block=a.wpb)
     cu = lambda x, d=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=d, device=dev)
@@ -842,7 +906,7 @@ def run_gpu(a, rank, world, local_rank):
     th_true = cu(sc["theta_true"])
     p_sorted, v_sorted = cu(sc["p_init"]), cu(sc["v_init"])
     gen = torch.Generator(device=dev)
-    gen.manual_seed(20241216 + 1000 * rank)
+    gen.manual_seed(20241216 + 1000 * l0)
     traj = api.simulate(th_true, p_sorted, v_sorted, scene_sorted, K, DT, A_MIN, ctx=ctx)
     Y_sorted = traj[1:]
     Y_sorted.add_(0.5 * torch.randn(Y_sorted.shape, device=dev, generator=gen))
@@ -876,6 +940,12 @@ def run_gpu(a, rank, world, local_rank):
     params_c = lib.make_params(s_th)
     sim_c = lib.make_sim(K, DT, A_MIN)
 
+    def reduce_hist():
+        # the job's loss history: the shards' FP64 histories summed (the one
+        # data-path collective; lanes never interact)
+        if dist is not None:
+            dist.all_reduce(hist, op=dist.ReduceOp.SUM)
+
     def step(in_lane, in_p, in_v, in_len, in_th, in_Y):
         lib.idm_layout(h, N, L, in_lane, in_p, perm, lane_off, mx, stream)
         lib.idm_gather(h, N, perm, [in_p, in_v, in_len] + [in_th[q] for q in range(6)],
@@ -883,6 +953,7 @@ def run_gpu(a, rank, world, local_rank):
         lib.idm_gather_rows(h, N, K, perm, in_Y, s_Y, stream)
         lib.idm_fit(h, scene_c, params_c, s_p, s_v, sim_c, s_Y, 1, a.iters, 0.1, 0.01, synth.BOX_LO, synth.BOX_HI,
                     hist, stream)
+        reduce_hist()
 
     launches_per_step = 4 + 1 + 1 + 3 + 3 * a.iters  # layout 4, gather 1, rows 1, prep 3, 3 per iteration
 
@@ -897,38 +968,47 @@ def run_gpu(a, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- warm-up -----------------------------------------------------------
-    for _ in range(a.warmup):
-        step(u_lane, u_p, u_v, u_len, u_th, u_Y)
-    torch.cuda.synchronize()
-    rc, flags = ctx.status()
-    if rc != 0:
-        raise RuntimeError("device status %d flags %d: %s" % (rc, flags, lib.idm_last_error(h)))
+    def measure(steps, warmup, sample_clocks):
+        """warmup untimed steps, then `steps` timed ones (device-resident
+        inputs); adjoint and forward launch times from the fit graph's events."""
+        for _ in range(warmup):
+            step(u_lane, u_p, u_v, u_len, u_th, u_Y)
+        torch.cuda.synchronize()
+        rc, flags = ctx.status()
+        if rc != 0:
+            raise RuntimeError("device status %d flags %d: %s" % (rc, flags, lib.idm_last_error(h)))
+        clocks = ClockSampler(local_rank) if sample_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        fwd_ms = bwd_ms = 0.0
+        n_fit_iters = 0
+        e0.record(stream)
+        for _ in range(steps):
+            step(u_lane, u_p, u_v, u_len, u_th, u_Y)
+            f, b, n = lib.idm_phase_times(h, stream)  # syncs the stream: per-launch event times of this step
+            fwd_ms += f
+            bwd_ms += b
+            n_fit_iters += n
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        return {"ms": ms, "fwd_avg_ms": fwd_ms / max(n_fit_iters, 1), "bwd_avg_ms": bwd_ms / max(n_fit_iters, 1),
+                "clocks": clk}
 
-    # ---- timed: device-resident inputs --------------------------------------
-    clocks = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    fwd_ms = bwd_ms = 0.0
-    n_fit_iters = 0
-    e0.record(stream)
-    for _ in range(a.steps):
-        step(u_lane, u_p, u_v, u_len, u_th, u_Y)
-        f, b, n = lib.idm_phase_times(h, stream)  # syncs the stream: per-launch event times of this step
-        fwd_ms += f
-        bwd_ms += b
-        n_fit_iters += n
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms)
-    final_loss = float(hist[-1].item()) / N
-    first_loss = None
+    peaks, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    units_per_step = a.iters * N * K
+
+    # ---- timed: device-resident inputs, the stated checkpoint interval ------
+    m = measure(a.steps, a.warmup, True)
+    ms = m["ms"]
+    final_loss = float(hist[-1].item()) / (N * world)
 
     # ---- timed: end to end from pinned host memory --------------------------
     e2e_steps = a.e2e_steps if a.e2e_steps is not None else a.steps
@@ -940,41 +1020,45 @@ def run_gpu(a, rank, world, local_rank):
         if rc != 0:
             raise RuntimeError("device status %d flags %d after e2e" % (rc, flags))
 
-    units_per_step = a.iters * N * K
     value = world * units_per_step * a.steps / (ms * 1e-3)
     e2e_value = world * units_per_step * e2e_steps / (ms_e2e * 1e-3) if ms_e2e else None
+    roofline = adjoint_roofline(N, K, a.ckpt, m["bwd_avg_ms"], n_sm, peaks, peak_kind)
 
-    # ---- roofline of the adjoint launch ----------------------------------------
-    peaks, peak_kind = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    bwd_avg_ms = bwd_ms / max(n_fit_iters, 1)
-    fwd_avg_ms = fwd_ms / max(n_fit_iters, 1)
-    units_launch = N * K
-    achieved_ginst = ADJ_OPS_PER_VS * units_launch / (bwd_avg_ms * 1e-3) / 1e9
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_ginst = alu_peak_ginst(sm_mhz, n_sm)
-    traffic = adjoint_traffic(N, K, a.ckpt)
-    roofline = {
-        "kernel": "backward_kernel (adjoint with checkpoint recompute + fused Adam)",
-        "bound": "alu", "achieved": achieved_ginst, "peak": peak_ginst, "unit": "Ginstr/s (FP32 pipe)",
-        "frac": achieved_ginst / peak_ginst,
-        "traffic": traffic,
-        "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (max SM clock, %s)" % (n_sm, sm_mhz, peak_kind),
-        "ops_per_vehicle_step": ADJ_OPS_PER_VS,
-        "avg_launch_ms": bwd_avg_ms,
-        "hbm_achieved_gbs": (4.0 + 16.0 / a.ckpt) * units_launch / (bwd_avg_ms * 1e-3) / 1e9,
-        "hbm_peak_gbs": peaks.get("hbm_gbs"),
-    }
+    # ---- the same step at the tuned checkpoint interval (labelled variant) ----
+    tuned = None
+    if a.tuned_ckpt and a.tuned_ckpt != a.ckpt and a.tuned_steps > 0:
+        ctx.set_tuning(a.vpt, a.G, a.tuned_ckpt, a.wpb)
+        lib.idm_set_profiling(h, 1)
+        mt = measure(a.tuned_steps, max(3, min(a.warmup, 3)), False)
+        tuned = {"ckpt_interval": a.tuned_ckpt, "steps": a.tuned_steps,
+                 "value": world * units_per_step * a.tuned_steps / (mt["ms"] * 1e-3),
+                 "ms_per_step": mt["ms"] / a.tuned_steps,
+                 "fwd_ms_per_timestep": mt["fwd_avg_ms"] / K, "bwd_ms_per_timestep": mt["bwd_avg_ms"] / K,
+                 "roofline": adjoint_roofline(N, K, a.tuned_ckpt, mt["bwd_avg_ms"], n_sm, peaks, peak_kind),
+                 "note": "the same workload with the checkpoint interval whose adjoint tape fits shared memory "
+                         "(no tape blocks); checkpoints then take %.1f GB instead of %.2f GB"
+                         % (16.0 * N * math.ceil(K / a.tuned_ckpt) / 1e9, 16.0 * N * math.ceil(K / a.ckpt) / 1e9)}
+        ctx.set_tuning(a.vpt, a.G, a.ckpt, a.wpb)
+
+    # ---- Sec. III-C events of the fitted and the true parameters ------------
+    ctx.set_event_counting(True)
+    ctx.event_counts()
+    api.simulate(s_th, s_p, s_v, api.Scene(lane_off, s_len, a.per_lane), K, DT, A_MIN, ctx=ctx)
+    ev_fit = ctx.event_counts()
+    api.simulate(th_true, p_sorted, v_sorted, scene_sorted, K, DT, A_MIN, ctx=ctx)
+    ev_true = ctx.event_counts()
+    ctx.set_event_counting(False)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(a), "vehicles_per_gpu": N, "K": K, "iters_per_step": a.iters,
+        "config": {"workload": workload_name(a), "vehicles_per_gpu": N, "lanes_per_gpu": L, "job_lanes": L_job,
+                   "K": K, "iters_per_step": a.iters,
                    "ckpt_interval": a.ckpt, "vpt": a.vpt, "warps_per_segment": a.G, "warps_per_block": a.wpb,
                    "l2": "inputs larger than L2 (targets %.1f GB per GPU)" % (K * N * 4 / 1e9),
-                   "parallelism": "dp%d (independent batches)" % world,
-                   "fwd_ms_per_timestep": fwd_avg_ms / K, "bwd_ms_per_timestep": bwd_avg_ms / K,
+                   "parallelism": "dp%d (one scene sharded by lanes; FP64 loss-history all-reduce per step)" % world,
+                   "fwd_ms_per_timestep": m["fwd_avg_ms"] / K, "bwd_ms_per_timestep": m["bwd_avg_ms"] / K,
                    "paper_context": "paper Fig. 1: < 30 ms per timestep forward and backward each at 2M vehicles "
                                     "(RTX A5000 or 16-thread Xeon W-2255), i.e. > 3.3e7 fwd+bwd vehicle-steps/s "
                                     "(a bound, not an exact figure: vs_baseline stays null)",
@@ -983,21 +1067,25 @@ def run_gpu(a, rank, world, local_rank):
                 "ms_per_step": (ms_e2e / e2e_steps) if ms_e2e else None},
         "gpu_launches": launches_per_step * a.steps,
         "roofline": roofline,
-        "clocks": clk,
+        "clocks": m["clocks"],
+        "events": {"fitted": ev_fit, "truth": ev_true,
+                   "what": "vehicle-steps with the raw gap below the 0.1 m floor / within 0.5 m/s^2 of the kink of "
+                           "max(-v/dt, a_min), over one simulation of the %d steps" % K},
     }
+    net = None
+    if world == 1 and not a.no_crossover:
+        line["cpu_gpu_crossover"] = cpu_gpu_crossover(a, dev)
+    if world == 1 and not a.no_recon:
+        line["reconstruction"] = reconstruction(a, dev)
+    if world == 1 and not a.no_pred:
+        line["prediction"] = prediction(a, dev)
+    if world == 1 and not a.no_batched:
+        line["batched"] = batched(a, dev)
     if world == 1 and not a.no_init_experiment:
         line["time_to_fit"], net = time_to_fit(a, dev)
         if not a.no_long_horizon:
             line["long_horizon"] = long_horizon(a, dev, net)
         net.close()
-    if world == 1 and not a.no_batched:
-        line["batched"] = batched(a, dev)
-    if world == 1 and not a.no_recon:
-        line["reconstruction"] = reconstruction(a, dev)
-    if world == 1 and not a.no_pred:
-        line["prediction"] = prediction(a, dev)
-    if world == 1 and not a.no_crossover:
-        line["cpu_gpu_crossover"] = cpu_gpu_crossover(a, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v1, secs1, desc = oracle_sample(iters=30)
         vc, secs_c, cores = oracle_all_cores(iters=10)
@@ -1005,12 +1093,48 @@ def run_gpu(a, rank, world, local_rank):
                                 "sample": "%d processes, each: %s" % (cores, desc.replace("30 fit", "10 fit")),
                                 "seconds": secs_c,
                                 "single_core": {"value": v1, "sample": desc, "seconds": secs1}}
+    if tuned is not None:
+        line["tuned_variant"] = tuned
+    line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def summary(line):
+    """The figures of every part of the metric in a few hundred characters,
+    printed last so that the tail of the line carries them."""
+    r = lambda x, n=4: (float("%.*g" % (n, x)) if isinstance(x, (int, float)) else x)
+    out = {"fwd_bwd_vehicle_steps_per_s": r(line["value"]), "ckpt_interval": line["config"]["ckpt_interval"],
+           "adjoint_ms": r(line["roofline"]["avg_launch_ms"]), "adjoint_fp32_frac": r(line["roofline"]["frac"], 3)}
+    tv = line.get("tuned_variant")
+    if tv:
+        out["tuned_ckpt_%d" % tv["ckpt_interval"]] = {"value": r(tv["value"]),
+                                                      "adjoint_ms": r(tv["roofline"]["avg_launch_ms"]),
+                                                      "adjoint_fp32_frac": r(tv["roofline"]["frac"], 3)}
+    ttf = line.get("time_to_fit")
+    if ttf:
+        f = ttf["fit"]
+        last = str(max(int(k) for k in f["plain"]["rmse_m_at"]))
+        out["time_to_fit_0.5m"] = {
+            k: {"iterations": f[k]["iterations"], "s": r(f[k]["seconds"]) if f[k]["seconds"] else None,
+                "rmse_m_last": r(f[k]["rmse_m_at"][last], 3)}
+            for k in ("learned", "plain", "training_mean_ablation")}
+        out["time_to_fit_0.5m"]["learned"]["init_ms"] = r(f["learned"]["init_ms"], 3)
+        out["time_to_fit_0.5m"]["ms_per_iteration"] = r(f["ms_per_iteration"], 3)
+    b = line.get("batched")
+    if b:
+        out["batched_vehicle_steps_per_s"] = r(b["vehicle_steps_per_s"])
+    lh = line.get("long_horizon")
+    if lh:
+        out["long_horizon"] = {"rmse_fit_m": r(lh["rmse_fit_window_m"], 3), "rmse_pred_m": r(lh["rmse_prediction_m"], 3),
+                               "fit_vehicle_steps_per_s": r(lh["fit_vehicle_steps_per_s"]),
+                               "oracle_max_abs_diff_m": r(lh["oracle_check"]["max_abs_diff_m"], 3)}
+    out["events_fitted"] = line["events"]["fitted"]
+    return out
 
 
 def main():

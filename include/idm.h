@@ -61,6 +61,12 @@ extern "C" {
  * derivative below the floor.  The paper is silent on gaps <= 0. */
 #define IDM_GAP_FLOOR 0.1f
 
+/* Kink band (m/s^2) of the lower bound a_lb = max(-v/dt, a_min) of Sec. III-C:
+ * a vehicle-step counts as near the kink when |-v/dt - a_min| is below it
+ * (for dt = 0.1 s and a_min = -10 m/s^2: speeds within 0.05 m/s of 1 m/s),
+ * where the derivative of a_lb jumps between -1/dt and 0. */
+#define IDM_KINK_BAND 0.5f
+
 typedef struct idm_ctx idm_ctx_t;
 
 /* Lane structure of a scene in head-first order.
@@ -113,6 +119,21 @@ const char *idm_last_error(const idm_ctx_t *ctx);
  * receives the IDM_STATUS_* bits.  Returns IDM_ERR_LANE or IDM_ERR_NONFINITE
  * when the matching bits are set, IDM_OK otherwise. */
 int idm_status(idm_ctx_t *ctx, uint32_t *flags, void *stream);
+
+/* Event counters of the modelling choices the paper leaves open (Sec. III-C):
+ * when counting is on (idm_set_event_counting, default off), every
+ * idm_forward and idm_batch_forward on this context adds, over the steps
+ * k = 0..K-1 it evaluates and every vehicle,
+ *   gap_floor_hits: vehicle-steps whose raw gap (p_h - p - length_h) is below
+ *                   IDM_GAP_FLOOR (the floor applies and its derivative is 0),
+ *   kink_near:      vehicle-steps with |-v/dt - a_min| < IDM_KINK_BAND (the
+ *                   lower bound is within the band of its kink; the strict
+ *                   -v/dt > a_min rule picks the branch there),
+ * both decided in FP32 as the step evaluates them.  The counts accumulate
+ * across calls until read.  idm_event_counts synchronises `stream`, returns
+ * both counts (host uint64, either pointer may be NULL) and clears them. */
+int idm_set_event_counting(idm_ctx_t *ctx, int on);
+int idm_event_counts(idm_ctx_t *ctx, void *stream, uint64_t *gap_floor_hits, uint64_t *kink_near);
 
 /* Kernel shape.  Whole lanes are packed into segments of at most
  * 32 * vpt * warps_per_segment vehicles, each simulated by warps_per_segment
@@ -322,28 +343,29 @@ int idm_batch_fit(idm_ctx_t *ctx, const idm_batch_t *batch, idm_params_t *params
 /* Size of the library's built-in device scratch array (16 MiB). */
 #define IDM_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* idm_loss_grad for callers that cannot allocate device memory: code whose
- * memory is owned by a custom allocator or a fixed budget, or that runs
- * where cudaMalloc is not allowed (for instance between the begin and end of
- * a stream capture).  The paper has no counterpart; this is a deployment
- * convenience.  No context is needed and nothing is allocated: the scratch
- * (segments, counters, status, initial gaps, loss partials, checkpoints)
+/* idm_loss_grad for callers that cannot allocate device memory: an
+ * application whose device memory belongs to its own allocator or pool (a
+ * cudaMalloc inside a library would bypass it and fragment what it manages),
+ * or one that admits work only against a memory budget fixed up front.  The
+ * paper has no counterpart; this is a deployment convenience.  No context is
+ * needed and nothing is allocated: the scratch (segments, counters, status,
+ * initial gaps, loss partials, checkpoints, the compensated gradient totals)
  * lives in one IDM_NOALLOC_SCRATCH_BYTES static device array that every GPU
  * loading the library holds until the process exits.
- *   Arguments and results are those of idm_loss_grad; the kernel shape is
- *   the default (checkpoint interval 8).
+ *   Arguments, argument checks and results are those of idm_loss_grad; the
+ *   kernel shape is the default (checkpoint interval 8).
  *   status_out (device uint32, may be NULL): receives the device status word
  *   (IDM_STATUS_* bits) of this call, since there is no context to query.
  * Limit: the scratch must hold about 16*n_lanes + 4*N + 64*n_lanes +
- * 16*N*ceil(K/8) bytes (plus 256-byte alignment of each piece), i.e. about
- * N * ceil(K/8) <= 1,000,000 vehicle-checkpoints; larger problems return
- * IDM_ERR_WORKSPACE before anything is launched.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Every call shares the one array and overwrites it: calls
- * that overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  Returns IDM_OK, IDM_ERR_ARG, IDM_ERR_WORKSPACE
- * or IDM_ERR_CUDA (no message string is kept). */
+ * 20*N*ceil(K/8) bytes, plus about 48*N bytes when K > 256 (plus 256-byte alignment
+ * of each piece), i.e. about N * ceil(K/8) <= 800,000 vehicle-checkpoints;
+ * larger problems return IDM_ERR_WORKSPACE before anything is launched.
+ * The first call in a CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it per context; make that first call
+ * before any stream capture.  Every call shares the one array and overwrites
+ * it: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Returns IDM_OK, IDM_ERR_ARG,
+ * IDM_ERR_WORKSPACE or IDM_ERR_CUDA (no message string is kept). */
 int idm_loss_grad_noalloc(const idm_scene_t *scene, const idm_params_t *params, const float *p_init,
                           const float *v_init, const idm_sim_t *sim, const float *targets, int32_t obs_stride,
                           double *loss_out, idm_params_t *grad, float *grad_p_init, float *grad_v_init,

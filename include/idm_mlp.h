@@ -91,6 +91,18 @@ int idm_mlp_get_weights(idm_mlp_t *mlp, float *weights, void *stream);
  * synchronises the stream.  Returns IDM_ERR_TIMEOUT if a bounded wait gave
  * up, IDM_ERR_NONFINITE for a non-finite loss. */
 int idm_mlp_status(idm_mlp_t *mlp, void *stream, uint32_t *bits);
+/* Clear the sticky status word (synchronises the stream). */
+int idm_mlp_clear_status(idm_mlp_t *mlp, void *stream);
+
+/* Bound on the polls of each wait of the network's tensor-core kernels for
+ * the tensor core, the copies or another role of the CTA (0 restores the
+ * default of 2^26 polls; every wait also gives up after 2 s).  A kernel
+ * whose wait runs out sets IDM_STATUS_TIMEOUT, lets every role of the CTA
+ * give up, waits (with the default bound) for the copies and tensor-core
+ * work it has issued, frees its tensor memory and returns; later calls run
+ * normally.  No counterpart in the paper: it lets a test exercise that path
+ * with a wait that cannot finish in one poll. */
+int idm_mlp_set_wait_limit(idm_mlp_t *mlp, uint32_t polls);
 
 /* ---- features ---------------------------------------------------------------
  * Feature rows for the vehicles perm[r] (r < n_rows; perm NULL = identity)

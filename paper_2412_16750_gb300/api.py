@@ -52,6 +52,16 @@ class Context:
             raise lib.IdmError(rc, lib.idm_last_error(self.handle))
         return flags
 
+    def set_event_counting(self, on):
+        """Count gap-floor hits and kink-band vehicle-steps in simulate /
+        batch_forward (idm_set_event_counting)."""
+        lib.idm_set_event_counting(self.handle, on)
+
+    def event_counts(self, stream=None):
+        """{"gap_floor_hits": n, "kink_near": n} since the last read (clears them)."""
+        a, b = lib.idm_event_counts(self.handle, stream or torch.cuda.current_stream())
+        return {"gap_floor_hits": a, "kink_near": b}
+
     def close(self):
         if self.handle is not None:
             lib.idm_ctx_destroy(self.handle)
@@ -347,6 +357,13 @@ class Mlp:
 
     def status(self):
         return lib.idm_mlp_status(self.handle, _stream())
+
+    def clear_status(self):
+        lib.idm_mlp_clear_status(self.handle, _stream())
+
+    def set_wait_limit(self, polls):
+        """Polls per tensor-core wait before a kernel gives up (0 = default)."""
+        lib.idm_mlp_set_wait_limit(self.handle, polls)
 
     def close(self):
         if self.handle is not None:

@@ -47,6 +47,7 @@ int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
 {
     if (bytes == 0) bytes = 16;
     if (b.n >= bytes) return IDM_OK;
+    if (c->no_alloc) return fail(c, IDM_ERR_WORKSPACE, "%s would need an allocation", name);
     size_t want = c->held - b.n + bytes;
     if (c->cap && want > c->cap)
         return fail(c, IDM_ERR_WORKSPACE, "workspace for %s needs %zu bytes in total, cap is %zu", name, want,
@@ -78,12 +79,18 @@ int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name)
 int ensure_status(idm_ctx *c)
 {
     if (c->status.p) return IDM_OK;
-    int rc = ensure(c, c->status, sizeof(unsigned) * 4, "status");
+    int rc = ensure(c, c->status, STATUS_BYTES, "status");
     if (rc) return rc;
-    cudaError_t e = cudaMemset(c->status.p, 0, sizeof(unsigned) * 4);
+    cudaError_t e = cudaMemset(c->status.p, 0, STATUS_BYTES);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();  // before any stream of the caller uses it
     if (e != cudaSuccess) return cuda_fail(c, e, "clearing the status word");
     return IDM_OK;
+}
+
+unsigned long long *event_counters(idm_ctx *c)
+{
+    if (!c->count_events || !c->status.p) return nullptr;
+    return reinterpret_cast<unsigned long long *>(static_cast<char *>(c->status.p) + STATUS_EVENTS_OFF);
 }
 
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
@@ -111,7 +118,7 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
     return IDM_OK;
 }
 
-static int check_scene(idm_ctx *c, const idm_scene_t *s)
+int check_scene(idm_ctx *c, const idm_scene_t *s)
 {
     if (!s) return fail(c, IDM_ERR_ARG, "scene is NULL");
     if (s->n_lanes < 1) return fail(c, IDM_ERR_ARG, "n_lanes must be >= 1 (got %d)", s->n_lanes);
@@ -132,7 +139,7 @@ int check_params(idm_ctx *c, const idm_params_t *p, bool all, long long n_vehicl
     return IDM_OK;
 }
 
-static int check_sim(idm_ctx *c, const idm_sim_t *s)
+int check_sim(idm_ctx *c, const idm_sim_t *s)
 {
     if (!s) return fail(c, IDM_ERR_ARG, "sim is NULL");
     if (s->K < 1) return fail(c, IDM_ERR_ARG, "K must be >= 1 (got %d)", s->K);
@@ -160,7 +167,9 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
     // segment; clamping it lets the adjoint's tape be only K steps deep
     const int C = std::min(c->C, sim->K);
     const int n_ck = (sim->K + C - 1) / C;
-    if (need_ckpt && (rc = ensure(c, c->ckpt, sizeof(float) * 4 * (size_t)n_ck * N, "checkpoints"))) return rc;
+    if (need_ckpt &&
+        (rc = ensure(c, c->ckpt, sizeof(float) * idm::STATE_ROWS * (size_t)n_ck * N, "checkpoints")))
+        return rc;
 
     SimArgs &a = P->a;
     memset(&a, 0, sizeof a);
@@ -221,7 +230,9 @@ int forward_grid(idm_ctx *c, Prep *P, int L)
 {
     forward_shape(P->vpt, P->G, &P->vpt_f, &P->G_f);
     const int G = P->G_f;
-    P->wpb_f = std::max(G, (c->wpb / G) * G);
+    // 8 vehicles per thread: blocks of up to 12 warps (their register budget,
+    // one block per SM); otherwise the context's warps per block
+    P->wpb_f = P->vpt_f == 8 ? std::max(G, (12 / G) * G) : std::max(G, (c->wpb / G) * G);
     const int warps_needed = L * G;  // segments <= lanes
     const int blocks_needed = (warps_needed + P->wpb_f - 1) / P->wpb_f;
     int occ_f = idm::occupancy_blocks(P->vpt_f, G, false, false, false, false, P->wpb_f, 0);
@@ -257,12 +268,25 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     if (T < C) {
         const size_t rows = (size_t)((C + T - 1) / T - 1);
         int rc;
-        if ((rc = ensure(c, c->sub_ckpt, sizeof(float) * 4 * rows * (size_t)std::max(P->a.N_total, 1),
+        if ((rc = ensure(c, c->sub_ckpt, sizeof(float) * idm::STATE_ROWS * rows * (size_t)std::max(P->a.N_total, 1),
                          "sub-checkpoints")))
             return rc;
         P->a.sub_ckpt = (float *)c->sub_ckpt.p;
     } else {
         P->a.sub_ckpt = nullptr;
+    }
+    // compensated totals of the gradient sums (folded only past the window),
+    // for the most segments the packing can produce (L: lanes of a single
+    // scene, or the batch's segments)
+    if (P->k_max > idm::GSUM_FOLD_STEPS && P->a.N_total > 0) {
+        const long long cap = 32LL * P->vpt * G;
+        const long long n_seg = std::min<long long>(
+            L, 2 * (((long long)P->a.N_total + cap - 1) / cap) + idm::SEG_BUILD_CHUNKS);
+        int rc;
+        if ((rc = ensure(c, c->gsum, idm::gsum_bytes((size_t)n_seg, (int)cap), "gradient totals"))) return rc;
+        P->a.gsum = (float *)c->gsum.p;
+    } else {
+        P->a.gsum = nullptr;
     }
     const size_t per_group = idm::backward_smem_bytes(P->vpt, dense, T, G, G, pf);
     int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
@@ -481,7 +505,7 @@ int idm_ctx_destroy(idm_ctx_t *c)
                    &c->lay_cursor, &c->eval_part, &c->sub_ckpt,    &c->scen_tab,     &c->scen_seg_off,
                    &c->scen_seg_idx, &c->lane_off_dev, &c->rec_oyy, &c->rec_oyc,    &c->rec_tape,
                    &c->rec_mom,  &c->rec_thm,    &c->rec_acc,      &c->rec_kmax,     &c->rec_multi,
-                   &c->fit_part};
+                   &c->fit_part, &c->gsum};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -528,7 +552,12 @@ size_t idm_workspace_bytes(const idm_ctx_t *c, const idm_scene_t *s, const idm_s
     // sub-checkpoints when the adjoint's tape is shallower than the interval
     // (at most ceil(C/2) - 1 rows; typically none for C <= 8)
     const size_t sub = C > 8 ? (size_t)((C + 1) / 2 - 1) : 0;
-    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + 16 * n_ck * N + 16 * sub * N;
+    const size_t cap = 512;  // default segment capacity
+    const size_t totals =
+        sim->K > idm::GSUM_FOLD_STEPS ? idm::gsum_bytes(std::min(L, 2 * ((N + cap - 1) / cap) + 1024), (int)cap) : 0;
+    const size_t sb = sizeof(float) * idm::STATE_ROWS;  // bytes of one stored state
+    return sizeof(Seg) * L + sizeof(int) * CTL_N + 16 + 4 * N + 8 * 8 * L + 16 + sb * n_ck * N + sb * sub * N +
+           totals;
 }
 
 int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
@@ -549,6 +578,30 @@ int idm_status(idm_ctx_t *c, uint32_t *flags, void *stream)
         return fail(c, IDM_ERR_OBS, "device status 0x%x: malformed observations or horizons", h);
     if (h & IDM_STATUS_BAD_LANES)
         return fail(c, IDM_ERR_LANES, "device status 0x%x: malformed lane polylines or lane index", h);
+    return IDM_OK;
+}
+
+int idm_set_event_counting(idm_ctx_t *c, int on)
+{
+    if (!c) return IDM_ERR_ARG;
+    int rc;
+    if ((rc = ensure_status(c))) return rc;
+    c->count_events = on ? 1 : 0;
+    return IDM_OK;
+}
+
+int idm_event_counts(idm_ctx_t *c, void *stream, uint64_t *gap_floor_hits, uint64_t *kink_near)
+{
+    if (!c) return IDM_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long h[2] = {0, 0};
+    if (c->status.p) {
+        char *p = static_cast<char *>(c->status.p) + STATUS_EVENTS_OFF;
+        CK(cudaMemcpy(h, p, sizeof h, cudaMemcpyDeviceToHost));
+        CK(cudaMemset(p, 0, sizeof h));
+    }
+    if (gap_floor_hits) *gap_floor_hits = h[0];
+    if (kink_near) *kink_near = h[1];
     return IDM_OK;
 }
 
@@ -594,6 +647,7 @@ int idm_forward(idm_ctx_t *c, const idm_scene_t *scene, const idm_params_t *para
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
     P.a.vtraj = vtraj;
+    P.a.events = event_counters(c);
     CK(idm::launch_forward(P.vpt_f, P.G_f, traj != nullptr, vtraj != nullptr, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }

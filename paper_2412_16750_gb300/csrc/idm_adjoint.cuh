@@ -15,8 +15,53 @@ namespace idm {
 // with mu = dt lv_{k+1}; the follower's terms arrive by one warp shuffle
 // (and across warps through the group's exchange cells).  The coefficients
 // of step k-1 are evaluated while the dependent chain of step k runs.
-// The six factored gradient sums of each slot accumulate in registers over
-// all steps.
+// The six factored gradient sums of each slot accumulate in registers and
+// are folded into compensated totals about every FOLD_STEPS steps.
+// ---------------------------------------------------------------------------
+// Compensated gradient sums.  Within a fold window of max(1, FOLD_STEPS / C)
+// checkpoint segments (counted from the last) the six factored sums of a slot
+// accumulate in FP32 registers; at the end of each window they are added to
+// the slot's running totals, kept in a.gsum as unevaluated float pairs
+// hi + lo, by Knuth's TwoSum, which returns the rounding error of the
+// addition exactly.  The error of a slot's sum then stays that of one
+// window's FP32 accumulation, whatever the horizon.  The totals of segment
+// s_idx occupy 6 x (capacity / 2) float4 (hi.x, hi.y, lo.x, lo.y) per vehicle
+// pair, each written and read back by the thread that owns the pair.
+// ---------------------------------------------------------------------------
+constexpr int FOLD_STEPS = GSUM_FOLD_STEPS;
+
+template <int NP, bool WD>
+__device__ __forceinline__ void fold_sums(const SimArgs &a, int s_idx, const Grp &g, f2 (&sacc)[6][NP], bool have,
+                                          bool last)
+{
+    const int pairs = 32 * NP * g.G;  // vehicle pairs of a segment
+    float4 *base = reinterpret_cast<float4 *>(a.gsum) + (size_t)s_idx * 6 * pairs + g.w * 32 * NP + g.lane;
+#pragma unroll
+    for (int q = 0; q < (WD ? 6 : 5); ++q) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float4 *t = base + (size_t)q * pairs + 32 * p;
+            f2 hi = F2(0.0f), lo = F2(0.0f);
+            if (have) {
+                const float4 v = *t;
+                hi = make_float2(v.x, v.y);
+                lo = make_float2(v.z, v.w);
+            }
+            const f2 x = sacc[q][p];
+            const f2 sum = add2(hi, x);  // TwoSum: sum + e == hi + x exactly
+            const f2 bb = sub2(sum, hi);
+            const f2 e = add2(sub2(hi, sub2(sum, bb)), sub2(x, bb));
+            lo = add2(lo, e);
+            if (last) {
+                sacc[q][p] = add2(sum, lo);
+            } else {
+                *t = make_float4(sum.x, sum.y, lo.x, lo.y);
+                sacc[q][p] = F2(0.0f);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Epilogue of a segment: the parameter gradients from the six factored
 // sums, then either their output or (fit) the Adam update with the box
@@ -119,7 +164,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     const int nb = a.bwd_pf ? 2 : 1;                // stages (double-buffered with prefetch)
     float *tg = tv + a.C * SLG;                     // (tape depth = checkpoint interval here)
     float *trb = tg + a.C * SLG;                    // nb tapes: targets, then seeds (MSE only)
-    float *ckb = tv + (DENSE ? 2 : 2 + nb) * a.C * SLG;  // nb checkpoint stages [4][SLG]
+    float *ckb = tv + (DENSE ? 2 : 2 + nb) * a.C * SLG;  // nb checkpoint stages [STATE_ROWS][SLG]
     const int Ns = sc.n_veh;
     const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
@@ -160,14 +205,16 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
             for (int k = obs_k, r = obs_row; k < c0 + n && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
                 prefetch_row<NP>(tr + (k - c0) * SLG + wb, yrow, lane, vx, vy);
         }
-        float *ck = ckb + par * 4 * SLG;
-        const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+        float *ck = ckb + par * STATE_ROWS * SLG;
+        const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * STATE_ROWS * Ns + wl;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * Ns, lane, vx, vy);
+        for (int f = 0; f < STATE_ROWS; ++f)
+            prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * Ns, lane, vx, vy);
         cp_async_commit();
     };
 
     const int n_ck = (sc.K + a.C - 1) / a.C;
+    const int fold_every = max(1, FOLD_STEPS / a.C);  // checkpoint segments per fold of the gradient sums
     if (a.bwd_pf) prefetch_segment(n_ck - 1);
     for (int cs = n_ck - 1; cs >= 0; --cs) {
         const int c0 = cs * a.C;
@@ -179,16 +226,17 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         if (!a.bwd_pf) prefetch_segment(cs);
         cp_async_wait<0>();  // this segment's targets and checkpoint (this thread's own slots)
         {
-            const float *ck = ckb + par * 4 * SLG + wb;
+            const float *ck = ckb + par * STATE_ROWS * SLG + wb;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
                 const f2 ph = lds2(ck + q), pl = lds2(ck + SLG + q), v = lds2(ck + 2 * SLG + q);
-                const f2 gp = lds2(ck + 3 * SLG + q);
+                const f2 gp = lds2(ck + 3 * SLG + q), vc = lds2(ck + 4 * SLG + q);
                 st[p].ph = make_float2(vx[p] ? ph.x : 0.0f, vy[p] ? ph.y : 0.0f);
                 st[p].pl = make_float2(vx[p] ? pl.x : 0.0f, vy[p] ? pl.y : 0.0f);
                 st[p].v = make_float2(vx[p] ? v.x : 0.0f, vy[p] ? v.y : 0.0f);
                 st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+                st[p].vc = make_float2(vx[p] ? vc.x : 0.0f, vy[p] ? vc.y : 0.0f);
             }
         }
         if (a.bwd_pf && cs > 0) prefetch_segment(cs - 1);  // lands while this segment runs
@@ -219,16 +267,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 obs_k += sc.obs_stride;
                 ++obs_row;
             }
-            f2 vcur[NP], vh[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
-            const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
-            leader_vals2<NP>(vcur, vh, lane, lead_in);
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
-                euler2(st[p], as, vh[p], dt);
-            }
+            step_pairs<NP, D4>(g, st, kc, sc, xp);
         }
         if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
             if (DENSE) {
@@ -333,8 +372,12 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 --row_hi;
             }
         }
+        // a fold window is fold_every checkpoint segments, counted from the last
+        if (cs > 0 && (n_ck - cs) % fold_every == 0)
+            fold_sums<NP, WD>(a, s_idx, g, sacc, n_ck - cs > fold_every, false);
         grp_sync(g);  // the tape may be overwritten by the next segment
     }
+    if (n_ck > fold_every) fold_sums<NP, WD>(a, s_idx, g, sacc, true, true);
 
     segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {
@@ -360,7 +403,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
     const int T = a.tape_T;                         // tape depth (steps per block)
     float *tg = tv + T * SLG;
     float *trb = tg + T * SLG;                      // nb tapes: targets, then seeds (MSE only)
-    float *ckb = tv + (DENSE ? 2 : 2 + nb) * T * SLG;  // nb state stages [4][SLG]
+    float *ckb = tv + (DENSE ? 2 : 2 + nb) * T * SLG;  // nb state stages [STATE_ROWS][SLG]
     const int Ns = sc.n_veh;
     const int wl = lb + wb;                         // scenario-local index of this warp's first slot
     const float dt = sc.dt;
@@ -395,10 +438,10 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
     auto n_sub = [&](int cs) { return (seg_len(cs) + T - 1) / T; };
     auto block_src = [&](int cs, int j, const float *&base, size_t &stride) {
         if (j == 0) {
-            base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+            base = a.ckpt + sc.ckpt_off + (size_t)cs * STATE_ROWS * Ns + wl;
             stride = (size_t)Ns;
         } else {
-            base = a.sub_ckpt + (size_t)(j - 1) * 4 * a.N_total + sg.veh_begin + wb;
+            base = a.sub_ckpt + (size_t)(j - 1) * STATE_ROWS * a.N_total + sg.veh_begin + wb;
             stride = (size_t)a.N_total;
         }
     };
@@ -415,29 +458,20 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
             for (int k = obs_k, r = obs_row; k < b0 + bn && r < sc.n_obs; k += sc.obs_stride, ++r, yrow += Ns)
                 prefetch_row<NP>(tr + (k - b0) * SLG + wb, yrow, lane, vx, vy);
         }
-        float *ck = ckb + par * 4 * SLG;
+        float *ck = ckb + par * STATE_ROWS * SLG;
         const float *base;
         size_t stride;
         block_src(cs, j, base, stride);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * stride, lane, vx, vy);
+        for (int f = 0; f < STATE_ROWS; ++f)
+            prefetch_row<NP>(ck + f * SLG + wb, base + (size_t)f * stride, lane, vx, vy);
         cp_async_commit();
     };
     // one forward step of the pair state (the leader's speed by shuffle)
-    auto fwd_step = [&]() {
-        f2 vcur[NP], vh[NP];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
-        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
-        leader_vals2<NP>(vcur, vh, lane, lead_in);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
-            euler2(st[p], as, vh[p], dt);
-        }
-    };
+    auto fwd_step = [&]() { step_pairs<NP, D4>(g, st, kc, sc, xp); };
 
     const int n_ck = (sc.K + a.C - 1) / a.C;
+    const int fold_every = max(1, FOLD_STEPS / a.C);  // checkpoint segments per fold of the gradient sums
     int par = 0;
     bool have_next = false;  // the next block's stage is already being filled
     if (a.bwd_pf && n_sub(n_ck - 1) == 1) {
@@ -448,7 +482,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
       const int nsub = n_sub(cs);
       if (nsub > 1) {  // forward pass over the segment writing the sub-checkpoints
         {
-            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * 4 * Ns + wl;
+            const float *base = a.ckpt + sc.ckpt_off + (size_t)cs * STATE_ROWS * Ns + wl;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
@@ -457,11 +491,12 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 st[p].v = load_pair(base + 2 * (size_t)Ns, q, vx[p], vy[p]);
                 const f2 gp = load_pair(base + 3 * (size_t)Ns, q, vx[p], vy[p]);
                 st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+                st[p].vc = load_pair(base + 4 * (size_t)Ns, q, vx[p], vy[p]);
             }
         }
         for (int j = 1; j < nsub; ++j) {
             for (int s = 0; s < T; ++s) fwd_step();
-            float *row = a.sub_ckpt + (size_t)(j - 1) * 4 * a.N_total + sg.veh_begin + wb;
+            float *row = a.sub_ckpt + (size_t)(j - 1) * STATE_ROWS * a.N_total + sg.veh_begin + wb;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
@@ -469,6 +504,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 store_pair(row + (size_t)a.N_total, q, st[p].pl, vx[p], vy[p]);
                 store_pair(row + 2 * (size_t)a.N_total, q, st[p].v, vx[p], vy[p]);
                 store_pair(row + 3 * (size_t)a.N_total, q, st[p].gap, vx[p], vy[p]);
+                store_pair(row + 4 * (size_t)a.N_total, q, st[p].vc, vx[p], vy[p]);
             }
         }
         __threadfence_block();  // the rows are read back below (this thread's own slots)
@@ -482,16 +518,17 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
         float *tr = trb + par * T * SLG;
         cp_async_wait<0>();  // this block's targets and starting state (this thread's own slots)
         {
-            const float *ck = ckb + par * 4 * SLG + wb;
+            const float *ck = ckb + par * STATE_ROWS * SLG + wb;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
                 const f2 ph = lds2(ck + q), pl = lds2(ck + SLG + q), v = lds2(ck + 2 * SLG + q);
-                const f2 gp = lds2(ck + 3 * SLG + q);
+                const f2 gp = lds2(ck + 3 * SLG + q), vc = lds2(ck + 4 * SLG + q);
                 st[p].ph = make_float2(vx[p] ? ph.x : 0.0f, vy[p] ? ph.y : 0.0f);
                 st[p].pl = make_float2(vx[p] ? pl.x : 0.0f, vy[p] ? pl.y : 0.0f);
                 st[p].v = make_float2(vx[p] ? v.x : 0.0f, vy[p] ? v.y : 0.0f);
                 st[p].gap = make_float2(vx[p] ? gp.x : INFINITY, vy[p] ? gp.y : INFINITY);
+                st[p].vc = make_float2(vx[p] ? vc.x : 0.0f, vy[p] ? vc.y : 0.0f);
             }
         }
         // start filling the other stage with the next block when its state exists
@@ -532,16 +569,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 obs_k += sc.obs_stride;
                 ++obs_row;
             }
-            f2 vcur[NP], vh[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
-            const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
-            leader_vals2<NP>(vcur, vh, lane, lead_in);
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
-                euler2(st[p], as, vh[p], dt);
-            }
+            step_pairs<NP, D4>(g, st, kc, sc, xp);
         }
         if (c0 + n == sc.K) {  // state is now at step K: seed of the final step
             if (DENSE) {
@@ -649,7 +677,10 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
         grp_sync(g);  // the tape may be overwritten by the next block
         if (a.bwd_pf) par ^= 1;
       }
+      if (cs > 0 && (n_ck - cs) % fold_every == 0)
+          fold_sums<NP, WD>(a, s_idx, g, sacc, n_ck - cs > fold_every, false);
     }
+    if (n_ck > fold_every) fold_sums<NP, WD>(a, s_idx, g, sacc, true, true);
 
     segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {

@@ -90,7 +90,7 @@ void plan_batch(const idm_batch_t *b, int C, int cap, BatchPlan &P)
         d.ckpt_off = ck;
         traj += (long long)(d.K + 1) * d.n_veh;
         tgt += (long long)d.n_obs * d.n_veh;
-        ck += 4LL * ((d.K + C - 1) / C) * d.n_veh;
+        ck += (long long)idm::STATE_ROWS * ((d.K + C - 1) / C) * d.n_veh;
         P.max_K = std::max(P.max_K, d.K);
         // greedy packing of this scenario's lanes
         int fill = 0, begin = 0;
@@ -187,6 +187,7 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
     a.N_total = N;
     a.G = G;
     Pp->loss_per_seg = G;
+    Pp->k_max = max_K;
     CK(idm::launch_prep_gap(b->lane_off, L, p_init, b->length, N, (float *)c->g0.p, a.status, st));
     return forward_grid(c, Pp, (int)std::max<size_t>(n_seg, 1));
 }
@@ -286,6 +287,7 @@ int idm_batch_forward(idm_ctx_t *c, const idm_batch_t *b, const idm_params_t *pa
     if ((rc = prepare_batch(c, b, params, p_init, v_init, false, &P, BP, st))) return rc;
     P.a.work = (int *)c->ctl.p + CTL_WORK_F;
     P.a.traj = traj;
+    P.a.events = event_counters(c);
     CK(idm::launch_forward(P.vpt_f, P.G_f, true, false, false, P.a, P.grid_f, P.wpb_f, st));
     return IDM_OK;
 }

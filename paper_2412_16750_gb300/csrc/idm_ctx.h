@@ -51,6 +51,7 @@ struct idm_ctx {
     idm::abi::Buf scen_tab, scen_seg_off, scen_seg_idx, lane_off_dev;  // batched scenarios
     idm::abi::Buf rec_oyy, rec_oyc, rec_multi, rec_tape, rec_mom, rec_thm, rec_acc, rec_kmax;  // reconstruction mode
     idm::abi::Buf fit_part;            // single-launch fit: loss partials of every iteration
+    idm::abi::Buf gsum;                // adjoint: compensated totals of the gradient sums [6][2][N]
     int fit_mode = IDM_FIT_AUTO;
     int last_fit_form = 0;             // IDM_FIT_GRAPH or IDM_FIT_SINGLE_LAUNCH of the last idm_fit (0: none)
     cudaStream_t cap_stream = nullptr;
@@ -58,6 +59,8 @@ struct idm_ctx {
     unsigned char fit_key[640] = {0};  // arguments the cached fit graph was captured with
     size_t fit_key_len = 0;
     int profiling = 0;
+    int count_events = 0;              // idm_forward / idm_batch_forward add to the event counters
+    int no_alloc = 0;                  // planning-only context: ensure() fails instead of allocating
     std::vector<cudaEvent_t> ev;       // per fit iteration: fwd begin/end, adjoint begin/end
     int ev_used = 0;                   // iterations recorded by the cached graph
 };
@@ -69,11 +72,21 @@ int fail(idm_ctx *c, int code, const char *fmt, ...);
 int cuda_fail(idm_ctx *c, cudaError_t e, const char *what);
 int ensure(idm_ctx *c, Buf &b, size_t bytes, const char *name);
 int ensure_status(idm_ctx *c);
+// The status buffer: status word (unsigned) at byte 0, the two 64-bit event
+// counters (gap-floor hits, kink band) at byte STATUS_EVENTS_OFF.
+constexpr size_t STATUS_BYTES = 32;
+constexpr size_t STATUS_EVENTS_OFF = 16;
+// Event counters for a forward launch of this context (NULL when off).
+unsigned long long *event_counters(idm_ctx *c);
 int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
 // Forward shape for the segment capacity of the adjoint shape (vpt, G).
 void forward_shape(int vpt, int G, int *vpt_f, int *G_f);
 // Parameter arrays: required unless the scene has no vehicles.
 int check_params(idm_ctx *c, const idm_params_t *p, bool all, long long n_vehicles);
+// Scene (lanes, lengths, max_lane) and simulation settings (K >= 1, finite
+// dt > 0, finite a_min < 0) of the single-scene calls.
+int check_scene(idm_ctx *c, const idm_scene_t *s);
+int check_sim(idm_ctx *c, const idm_sim_t *s);
 int forward_grid(idm_ctx *c, Prep *P, int L);
 int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, int L);
 // Capture (or reuse) the n_iter-iteration fit graph for plan P and launch it.

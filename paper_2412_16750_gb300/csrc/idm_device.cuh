@@ -91,6 +91,22 @@ __device__ __forceinline__ void sigmoid2(f2 x, f2 e, f2 &sig, f2 &sig_neg)
     sig_neg = make_float2(x.x >= 0.0f ? ed.x : d.x, x.y >= 0.0f ? ed.y : d.y);
 }
 
+// ln(1 + e) for e = exp(-|x|) in [0, 1]: for e < 2^-6 the series
+// e - e^2/2 + e^3/3 - e^4/4 (truncation error below e^5/5 < 2e-10);
+// otherwise ln 2 * log2(1 + e).  (log2 of the rounded 1 + e keeps only the
+// bits of e above 2^-24: a relative error of up to 2^-24 / e, which for the
+// e ~ 5e-5 of ordinary driving is ~1e-3 of the term.)
+// The direct form is evaluated only when some lane of the warp needs it
+// (the result of each element does not depend on the other lanes).
+__device__ __forceinline__ f2 log1p_exp2(f2 e)
+{
+    const f2 series = mul2(e, fma2(e, fma2(e, fma2(e, F2(-0.25f), F2(1.0f / 3.0f)), F2(-0.5f)), F2(1.0f)));
+    const bool sx = e.x < 0.015625f, sy = e.y < 0.015625f;
+    if (__all_sync(FULL, sx && sy)) return series;
+    const f2 direct = mul2(lg2(add2(F2(1.0f), e)), F2(LN2));
+    return make_float2(sx ? series.x : direct.x, sy ? series.y : direct.y);
+}
+
 // Per-vehicle constants of one call, for a pair of vehicles.
 struct VehConst2 {
     f2 inv_v0;          // 1 / v0
@@ -98,7 +114,11 @@ struct VehConst2 {
     f2 delta;
 };
 
-__device__ __forceinline__ float c_of(float am, float b) { return __fmul_rn(0.5f, rsqrtf(__fmul_rn(am, b))); }
+// c = 1 / (2 sqrt(a_max b)), correctly rounded steps (a per-vehicle constant:
+// an approximate square root would perturb every step of the vehicle the
+// same way).
+__device__ __forceinline__ float c_of(float am, float b) { return __fdiv_rn(0.5f, __fsqrt_rn(__fmul_rn(am, b))); }
+
 
 // (v / v0)^delta.  D4: every vehicle of the warp has delta == 4 (decided once
 // per segment), so the power is two squarings.
@@ -139,22 +159,36 @@ __device__ __forceinline__ f2 accel_star2(f2 v, f2 gap_raw, f2 vh, const VehCons
     const f2 a = mul2(k.am, sub2(sub2(F2(1.0f), rd), mul2(z, z)));  // Eq. 2
     bool bx, by;
     const f2 a_lb = lower_bound(mul2(v, F2(-inv_dt)), a_min, bx, by);  // Sec. III-C
-    const Soft2 s2 = softplus2(sub2(a, a_lb));
-    return add2(a_lb, s2.sp);
+    // a_lb + sp(a - a_lb) = max(a, a_lb) + ln(1 + exp(-|a - a_lb|)): the
+    // large a_lb (a_min in ordinary driving) cancels exactly in the max
+    // instead of through the rounded difference, so a* keeps the precision
+    // of a rather than that of |a_lb|
+    const f2 x = sub2(a, a_lb);
+    const f2 e = make_float2(ex2_approx(fabsf(x.x) * -LOG2E), ex2_approx(fabsf(x.y) * -LOG2E));
+    return add2(vmax(a, a_lb), log1p_exp2(e));
 }
 
 // Vehicle-pair state: absolute position as an unevaluated float pair
 // (ph + pl, ph the float32 position, pl the accumulated rounding error),
-// speed, and raw gap to the leader.
+// speed as a Kahan-compensated sum (v the float32 running sum of the
+// increments dt a*, vc minus its lost low part: the speed is v - vc), and
+// raw gap to the leader.  The step's model is evaluated at v, which stays
+// within an ulp or so of the speed.  Without the compensation the rounding
+// of v at every step (half an ulp, ~1e-6 m/s at 20 m/s) accumulates into a
+// position drift of ~1 cm over 2,000 steps; the gap moves with the
+// compensated speeds of both vehicles (vh - v + vc - vch), so that it stays
+// the difference of the positions.
 struct State2 {
-    f2 ph, pl, v, gap;
+    f2 ph, pl, v, gap, vc;
 };
 
 // Explicit Euler step (Eq. 3): positions use the old speeds, so the gap moves
 // by dt (vh - v).  The position is accumulated with TwoSum plus the exact
-// rounding error of dt*v (en = d - dt*v, so the error is -en), keeping
-// ph + pl within ~1e-10 relative of the exact sum.
-__device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, float dt)
+// rounding error of dt*v (en = d - dt*v, so the error is -en) and the speed's
+// compensation (-dt vc), keeping ph + pl within ~1e-10 relative of the sum of
+// dt times the speeds.  The speed takes dt a* by Kahan's compensated
+// summation.
+__device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, f2 vch, float dt)
 {
     const f2 d = mul2(F2(dt), s.v);
     const f2 en = fma2(F2(-dt), s.v, d);
@@ -162,10 +196,16 @@ __device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, float dt)
     const f2 bb = sub2(t, s.ph);
     const f2 err = add2(sub2(s.ph, sub2(t, bb)), sub2(d, bb));
     s.ph = t;
-    s.pl = add2(s.pl, sub2(err, en));
-    s.gap = fma2(F2(dt), sub2(vh, s.v), s.gap);
-    s.v = fma2(F2(dt), a_star, s.v);
+    s.pl = fma2(F2(-dt), s.vc, add2(s.pl, sub2(err, en)));
+    s.gap = fma2(F2(dt), add2(sub2(vh, s.v), sub2(s.vc, vch)), s.gap);
+    const f2 y = sub2(mul2(F2(dt), a_star), s.vc);
+    const f2 tv = add2(s.v, y);
+    s.vc = sub2(sub2(tv, s.v), y);
+    s.v = tv;
 }
+
+// The speed of the state: the running sum minus its compensation.
+__device__ __forceinline__ f2 speed2(const State2 &s) { return sub2(s.v, s.vc); }
 
 // ph + pl - y.  ph - y is exact when the target is within a factor two of the
 // position (Sterbenz) and otherwise rounds at the scale of the residual.

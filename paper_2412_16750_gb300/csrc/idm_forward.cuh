@@ -17,7 +17,10 @@ struct FwdFlags {
     bool traj, vtraj, ckpt, eval;
 };
 
-template <int NP, bool D4>
+// COUNT: also count the vehicle-steps with the raw gap below the floor and
+// those within IDM_KINK_BAND of the kink of the lower bound into a.events
+// (a separate instantiation, so the plain forward carries no cost of it).
+template <int NP, bool D4, bool COUNT = false>
 __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc &sc, int s_idx, int lb, Grp &g,
                                                 const VehConst2 (&kc)[NP], State2 (&st)[NP], const bool (&vx)[NP],
                                                 const bool (&vy)[NP], FwdFlags f)
@@ -29,9 +32,10 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     int xp = 0;
     int obs_k = sc.obs_stride, obs_row = 0;  // next observed step and its target row (eval)
     float esum = 0.0f, ecomp = 0.0f;         // squared residuals (eval), Kahan over observed steps
+    int n_floor = 0, n_kink = 0;             // event counts of this thread's slots (count)
     for (int k = 0;; ++k) {
         if (f.ckpt && k == next_ck && k < sc.K) {
-            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * 4 * Ns + wl;
+            float *base = a.ckpt + sc.ckpt_off + (size_t)ck_idx * STATE_ROWS * Ns + wl;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
@@ -39,6 +43,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
                 store_pair(base + (size_t)Ns, q, st[p].pl, vx[p], vy[p]);
                 store_pair(base + 2 * (size_t)Ns, q, st[p].v, vx[p], vy[p]);
                 store_pair(base + 3 * (size_t)Ns, q, st[p].gap, vx[p], vy[p]);
+                store_pair(base + 4 * (size_t)Ns, q, st[p].vc, vx[p], vy[p]);
             }
             next_ck += a.C;
             ++ck_idx;
@@ -49,7 +54,7 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             for (int p = 0; p < NP; ++p) {
                 const int q = 64 * p + 2 * lane;
                 if (f.traj) store_pair(a.traj + row, q, position2(st[p]), vx[p], vy[p]);
-                if (f.vtraj) store_pair(a.vtraj + row, q, st[p].v, vx[p], vy[p]);
+                if (f.vtraj) store_pair(a.vtraj + row, q, speed2(st[p]), vx[p], vy[p]);
             }
         }
         if (f.eval && k == obs_k) {
@@ -69,17 +74,19 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
             ++obs_row;
         }
         if (k == sc.K) break;
-
-        f2 vcur[NP], vh[NP];
+        if (COUNT) {
+            // the step's raw gap below the floor (derivative 0 there), and -v/dt
+            // within IDM_KINK_BAND of a_min, as the step below evaluates it
 #pragma unroll
-        for (int p = 0; p < NP; ++p) vcur[p] = st[p].v;
-        const float lead_in = grp_lead_in(g, vcur[NP - 1].y, xp);
-        leader_vals2<NP>(vcur, vh, lane, lead_in);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
-            euler2(st[p], as, vh[p], sc.dt);
+            for (int p = 0; p < NP; ++p) {
+                const f2 lbv = mul2(st[p].v, F2(-sc.inv_dt));
+                n_floor += (vx[p] && st[p].gap.x < IDM_GAP_FLOOR) + (vy[p] && st[p].gap.y < IDM_GAP_FLOOR);
+                n_kink += (vx[p] && fabsf(__fsub_rn(lbv.x, sc.a_min)) < IDM_KINK_BAND) +
+                          (vy[p] && fabsf(__fsub_rn(lbv.y, sc.a_min)) < IDM_KINK_BAND);
+            }
         }
+
+        step_pairs<NP, D4>(g, st, kc, sc, xp);
     }
     bool bad = false;
 #pragma unroll
@@ -88,6 +95,11 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
         if (vy[p] && !(isfinite(st[p].v.y) && isfinite(st[p].ph.y))) bad = true;
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, IDM_STATUS_NONFINITE);
+    if (COUNT) {
+        const int cf = __reduce_add_sync(FULL, (unsigned)n_floor), ck = __reduce_add_sync(FULL, (unsigned)n_kink);
+        if (lane == 0 && cf) atomicAdd(a.events, (unsigned long long)cf);
+        if (lane == 0 && ck) atomicAdd(a.events + 1, (unsigned long long)ck);
+    }
     if (f.eval) {
         const double part = warp_sum_double((double)esum - (double)ecomp) * (double)sc.inv_nobs;
         if (lane == 0) a.eval_part[(size_t)s_idx * g.G + g.w] = part;

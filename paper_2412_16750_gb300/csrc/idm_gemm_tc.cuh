@@ -100,11 +100,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 }
 
 // Wait until the phase with the given parity has completed; false when the
-// iteration or time limit runs out first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// iteration limit (`limit` polls) or the time limit runs out first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = WAIT_ITERS)
 {
     uint64_t t0 = 0;
-    for (uint32_t i = 0; i < WAIT_ITERS; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -132,10 +132,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 
 // mbar_wait that also gives up as soon as another role of the CTA has set
 // the shared abort flag, and sets it when it gives up itself.
-__device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, volatile int *abort,
+                                                uint32_t limit = WAIT_ITERS)
 {
     uint64_t t0 = 0;
-    for (uint32_t i = 0; i < WAIT_ITERS; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -244,9 +245,11 @@ __device__ __forceinline__ void load_stage(const TileArgs &t, int k0, int kw, ui
 // Accumulate the tile into tensor memory at `tmem`.  Every thread of the CTA
 // calls it.  Returns false (status recorded, issued work drained) when a
 // wait gave up; returns true with *empty set when the K range is empty (the
-// accumulator is then not written).
+// accumulator is then not written).  `limit` bounds the polls of each wait
+// for the tensor core (WAIT_ITERS normally; the drain after a give-up always
+// uses WAIT_ITERS).
 __device__ __forceinline__ bool mainloop(const TileArgs &t, uint8_t *smem, uint32_t tmem, unsigned *status,
-                                         bool *empty)
+                                         bool *empty, uint32_t limit = WAIT_ITERS)
 {
     const int tid = threadIdx.x;
     const uint32_t sA = smem_u32(smem), sB = sA + 2 * A_STAGE_BYTES;
@@ -279,7 +282,7 @@ __device__ __forceinline__ bool mainloop(const TileArgs &t, uint8_t *smem, uint3
             if (kt >= 1) {
                 // every thread takes the same decision, so that no thread
                 // leaves while others still wait at a CTA barrier
-                const bool done = __syncthreads_and(mbar_wait(bars + 8 * nb, (uint32_t)(((kt - 1) >> 1) & 1)));
+                const bool done = __syncthreads_and(mbar_wait(bars + 8 * nb, (uint32_t)(((kt - 1) >> 1) & 1), limit));
                 if (!done) {
                     if (tid == 0) atomicOr(status, IDM_STATUS_TIMEOUT);
                     mbar_wait(bars + 8 * buf, (uint32_t)((kt >> 1) & 1));  // drain what was issued
@@ -291,7 +294,7 @@ __device__ __forceinline__ bool mainloop(const TileArgs &t, uint8_t *smem, uint3
         }
     }
     const int last = nkt - 1;
-    const bool done = __syncthreads_and(mbar_wait(bars + 8 * (last & 1), (uint32_t)((last >> 1) & 1)));
+    const bool done = __syncthreads_and(mbar_wait(bars + 8 * (last & 1), (uint32_t)((last >> 1) & 1), limit));
     if (!done) {
         if (tid == 0) atomicOr(status, IDM_STATUS_TIMEOUT);
         mbar_wait(bars + 8 * (last & 1), (uint32_t)((last >> 1) & 1));

@@ -73,7 +73,26 @@ struct SimArgs {
     // into double-buffered shared stages while the current segment runs
     // (needs more shared memory), 0 = load each segment when it starts
     int bwd_pf;
+    // adjoint: compensated running totals of the six factored gradient sums,
+    // per segment 6 x (capacity / 2) float4 (16-byte aligned); needed
+    // (non-NULL) when a horizon exceeds GSUM_FOLD_STEPS
+    float *gsum;
+    // forward: event counters (NULL = not counted): [0] vehicle-steps with the
+    // raw gap below the floor, [1] vehicle-steps within IDM_KINK_BAND of the
+    // kink of the lower bound max(-v/dt, a_min)
+    unsigned long long *events;
 };
+
+// Steps of FP32 accumulation between two compensated folds of the gradient
+// sums (idm_adjoint.cuh); a call whose longest horizon exceeds it needs gsum:
+// gsum_bytes(segments, capacity) bytes.
+inline size_t gsum_bytes(size_t n_seg, int capacity) { return n_seg * (size_t)capacity * 12 * sizeof(float); }
+constexpr int GSUM_FOLD_STEPS = 256;
+
+// Floats per vehicle of a stored state (checkpoints, sub-checkpoints, the
+// adjoint's state stage): position high and low parts, speed, raw gap and the
+// compensation of the speed sum (State2).
+constexpr int STATE_ROWS = 5;
 
 // Launchers (idm_sim.cu).  Return cudaError_t of the launch.
 cudaError_t launch_prep_gap(const int *lane_off, int n_lanes, const float *p_init, const float *length,

@@ -158,19 +158,37 @@ cudaError_t launch_gather(int N, const int32_t *perm, int count, const float *co
 
 // dst[r][j] = src[r][perm[j]] for a row-major [n_rows][N] matrix (columns
 // are vehicles): coalesced writes, gathered reads.
-__global__ void gather_rows_kernel(int N, int n_rows, const int32_t *perm, const float *src, float *dst)
+// dst[r][j] = src[r][perm[j]] over the flattened [n_rows][N] index space:
+// block b covers elements [b * ROWS_CHUNK, (b + 1) * ROWS_CHUNK), so the blocks
+// resident at any time (dispatched in index order) work on one or two rows.
+// The random reads of a row then hit its copy in L2 (each 32-byte sector is
+// fetched from DRAM once and serves all eight of its elements) instead of
+// fetching a sector per element, and perm stays in L2 across rows.
+constexpr int ROWS_CHUNK = 2048;
+
+__global__ void __launch_bounds__(256) gather_rows_kernel(int N, long long total, const int32_t *perm,
+                                                          const float *src, float *dst)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    const int s = perm[j];
-    for (int r = blockIdx.y; r < n_rows; r += gridDim.y) dst[(size_t)r * N + j] = src[(size_t)r * N + s];
+    const long long base = (long long)blockIdx.x * ROWS_CHUNK;
+    long long r = base / N;
+    int j = (int)(base - r * N) + (int)threadIdx.x;
+    for (int e = threadIdx.x; e < ROWS_CHUNK; e += 256, j += 256) {
+        while (j >= N) {
+            j -= N;
+            ++r;
+        }
+        if (base + e >= total) return;
+        const size_t row = (size_t)r * (size_t)N;
+        dst[row + j] = __ldg(src + row + __ldg(perm + j));
+    }
 }
 
 cudaError_t launch_gather_rows(int N, int n_rows, const int32_t *perm, const float *src, float *dst, cudaStream_t st)
 {
     if (N > 0 && n_rows > 0) {
-        dim3 grid((N + 255) / 256, n_rows < 64 ? n_rows : 64);
-        gather_rows_kernel<<<grid, 256, 0, st>>>(N, n_rows, perm, src, dst);
+        const long long total = (long long)N * n_rows;
+        const long long blocks = (total + ROWS_CHUNK - 1) / ROWS_CHUNK;
+        gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(N, total, perm, src, dst);
     }
     return cudaGetLastError();
 }

@@ -60,6 +60,7 @@ struct GemmArgs {
     float lo[OUT], hi[OUT];
     unsigned *status;
     int stages;          // A stages of the persistent kernel
+    unsigned wait_iters; // polls per tensor-core wait before giving up (tc::WAIT_ITERS normally)
 };
 
 // Normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 and density phi(z) with erf
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(tc::NTHREADS) mlp_gemm_kernel(const GemmArgs g
     t.kb = blockIdx.z * g.k_chunk;
     t.ke = min(g.K, t.kb + g.k_chunk);
     bool empty = false;
-    const bool ok = tc::mainloop(t, smem, tmem, g.status, &empty);
+    const bool ok = tc::mainloop(t, smem, tmem, g.status, &empty, g.wait_iters);
     if (ok)
         epilogue_row<MODE>(g, t.m0 + threadIdx.x, tmem + ((uint32_t)(warp * 32) << 16), t.n0, 0, t.BN, empty, blockIdx.z,
                            blockIdx.x * 4 + warp, g.bias);
@@ -370,7 +371,9 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
             const int m0 = tile * tc::BM;
             for (int kt = 0; kt < nkt; ++kt, ++q) {
                 const int s = q % S;
-                int got = lane == 0 ? (int)tc::mbar_wait_abort(empty_bar(s), (uint32_t)(((q / S) & 1) ^ 1), abort) : 0;
+                int got = lane == 0 ? (int)tc::mbar_wait_abort(empty_bar(s), (uint32_t)(((q / S) & 1) ^ 1), abort,
+                                                               g.wait_iters)
+                                    : 0;
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -390,19 +393,22 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full_bar(s)) : "memory");
             }
         }
+        // after a give-up some copies may still be in flight: they land
+        // before the CTA leaves (in normal operation they already have)
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 1) {
         // ---- MMA issue (one thread) --------------------------------------------
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16(tc::BM, N);
-            bool ok = tc::mbar_wait_abort(wbar, 0, abort);
+            bool ok = tc::mbar_wait_abort(wbar, 0, abort, g.wait_iters);
             int q = 0, i = 0;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++i) {
                 const int acc = i & 1, u = i >> 1;
-                if (!(ok = tc::mbar_wait_abort(tempty_bar(acc), (uint32_t)((u & 1) ^ 1), abort))) break;
+                if (!(ok = tc::mbar_wait_abort(tempty_bar(acc), (uint32_t)((u & 1) ^ 1), abort, g.wait_iters))) break;
                 tc::fence_after_sync();
                 for (int kt = 0; kt < nkt && ok; ++kt, ++q) {
                     const int s = q % S;
-                    if (!(ok = tc::mbar_wait_abort(full_bar(s), (uint32_t)((q / S) & 1), abort))) break;
+                    if (!(ok = tc::mbar_wait_abort(full_bar(s), (uint32_t)((q / S) & 1), abort, g.wait_iters))) break;
                     // the stage was written by cp.async (generic proxy); the
                     // tensor core reads it through the async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i & 1, u = i >> 1;
-            int got = lane == 0 ? (int)tc::mbar_wait_abort(tfull_bar(acc), (uint32_t)(u & 1), abort) : 0;
+            int got = lane == 0 ? (int)tc::mbar_wait_abort(tfull_bar(acc), (uint32_t)(u & 1), abort, g.wait_iters) : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) break;
             tc::fence_after_sync();
@@ -718,6 +724,7 @@ struct idm_mlp {
     void *inf_arena = nullptr;
     bf16 *IH[2] = {};
     int inf_rows = 0;
+    unsigned wait_iters = idm::tc::WAIT_ITERS;  // polls per tensor-core wait (idm_mlp_set_wait_limit)
     char err[256] = {0};
 };
 
@@ -758,6 +765,7 @@ GemmArgs base_args(idm_mlp *n)
     GemmArgs g;
     memset(&g, 0, sizeof g);
     g.status = n->status;
+    g.wait_iters = n->wait_iters;
     return g;
 }
 
@@ -979,6 +987,7 @@ int idm_gemm_bf16(const void *A, const void *B, int32_t M, int32_t N, int32_t K,
     g.k_chunk = K;
     g.Cf = C;
     g.status = status;
+    g.wait_iters = idm::tc::WAIT_ITERS;
     cudaError_t e = gemm<F32_PART>(g, M, 1, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1122,6 +1131,21 @@ int idm_mlp_get_weights(idm_mlp_t *n, float *weights, void *stream)
     if (!n) return IDM_ERR_ARG;
     if (!weights) return mfail(n, IDM_ERR_ARG, "weights are required");
     MCK(cudaMemcpyAsync(weights, n->w, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return IDM_OK;
+}
+
+int idm_mlp_set_wait_limit(idm_mlp_t *n, uint32_t polls)
+{
+    if (!n) return IDM_ERR_ARG;
+    n->wait_iters = polls == 0 ? idm::tc::WAIT_ITERS : std::min<uint32_t>(polls, idm::tc::WAIT_ITERS);
+    return IDM_OK;
+}
+
+int idm_mlp_clear_status(idm_mlp_t *n, void *stream)
+{
+    if (!n) return IDM_ERR_ARG;
+    MCK(cudaMemsetAsync(n->status, 0, sizeof(unsigned), (cudaStream_t)stream));
+    MCK(cudaStreamSynchronize((cudaStream_t)stream));
     return IDM_OK;
 }
 

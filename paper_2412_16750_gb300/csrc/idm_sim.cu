@@ -138,8 +138,16 @@ cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *s
     return cudaGetLastError();
 }
 
+// Register budgets: 8 vehicles per thread (four pairs of state and constants)
+// need more than the 128 registers of 16 warps per SM: their blocks are
+// capped at 12 warps (one block per SM, up to 168 registers).
 template <int VPT>
-__global__ void __launch_bounds__(512)
+struct FwdBounds {
+    static constexpr int threads = VPT == 8 ? 384 : 512;
+};
+
+template <int VPT, bool COUNT>
+__global__ void __launch_bounds__(FwdBounds<VPT>::threads)
 forward_kernel(SimArgs a, FwdFlags f)
 {
     constexpr int NP = VPT / 2;
@@ -160,9 +168,9 @@ forward_kernel(SimArgs a, FwdFlags f)
         bool vx[NP], vy[NP];
         load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
         if (segment_is_d4<NP>(kc, vx, vy))
-            forward_segment<NP, true>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
+            forward_segment<NP, true, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
         else
-            forward_segment<NP, false>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
+            forward_segment<NP, false, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
     }
 }
 
@@ -231,11 +239,12 @@ cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, con
                            cudaStream_t st)
 {
     FwdFlags f{traj, vtraj, ckpt, a.eval_targets != nullptr && a.eval_part != nullptr};
+    const bool count = a.events != nullptr;
     void *fn = nullptr;
     switch (vpt) {
-    case 2: fn = (void *)forward_kernel<2>; break;
-    case 4: fn = (void *)forward_kernel<4>; break;
-    case 8: fn = (void *)forward_kernel<8>; break;
+    case 2: fn = count ? (void *)forward_kernel<2, true> : (void *)forward_kernel<2, false>; break;
+    case 4: fn = count ? (void *)forward_kernel<4, true> : (void *)forward_kernel<4, false>; break;
+    case 8: fn = count ? (void *)forward_kernel<8, true> : (void *)forward_kernel<8, false>; break;
     default: return cudaErrorInvalidValue;
     }
     const size_t smem = forward_smem_bytes(vpt, G, wpb);
@@ -336,9 +345,9 @@ int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool 
     void *fn = nullptr;
     if (!backward) {
         switch (vpt) {
-        case 2: fn = (void *)forward_kernel<2>; break;
-        case 4: fn = (void *)forward_kernel<4>; break;
-        case 8: fn = (void *)forward_kernel<8>; break;
+        case 2: fn = (void *)forward_kernel<2, false>; break;
+        case 4: fn = (void *)forward_kernel<4, false>; break;
+        case 8: fn = (void *)forward_kernel<8, false>; break;
         }
         smem = forward_smem_bytes(vpt, G, wpb);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -76,12 +76,12 @@ struct Grp {
     int lane;
     int bar;     // named barrier id (1 + group index in the block)
     int *cell;   // [2] work-item broadcast
-    float *xl;   // [2][G] leader exchange
+    float *xl;   // [2][G][2] leader exchange (speed, speed compensation)
     float *xf;   // [2][2][G] follower exchange
 };
 
 // Shared floats of one group's control area (cells + exchange cells).
-__host__ __device__ __forceinline__ int grp_ctrl_floats(int G) { return ((2 + 6 * G) + 3) & ~3; }
+__host__ __device__ __forceinline__ int grp_ctrl_floats(int G) { return ((2 + 8 * G) + 3) & ~3; }
 
 __device__ __forceinline__ void grp_sync(const Grp &g)
 {
@@ -101,7 +101,7 @@ __device__ __forceinline__ Grp make_grp(int G, float *ctrl)
     g.bar = 1 + warp / G;
     g.cell = reinterpret_cast<int *>(ctrl);
     g.xl = ctrl + 2;
-    g.xf = ctrl + 2 + 2 * G;
+    g.xf = ctrl + 2 + 4 * G;
     return g;
 }
 
@@ -115,14 +115,16 @@ __device__ __forceinline__ int grp_next(const Grp &g, int *work, int &par)
     return s;
 }
 
-// Leader speed of this warp's first slot (0 for the group's first warp);
-// last_v is this lane's value of the warp's last slot (used by lane 31).
-__device__ __forceinline__ float grp_lead_in(const Grp &g, float last_v, int &xp)
+// Leader speed and speed compensation of this warp's first slot (0 for the
+// group's first warp); last is this lane's pair of the warp's last slot
+// (used by lane 31).
+__device__ __forceinline__ float2 grp_lead_in(const Grp &g, float2 last, int &xp)
 {
-    if (g.G == 1) return 0.0f;
-    if (g.lane == 31) g.xl[xp * g.G + g.w] = last_v;
+    if (g.G == 1) return make_float2(0.0f, 0.0f);
+    float2 *c = reinterpret_cast<float2 *>(g.xl);
+    if (g.lane == 31) c[xp * g.G + g.w] = last;
     grp_sync(g);
-    const float r = g.w > 0 ? g.xl[xp * g.G + g.w - 1] : 0.0f;
+    const float2 r = g.w > 0 ? c[xp * g.G + g.w - 1] : make_float2(0.0f, 0.0f);
     xp ^= 1;
     return r;
 }
@@ -145,6 +147,29 @@ __device__ __forceinline__ void grp_follow_in(const Grp &g, float p_first, float
         in_v = c[g.G + g.w + 1];
     }
     xp ^= 1;
+}
+
+// One Euler step (Eq. 1-3 with the Sec. III-C bounds) of this thread's
+// vehicle pairs: the leaders' speeds and speed compensations by shuffle
+// (across warps through the group's cells), then a* and the state update.
+template <int NP, bool D4>
+__device__ __forceinline__ void step_pairs(const Grp &g, State2 (&st)[NP], const VehConst2 (&kc)[NP],
+                                           const ScenDesc &sc, int &xp)
+{
+    f2 vcur[NP], ccur[NP], vh[NP], ch[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        vcur[p] = st[p].v;
+        ccur[p] = st[p].vc;
+    }
+    const float2 lead_in = grp_lead_in(g, make_float2(vcur[NP - 1].y, ccur[NP - 1].y), xp);
+    leader_vals2<NP>(vcur, vh, g.lane, lead_in.x);
+    leader_vals2<NP>(ccur, ch, g.lane, lead_in.y);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const f2 as = accel_star2<D4>(st[p].v, st[p].gap, vh[p], kc[p], sc.inv_dt, sc.a_min);
+        euler2(st[p], as, vh[p], ch[p], sc.dt);
+    }
 }
 
 template <int NP>
@@ -175,12 +200,12 @@ __device__ __forceinline__ void load_vehicles(const SimArgs &a, const Seg &sg, i
                 vx[p] = ok;
                 kc[p].inv_v0.x = inv_v0; kc[p].T.x = T; kc[p].s0.x = s0; kc[p].am.x = am; kc[p].c.x = cc;
                 kc[p].delta.x = dl;
-                st[p].ph.x = ph; st[p].pl.x = 0.0f; st[p].v.x = v; st[p].gap.x = gap;
+                st[p].ph.x = ph; st[p].pl.x = 0.0f; st[p].v.x = v; st[p].gap.x = gap; st[p].vc.x = 0.0f;
             } else {
                 vy[p] = ok;
                 kc[p].inv_v0.y = inv_v0; kc[p].T.y = T; kc[p].s0.y = s0; kc[p].am.y = am; kc[p].c.y = cc;
                 kc[p].delta.y = dl;
-                st[p].ph.y = ph; st[p].pl.y = 0.0f; st[p].v.y = v; st[p].gap.y = gap;
+                st[p].ph.y = ph; st[p].pl.y = 0.0f; st[p].v.y = v; st[p].gap.y = gap; st[p].vc.y = 0.0f;
             }
         }
     }
@@ -219,7 +244,7 @@ __device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<co
 __device__ __forceinline__ void sts2(float *p, f2 x) { *reinterpret_cast<f2 *>(p) = x; }
 
 // Shared floats of one adjoint group: tape v/gap [T][G*SL], target/seed
-// tapes [T][G*SL] (MSE only), state stages [4][G*SL], control area; T is the tape depth (the checkpoint interval, or less when
+// tapes [T][G*SL] (MSE only), state stages [STATE_ROWS][G*SL], control area; T is the tape depth (the checkpoint interval, or less when
 // blocks restart from sub-checkpoints).  With prefetch the target tape and
 // the state stage are doubled and the next block's targets and starting
 // state are copied (cp.async) into the idle pair while the current block
@@ -227,7 +252,7 @@ __device__ __forceinline__ void sts2(float *p, f2 x) { *reinterpret_cast<f2 *>(p
 __host__ __device__ __forceinline__ int bwd_group_floats(int vpt, bool dense, int T, int G, bool pf)
 {
     const int nb = pf ? 2 : 1;
-    return ((dense ? 2 : 2 + nb) * T + 4 * nb) * 32 * vpt * G + grp_ctrl_floats(G);
+    return ((dense ? 2 : 2 + nb) * T + STATE_ROWS * nb) * 32 * vpt * G + grp_ctrl_floats(G);
 }
 
 }  // namespace idm

@@ -38,6 +38,7 @@ IDM_MLP_PREFIX = 20
 IDM_MLP_N_PARAMS = 153605
 
 GAP_FLOOR = 0.1
+KINK_BAND = 0.5
 
 _vp = ctypes.c_void_p
 
@@ -78,6 +79,8 @@ _SIGS = {
     "idm_ctx_destroy": (ctypes.c_int, [_vp]),
     "idm_last_error": (ctypes.c_char_p, [_vp]),
     "idm_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), _vp]),
+    "idm_set_event_counting": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "idm_event_counts": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "idm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "idm_max_lane_supported": (ctypes.c_int, []),
     "idm_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.POINTER(idm_scene_t), ctypes.POINTER(idm_sim_t)]),
@@ -123,6 +126,8 @@ _SIGS = {
     "idm_mlp_set_weights": (ctypes.c_int, [_vp, _vp, _vp]),
     "idm_mlp_get_weights": (ctypes.c_int, [_vp, _vp, _vp]),
     "idm_mlp_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "idm_mlp_clear_status": (ctypes.c_int, [_vp, _vp]),
+    "idm_mlp_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "idm_mlp_features": (ctypes.c_int, [ctypes.POINTER(idm_scene_t), _vp, _vp, ctypes.POINTER(idm_sim_t), _vp,
                                         ctypes.c_int32, _vp, ctypes.c_int32, _vp, ctypes.POINTER(idm_params_t), _vp,
                                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _vp]),
@@ -236,6 +241,17 @@ def idm_status(ctx, stream=None):
     flags = ctypes.c_uint32(0)
     rc = load().idm_status(ctx, ctypes.byref(flags), stream_ptr(stream))
     return rc, flags.value
+
+
+def idm_set_event_counting(ctx, on):
+    return check(ctx, load().idm_set_event_counting(ctx, 1 if on else 0))
+
+
+def idm_event_counts(ctx, stream=None):
+    """(gap_floor_hits, kink_near) since the last read; clears them."""
+    a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(ctx, load().idm_event_counts(ctx, stream_ptr(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def idm_set_tuning(ctx, vpt=0, warps_per_segment=0, ckpt_interval=8, warps_per_block=8):
@@ -493,6 +509,14 @@ def idm_mlp_status(mlp, stream=None):
     bits = ctypes.c_uint32(0)
     rc = load().idm_mlp_status(mlp, stream_ptr(stream), ctypes.byref(bits))
     return rc, bits.value
+
+
+def idm_mlp_clear_status(mlp, stream=None):
+    return mcheck(mlp, load().idm_mlp_clear_status(mlp, stream_ptr(stream)))
+
+
+def idm_mlp_set_wait_limit(mlp, polls):
+    return mcheck(mlp, load().idm_mlp_set_wait_limit(mlp, int(polls)))
 
 
 def idm_mlp_features(scene, p_init, v_init, sim, targets, obs_stride, perm, n_rows, X, label_params=None,

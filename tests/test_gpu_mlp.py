@@ -307,3 +307,41 @@ def test_gelu_approximation_error_bound(api):
     tol = 4e-7 * np.maximum(1.0, np.abs(zd))
     assert np.all(np.abs(g.double().cpu().numpy() - zd * cdf) <= tol)
     assert np.all(np.abs(dg.double().cpu().numpy() - (cdf + zd * pdf)) <= tol)
+
+
+@pytest.mark.parametrize("B", [1000, 2 * 152 * 128 + 77])
+def test_bounded_wait_gives_up_then_recovers(api, B):
+    """A tensor-core wait limited to one poll cannot see its copies or MMAs
+    finish: the kernel sets IDM_STATUS_TIMEOUT, drains what it issued, frees
+    its tensor memory and returns (the host sees IDM_ERR_TIMEOUT).  With the
+    default limit back, the same calls succeed and match the oracle, so the
+    context is usable and the tensor memory was released.  B = 1000 runs the
+    per-tile GEMM, the larger batch the persistent weight-stationary one;
+    loss_grad adds the split-K weight-gradient GEMMs."""
+    from paper_2412_16750_gb300 import lib
+    w = synth.mlp_init(7)
+    X, T = random_batch(B, 90)
+    Xc, Tc = to_bf16_cuda(X), torch.as_tensor(T, dtype=torch.float32, device="cuda")
+    net = api.Mlp(max_batch=B, weights=w)
+    net.set_wait_limit(1)
+    net.forward(Xc)
+    rc, bits = net.status()
+    assert rc == lib.IDM_ERR_TIMEOUT and bits & lib.IDM_STATUS_TIMEOUT
+    net.clear_status()
+    net.loss_grad(Xc, Tc)
+    rc, bits = net.status()
+    assert rc == lib.IDM_ERR_TIMEOUT and bits & lib.IDM_STATUS_TIMEOUT
+    net.set_wait_limit(0)
+    net.clear_status()
+    assert net.status() == (0, 0)
+    wb = bf16_weights(w)
+    S = net.forward(Xc).double().cpu().numpy()
+    np.testing.assert_allclose(S, M.forward(wb, X)["s"], rtol=1e-2, atol=1e-3)
+    loss, g = net.loss_grad(Xc, Tc)
+    torch.cuda.synchronize()
+    L_ref, g_ref = M.loss_grad(wb, X, synth.f32(T))
+    assert abs(loss.item() - L_ref) <= 1e-2 * L_ref
+    gd, rd = M.unpack(g.double().cpu().numpy()), M.unpack(g_ref)
+    for name, _ in M.SHAPES:
+        assert cosine(gd[name], rd[name]) >= 0.999, name
+    assert net.status() == (0, 0)

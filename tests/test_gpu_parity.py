@@ -3,7 +3,7 @@
 Tolerances (the workload statement's bar):
   * positions: max |p_gpu - p_oracle| <= 1e-3 m over 100 steps;
   * gradients: for each of the six parameters, ||g_gpu - g_ref|| / ||g_ref||
-    <= 1e-4, and every element within 1e-3 * max |g_ref|;
+    <= 1e-4, and every element within 1e-4 * max |g_ref|;
   * integer work (layout permutation): bit-exact.
 Both sides start from identical float32-representable inputs (dt is the
 float32 value of 0.1 on both sides).
@@ -21,7 +21,7 @@ DT = float(np.float32(0.1))
 A_MIN = -10.0
 POS_TOL = 1e-3
 GRAD_RTOL = 1e-4
-GRAD_ELEM = 1e-3
+GRAD_ELEM = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -319,6 +319,22 @@ def _oracle_fit_prefix(sc, th0, Y, K, s, n_iter, m):
     return th
 
 
+@pytest.mark.parametrize("N,R", [(1, 7), (5, 3), (2047, 2), (4099, 5), (100003, 3)])
+def test_gather_rows_bitexact(api, N, R):
+    """idm_gather_rows: dst[r][j] = src[r][perm[j]] over row-major [R][N]
+    arrays, bit for bit, for sizes that end mid-chunk and rows shorter than a
+    chunk."""
+    from paper_2412_16750_gb300 import lib
+    rng = np.random.default_rng(N + R)
+    perm = rng.permutation(N).astype(np.int32)
+    src = rng.normal(size=(R, N)).astype(np.float32)
+    ctx = api.Context()
+    d = torch.full((R, N), float("nan"), device="cuda")
+    lib.idm_gather_rows(ctx.handle, N, R, cuda(perm, torch.int32), cuda(src), d, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), src[:, perm])
+
+
 def test_layout_bitexact(api):
     rng = np.random.default_rng(109)
     N, L = 20000, 613
@@ -473,3 +489,110 @@ def test_braking_to_rest_delta_gradient(api):
     assert abs(loss - L) <= 1e-5 * L
     grad_close(g, g_ref)
     assert api.default_context().check_status() == 0
+
+
+# ---------------------------------------------------------------------------
+# config 4's fit window: 2,000 steps, checkpoints every 45 steps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("init", ["near_truth", "plain"])
+def test_long_horizon_gradients_2000_steps(api, init):
+    """Loss and gradients over 2,000 steps, every step observed, with the
+    checkpoint interval of the long-horizon fit (45 steps: tape blocks
+    restarted from sub-checkpoints), element by element against the FP64
+    adjoint.  The per-vehicle gradient sums run over 2,000 terms; their
+    compensated accumulation keeps them at the 1e-4 bar."""
+    rng = np.random.default_rng(116)
+    counts = [100, 100, 37, 100, 64, 100, 1, 100, 100, 3, 100, 100]   # ragged lanes, several segments
+    sc = synth.make_scene(counts, rng)
+    N, K = int(sum(counts)), 2000
+    Y = noisy_targets(sc, K, 1, rng)
+    if init == "plain":
+        theta = synth.plain_init(N)
+    else:
+        theta = synth.f32(sc["theta_true"] * rng.uniform(0.97, 1.03, size=(6, N)))
+        theta[5] = 4.0
+    L, g, gp, gv, _ = oracle_loss_grad(sc, theta, Y, K, 1)
+    ctx = api.Context(ckpt_interval=45)
+    Lg, gg, gpg, gvg = run_loss_grad(api, sc, theta, Y, K, 1, ctx=ctx)
+    assert ctx.check_status() == 0
+    assert Lg == pytest.approx(L, rel=1e-5)
+    grad_close(gg, g)
+    grad_close(np.stack([gpg, gvg]), np.stack([gp, gv]), rows=range(2))
+
+
+# ---------------------------------------------------------------------------
+# event counters: gap-floor hits and the kink band of the lower bound
+# ---------------------------------------------------------------------------
+
+def event_scene():
+    """Lanes built to hit the gap floor and to sit near v = 1 m/s (the kink of
+    max(-v/dt, a_min) at dt = 0.1 s, a_min = -10):
+      * lone vehicles with v0 = 0.98, 1.0, 1.03 m/s starting at their v0:
+        every step in the band;
+      * a follower 3 cm behind a faster leader (floor at its first steps),
+        braking hard through the band;
+      * a queue starting from rest (accelerating through 1 m/s), its followers
+        5-8 cm apart."""
+    p, v, th = [], [], []
+    counts = []
+    base = [30.0, 1.5, 2.0, 1.0, 2.0, 4.0]
+    for v0 in (0.98, 1.0, 1.03):
+        p.append(0.0); v.append(v0); th.append([v0] + base[1:]); counts.append(1)
+    p += [0.0, -5.03]; v += [10.0, 9.5]; th += [base, base]; counts.append(2)
+    q = [0.0]
+    for gap in (0.05, 0.07, 0.06, 0.08):
+        q.append(q[-1] - 5.0 - gap)
+    p += q; v += [0.0] * len(q); th += [base] * len(q); counts.append(len(q))
+    N = len(p)
+    return dict(lane_off=synth.lane_offsets(counts), length=synth.f32(np.full(N, 5.0)), p_init=synth.f32(p),
+                v_init=synth.f32(v), theta_true=synth.f32(np.array(th).T))
+
+
+def oracle_event_bounds(sc, K, margin_gap=1e-4, margin_kink=1e-3):
+    """Counts over steps 0..K-1 from the oracle's trajectory (gap of a
+    follower = P_leader - P - length_leader; the kink quantity -v/dt - a_min),
+    as [definitely inside, possibly inside] given the FP32/FP64 difference of
+    the states (well below the margins)."""
+    P, V = oracle.forward(sc["lane_off"], sc["length"], sc["theta_true"], sc["p_init"], sc["v_init"], K, DT, A_MIN)
+    N = P.shape[1]
+    lo = sc["lane_off"]
+    head = np.zeros(N, dtype=bool)
+    head[[int(lo[l]) for l in range(len(lo) - 1) if lo[l + 1] > lo[l]]] = True
+    gap = np.full((K, N), np.inf)
+    gap[:, 1:] = P[:K, :-1] - P[:K, 1:] - sc["length"][None, :-1]
+    gap[:, head] = np.inf
+    x = np.abs(-V[:K] / DT - A_MIN)
+    floor = (int((gap < 0.1 - margin_gap).sum()), int((gap < 0.1 + margin_gap).sum()))
+    kink = (int((x < 0.5 - margin_kink).sum()), int((x < 0.5 + margin_kink).sum()))
+    return floor, kink
+
+
+def test_event_counts_against_oracle(api):
+    sc = event_scene()
+    K = 200
+    (f_lo, f_hi), (k_lo, k_hi) = oracle_event_bounds(sc, K)
+    assert f_lo > 0 and k_lo >= 3 * K    # the scene does exercise both counters
+    ctx = api.Context()
+    th, p0, v0 = cuda(sc["theta_true"]), cuda(sc["p_init"]), cuda(sc["v_init"])
+    api.simulate(th, p0, v0, scene_of(api, sc), K, DT, A_MIN, ctx=ctx)
+    assert ctx.event_counts() == {"gap_floor_hits": 0, "kink_near": 0}      # off by default
+    ctx.set_event_counting(True)
+    api.simulate(th, p0, v0, scene_of(api, sc), K, DT, A_MIN, ctx=ctx)
+    got = ctx.event_counts()
+    assert f_lo <= got["gap_floor_hits"] <= f_hi, (got, f_lo, f_hi)
+    assert k_lo <= got["kink_near"] <= k_hi, (got, k_lo, k_hi)
+    assert ctx.event_counts() == {"gap_floor_hits": 0, "kink_near": 0}      # read clears
+    for _ in range(2):                                                      # counts accumulate until read
+        api.simulate(th, p0, v0, scene_of(api, sc), K, DT, A_MIN, ctx=ctx)
+    assert ctx.event_counts() == {"gap_floor_hits": 2 * got["gap_floor_hits"], "kink_near": 2 * got["kink_near"]}
+    # the batched forward counts the same events (two copies of the scene as scenarios)
+    lanes = np.diff(sc["lane_off"])
+    L = len(lanes)
+    b = api.Batch(np.array([0, L, 2 * L], np.int32), np.array([K, K], np.int32), np.array([DT, DT], np.float32),
+                  np.array([1, 1], np.int32), synth.lane_offsets(np.concatenate([lanes, lanes])),
+                  np.concatenate([sc["length"], sc["length"]]), A_MIN)
+    two = lambda x: cuda(np.concatenate([x, x], axis=-1))
+    api.batch_forward(two(sc["theta_true"]), two(sc["p_init"]), two(sc["v_init"]), b, ctx=ctx)
+    assert ctx.event_counts() == {"gap_floor_hits": 2 * got["gap_floor_hits"], "kink_near": 2 * got["kink_near"]}
+    assert ctx.check_status() == 0
