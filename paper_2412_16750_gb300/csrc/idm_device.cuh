@@ -91,22 +91,6 @@ __device__ __forceinline__ void sigmoid2(f2 x, f2 e, f2 &sig, f2 &sig_neg)
     sig_neg = make_float2(x.x >= 0.0f ? ed.x : d.x, x.y >= 0.0f ? ed.y : d.y);
 }
 
-// ln(1 + e) for e = exp(-|x|) in [0, 1]: for e < 2^-6 the series
-// e - e^2/2 + e^3/3 - e^4/4 (truncation error below e^5/5 < 2e-10);
-// otherwise ln 2 * log2(1 + e).  (log2 of the rounded 1 + e keeps only the
-// bits of e above 2^-24: a relative error of up to 2^-24 / e, which for the
-// e ~ 5e-5 of ordinary driving is ~1e-3 of the term.)
-// The direct form is evaluated only when some lane of the warp needs it
-// (the result of each element does not depend on the other lanes).
-__device__ __forceinline__ f2 log1p_exp2(f2 e)
-{
-    const f2 series = mul2(e, fma2(e, fma2(e, fma2(e, F2(-0.25f), F2(1.0f / 3.0f)), F2(-0.5f)), F2(1.0f)));
-    const bool sx = e.x < 0.015625f, sy = e.y < 0.015625f;
-    if (__all_sync(FULL, sx && sy)) return series;
-    const f2 direct = mul2(lg2(add2(F2(1.0f), e)), F2(LN2));
-    return make_float2(sx ? series.x : direct.x, sy ? series.y : direct.y);
-}
-
 // Per-vehicle constants of one call, for a pair of vehicles.
 struct VehConst2 {
     f2 inv_v0;          // 1 / v0
@@ -159,13 +143,8 @@ __device__ __forceinline__ f2 accel_star2(f2 v, f2 gap_raw, f2 vh, const VehCons
     const f2 a = mul2(k.am, sub2(sub2(F2(1.0f), rd), mul2(z, z)));  // Eq. 2
     bool bx, by;
     const f2 a_lb = lower_bound(mul2(v, F2(-inv_dt)), a_min, bx, by);  // Sec. III-C
-    // a_lb + sp(a - a_lb) = max(a, a_lb) + ln(1 + exp(-|a - a_lb|)): the
-    // large a_lb (a_min in ordinary driving) cancels exactly in the max
-    // instead of through the rounded difference, so a* keeps the precision
-    // of a rather than that of |a_lb|
-    const f2 x = sub2(a, a_lb);
-    const f2 e = make_float2(ex2_approx(fabsf(x.x) * -LOG2E), ex2_approx(fabsf(x.y) * -LOG2E));
-    return add2(vmax(a, a_lb), log1p_exp2(e));
+    const Soft2 s2 = softplus2(sub2(a, a_lb));
+    return add2(a_lb, s2.sp);
 }
 
 // Vehicle-pair state: absolute position as an unevaluated float pair
