@@ -267,7 +267,9 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 obs_k += sc.obs_stride;
                 ++obs_row;
             }
-            step_pairs<NP, D4>(g, st, kc, sc, xp);
+            // the state after the segment's last step is needed only at the
+            // end of the horizon (the seed of step K)
+            if (s + 1 < n || cs == n_ck - 1) step_pairs<NP, D4>(g, st, kc, sc, xp);
         }
         if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
             if (DENSE) {
@@ -569,7 +571,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 obs_k += sc.obs_stride;
                 ++obs_row;
             }
-            step_pairs<NP, D4>(g, st, kc, sc, xp);
+            if (s + 1 < n || c0 + n == sc.K) step_pairs<NP, D4>(g, st, kc, sc, xp);
         }
         if (c0 + n == sc.K) {  // state is now at step K: seed of the final step
             if (DENSE) {
