@@ -163,24 +163,40 @@ cudaError_t launch_gather(int N, const int32_t *perm, int count, const float *co
 // resident at any time (dispatched in index order) work on one or two rows.
 // The random reads of a row then hit its copy in L2 (each 32-byte sector is
 // fetched from DRAM once and serves all eight of its elements) instead of
-// fetching a sector per element, and perm stays in L2 across rows.
-constexpr int ROWS_CHUNK = 2048;
+// fetching a sector per element, and perm stays in L2 across rows.  Each
+// thread takes GR_PER elements and issues all their loads before its stores,
+// so the random reads overlap instead of waiting one by one.
+constexpr int GR_PER = 8;
+constexpr int ROWS_CHUNK = 256 * GR_PER;
 
-__global__ void __launch_bounds__(256) gather_rows_kernel(int N, long long total, const int32_t *perm,
-                                                          const float *src, float *dst)
+__global__ void __launch_bounds__(256) gather_rows_kernel(int N, long long total, const int32_t *__restrict__ perm,
+                                                          const float *__restrict__ src, float *__restrict__ dst)
 {
     const long long base = (long long)blockIdx.x * ROWS_CHUNK;
     long long r = base / N;
     int j = (int)(base - r * N) + (int)threadIdx.x;
-    for (int e = threadIdx.x; e < ROWS_CHUNK; e += 256, j += 256) {
+    size_t at[GR_PER];
+    int col[GR_PER];
+    bool ok[GR_PER];
+#pragma unroll
+    for (int e = 0; e < GR_PER; ++e, j += 256) {
         while (j >= N) {
             j -= N;
             ++r;
         }
-        if (base + e >= total) return;
-        const size_t row = (size_t)r * (size_t)N;
-        dst[row + j] = __ldg(src + row + __ldg(perm + j));
+        ok[e] = base + (long long)(e * 256 + (int)threadIdx.x) < total;
+        at[e] = (size_t)r * (size_t)N;
+        col[e] = j;
     }
+    int sj[GR_PER];
+#pragma unroll
+    for (int e = 0; e < GR_PER; ++e) sj[e] = ok[e] ? __ldg(perm + col[e]) : 0;
+    float v[GR_PER];
+#pragma unroll
+    for (int e = 0; e < GR_PER; ++e) v[e] = ok[e] ? __ldg(src + at[e] + sj[e]) : 0.0f;
+#pragma unroll
+    for (int e = 0; e < GR_PER; ++e)
+        if (ok[e]) dst[at[e] + col[e]] = v[e];
 }
 
 cudaError_t launch_gather_rows(int N, int n_rows, const int32_t *perm, const float *src, float *dst, cudaStream_t st)

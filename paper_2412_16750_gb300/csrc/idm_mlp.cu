@@ -126,6 +126,48 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
+// 16 accumulator columns [n, n + 16) of row r after the tensor-memory load.
+template <int MODE>
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, int split, const float *bias,
+                                               float (&v)[16])
+{
+    const bool row_ok = r < g.M_rows;
+    if (MODE == F32_PART) {
+        if (row_ok) store16_f32(g.Cf + ((size_t)split * g.M_rows + r) * g.N + n, v);
+        return;
+    }
+    float h[16];
+    if (MODE == GELU_FWD) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += bias[n + i];
+        if (g.Z && row_ok) store16_f32(g.Z + (size_t)r * g.N + n, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = gelu(v[i]);
+    } else {  // DGELU
+        float z[16];
+        if (row_ok) {
+            const float4 *zp = reinterpret_cast<const float4 *>(g.Z + (size_t)r * g.N + n);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 q = zp[i];
+                z[4 * i] = q.x; z[4 * i + 1] = q.y; z[4 * i + 2] = q.z; z[4 * i + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = v[i] * gelu_grad(z[i]);
+    }
+    if (row_ok) {
+        if (g.H) store16_bf16(g.H + (size_t)r * g.N + n, h);
+        if (g.HT) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) g.HT[(size_t)(n + i) * g.ldt + r] = __float2bfloat16_rn(h[i]);
+        }
+    }
+}
+
 // Epilogue of one accumulator row: row r of the output, tw = the tensor-
 // memory address of this row's column 0 of the tile, columns [c0, c1) of the
 // tile (global column n0 + c), split = K-split index (F32_PART), loss_slot =
@@ -178,7 +220,26 @@ __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t 
         l = warp_sum(l);
         if ((threadIdx.x & 31) == 0) g.loss_part[loss_slot] = l * (double)g.scale;
     } else {
-        for (int c = c0; c < c1; c += 16) {
+        // 64 columns per tensor-memory load where the range allows, else 16
+        for (int c = c0; c < c1;) {
+            if (c + 64 <= c1) {
+                float w[64];
+                if (empty) {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) w[i] = 0.0f;
+                } else {
+                    tc::tmem_ld64(tw + (uint32_t)c, w);
+                }
+#pragma unroll
+                for (int part = 0; part < 4; ++part) {
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = w[16 * part + i];
+                    epilogue_chunk<MODE>(g, r, n0 + c + 16 * part, split, bias, v);
+                }
+                c += 64;
+                continue;
+            }
             float v[16];
             if (empty) {
 #pragma unroll
@@ -186,41 +247,8 @@ __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t 
             } else {
                 tc::tmem_ld16(tw + (uint32_t)c, v);
             }
-            const int n = n0 + c;
-            if (MODE == F32_PART) {
-                if (row_ok) store16_f32(g.Cf + ((size_t)split * g.M_rows + r) * g.N + n, v);
-                continue;
-            }
-            float h[16];
-            if (MODE == GELU_FWD) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += bias[n + i];
-                if (g.Z && row_ok) store16_f32(g.Z + (size_t)r * g.N + n, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) h[i] = gelu(v[i]);
-            } else {  // DGELU
-                float z[16];
-                if (row_ok) {
-                    const float4 *zp = reinterpret_cast<const float4 *>(g.Z + (size_t)r * g.N + n);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 q = zp[i];
-                        z[4 * i] = q.x; z[4 * i + 1] = q.y; z[4 * i + 2] = q.z; z[4 * i + 3] = q.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) z[i] = 0.0f;
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) h[i] = v[i] * gelu_grad(z[i]);
-            }
-            if (row_ok) {
-                if (g.H) store16_bf16(g.H + (size_t)r * g.N + n, h);
-                if (g.HT) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) g.HT[(size_t)(n + i) * g.ldt + r] = __float2bfloat16_rn(h[i]);
-                }
-            }
+            epilogue_chunk<MODE>(g, r, n0 + c, split, bias, v);
+            c += 16;
         }
     }
 }
