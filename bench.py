@@ -455,6 +455,17 @@ def time_to_fit(a, dev):
         th_buf.copy_(plain)
         _, init_ms = timed(lambda: net.predict_params(
             api.mlp_features(scene, p0, v0, K, DT, Y, 1), th_buf))
+    # label MSE of the learned guess on this (held-out) scene, in the
+    # network's normalized units, beside that of the training-label mean
+    lo_t = torch.tensor(synth.BOX_LO, device=dev, dtype=torch.float64)[:, None]
+    hi_t = torch.tensor(synth.BOX_HI, device=dev, dtype=torch.float64)[:, None]
+    _, lab_fit = api.mlp_features(scene, p0, v0, K, DT, Y, 1, theta=th_true)
+    lab_fit = lab_fit.double().t()
+    pred_norm = (th_buf[:5].double() - lo_t) / (hi_t - lo_t)
+    label_mse = {"network": float(((pred_norm - lab_fit) ** 2).mean().item()),
+                 "training_mean": float(((torch.as_tensor(label_mean, device=dev)[:, None] - lab_fit) ** 2)
+                                        .mean().item())}
+    del lab_fit, pred_norm
     _, ev_learned = api.fit(th_buf, p0, v0, scene, K, DT, Y, 1, a.fit_iters, ctx=ctx, eval_targets=clean)
     it_learned, rmse_learned = first_below(ev_learned)
     ctx.set_event_counting(True)
@@ -480,7 +491,7 @@ def time_to_fit(a, dev):
                             "rmse_m_at": {str(i): float(rmse_plain[i]) for i in (0, 10, 50, 100, a.fit_iters - 1)
                                           if i < a.fit_iters}},
                   "learned": {"iterations": it_learned, "seconds": wall(it_learned, init_ms),
-                              "init_ms": init_ms,
+                              "init_ms": init_ms, "label_mse_held_out": label_mse,
                               "rmse_m_at": {str(i): float(rmse_learned[i])
                                             for i in (0, 10, 50, 100, a.fit_iters - 1) if i < a.fit_iters}},
                   "events_learned_fit": events_learned,

@@ -193,48 +193,18 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
 }
 
 // Per-scenario losses: one thread per scenario sums its segments' per-warp
-// partials in a fixed order; thread 0 then sums the scenarios.
+// partials in a fixed order.  The batch total is the sum of every segment's
+// partials (each segment belongs to one scenario), reduced in parallel by
+// launch_loss_finalize as for a single scene.
 __global__ void scen_loss_kernel(const double *part, int per_seg, const int *seg_off, const int *seg_idx, int S,
-                                 double *scen_loss, double *total)
+                                 double *scen_loss)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int i = seg_off[s]; i < seg_off[s + 1]; ++i)
             for (int w = 0; w < per_seg; ++w) acc += part[(size_t)seg_idx[i] * per_seg + w];
-        if (scen_loss) scen_loss[s] = acc;
+        scen_loss[s] = acc;
     }
-}
-
-__global__ void scen_total_kernel(const double *part, int per_seg, const int *seg_off, const int *seg_idx, int S,
-                                  double *total)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double t = 0.0;
-    for (int s = 0; s < S; ++s) {
-        double acc = 0.0;
-        for (int i = seg_off[s]; i < seg_off[s + 1]; ++i)
-            for (int w = 0; w < per_seg; ++w) acc += part[(size_t)seg_idx[i] * per_seg + w];
-        t += acc;
-    }
-    *total = t;
-}
-
-// Summed loss of every iteration of a single-launch batch fit: thread it
-// sums iteration it's partials in the order of scen_total_kernel.
-__global__ void scen_total_iters_kernel(const double *part, long long stride, int per_seg, const int *seg_off,
-                                        const int *seg_idx, int S, int n_iter, double *hist)
-{
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= n_iter) return;
-    const double *pi = part + (size_t)it * (size_t)stride;
-    double t = 0.0;
-    for (int s = 0; s < S; ++s) {
-        double acc = 0.0;
-        for (int i = seg_off[s]; i < seg_off[s + 1]; ++i)
-            for (int w = 0; w < per_seg; ++w) acc += pi[(size_t)seg_idx[i] * per_seg + w];
-        t += acc;
-    }
-    hist[it] = t;
 }
 
 struct BatchFinalize {
@@ -248,10 +218,8 @@ cudaError_t batch_finalize(idm_ctx *c, const Prep &P, int it, double *hist, cuda
     const int S = g_bfin.S;
     if (g_bfin.scen_loss)
         scen_loss_kernel<<<(S + 255) / 256, 256, 0, st>>>(P.a.loss_part, P.loss_per_seg, (const int *)c->scen_seg_off.p,
-                                                          (const int *)c->scen_seg_idx.p, S, g_bfin.scen_loss, nullptr);
-    if (hist)
-        scen_total_kernel<<<1, 32, 0, st>>>(P.a.loss_part, P.loss_per_seg, (const int *)c->scen_seg_off.p,
-                                            (const int *)c->scen_seg_idx.p, S, hist + it);
+                                                          (const int *)c->scen_seg_idx.p, S, g_bfin.scen_loss);
+    if (hist) return idm::launch_loss_finalize(P.a.loss_part, P.a.n_seg, P.loss_per_seg, hist + it, st);
     return cudaGetLastError();
 }
 
@@ -363,12 +331,10 @@ int idm_batch_fit(idm_ctx_t *c, const idm_batch_t *b, idm_params_t *params, cons
             return rc;
         const SimArgs &a = P.a;
         const int *seg_off = (const int *)c->scen_seg_off.p, *seg_idx = (const int *)c->scen_seg_idx.p;
-        if (loss_hist)
-            scen_total_iters_kernel<<<(n_iter + 127) / 128, 128, 0, st>>>(a.loss_part, stride, P.loss_per_seg,
-                                                                          seg_off, seg_idx, S, n_iter, loss_hist);
+        if (loss_hist) CK(idm::launch_loss_finalize_iters(a.loss_part, stride, a.n_seg, P.loss_per_seg, n_iter, loss_hist, st));
         if (scen_loss)
             scen_loss_kernel<<<(S + 255) / 256, 256, 0, st>>>(a.loss_part + (size_t)(n_iter - 1) * (size_t)stride,
-                                                              P.loss_per_seg, seg_off, seg_idx, S, scen_loss, nullptr);
+                                                              P.loss_per_seg, seg_off, seg_idx, S, scen_loss);
         CK(cudaGetLastError());
         return IDM_OK;
     }
