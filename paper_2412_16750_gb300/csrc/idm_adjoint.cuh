@@ -693,21 +693,26 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
 
 // Register budgets: 2 vehicles per thread fit 128 registers (2 blocks of 8
 // warps per SM); 4 per thread need ~168 without spilling, so their blocks
-// are 4 warps (3 blocks per SM) unless the segment has 8 warps (BIG, 256
-// threads, one block per SM); 8 per thread use up to 255.
-template <int VPT, bool BIG>
+// are 4 warps (3 blocks per SM) unless the segment has 8 warps (256 threads,
+// one block per SM); 8 per thread use up to 255.
+template <int VPT, int GW>
 struct BwdBounds {
-    static constexpr int threads = (VPT == 4 && !BIG) ? 128 : 256;
-    static constexpr int blocks = VPT == 2 ? 2 : ((VPT == 4 && !BIG) ? 3 : 1);
+    static constexpr bool narrow = VPT == 4 && GW < 8;
+    static constexpr int threads = narrow ? 128 : 256;
+    static constexpr int blocks = VPT == 2 ? 2 : (narrow ? 3 : 1);
 };
 
-template <int VPT, bool DENSE, bool ADAM, bool WD, bool BIG, bool SUB>
-__global__ void __launch_bounds__(BwdBounds<VPT, BIG>::threads, BwdBounds<VPT, BIG>::blocks)
+// The warps per segment GW are a compile-time constant of each kernel: the
+// group exchange, its barriers and every slot offset of the shared tape then
+// fold into immediates (measured on GB300 at 4 vehicles x 4 warps: 7 % fewer
+// instructions and an 11 % shorter adjoint than with GW read from SimArgs).
+template <int VPT, int GW, bool DENSE, bool ADAM, bool WD, bool SUB>
+__global__ void __launch_bounds__(BwdBounds<VPT, GW>::threads, BwdBounds<VPT, GW>::blocks)
 backward_kernel(SimArgs a)
 {
     constexpr int NP = VPT / 2;
+    constexpr int G = GW;
     extern __shared__ float smem[];
-    const int G = a.G;
     const int warp = threadIdx.x >> 5;
     float *gbase = smem + (warp / G) * bwd_group_floats(VPT, DENSE, a.tape_T, G, a.bwd_pf != 0);
     float *ctrl = gbase + bwd_group_floats(VPT, DENSE, a.tape_T, G, a.bwd_pf != 0) - grp_ctrl_floats(G);
@@ -737,18 +742,18 @@ backward_kernel(SimArgs a)
     }
 }
 
-// Kernel variants of one vehicles-per-thread value: seeds from dense
-// gradients or from targets, fused Adam or gradient output, with or without
-// the delta gradient, block form (BIG) and tape blocks (SUB).
-template <int VPT, bool BIG, bool SUB>
+// Kernel variants of one (vehicles per thread, warps per segment) shape:
+// seeds from dense gradients or from targets, fused Adam or gradient output,
+// with or without the delta gradient, and tape blocks (SUB).
+template <int VPT, int GW, bool SUB>
 inline void *backward_fn_t(bool dense, bool adam, bool wd)
 {
     if (dense)
-        return wd ? (void *)backward_kernel<VPT, true, false, true, BIG, SUB>
-                  : (void *)backward_kernel<VPT, true, false, false, BIG, SUB>;
-    if (adam) return (void *)backward_kernel<VPT, false, true, false, BIG, SUB>;
-    return wd ? (void *)backward_kernel<VPT, false, false, true, BIG, SUB>
-              : (void *)backward_kernel<VPT, false, false, false, BIG, SUB>;
+        return wd ? (void *)backward_kernel<VPT, GW, true, false, true, SUB>
+                  : (void *)backward_kernel<VPT, GW, true, false, false, SUB>;
+    if (adam) return (void *)backward_kernel<VPT, GW, false, true, false, SUB>;
+    return wd ? (void *)backward_kernel<VPT, GW, false, false, true, SUB>
+              : (void *)backward_kernel<VPT, GW, false, false, false, SUB>;
 }
 
 }  // namespace idm

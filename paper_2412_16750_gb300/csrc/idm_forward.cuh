@@ -106,4 +106,46 @@ __device__ __forceinline__ void forward_segment(const SimArgs &a, const ScenDesc
     }
 }
 
+// Register budgets: 8 vehicles per thread (four pairs of state and constants)
+// need more than the 128 registers of 16 warps per SM: their blocks are
+// capped at 12 warps (one block per SM, up to 168 registers).
+template <int VPT>
+struct FwdBounds {
+    static constexpr int threads = VPT == 8 ? 384 : 512;
+};
+
+template <int VPT, int GW, bool COUNT>
+__global__ void __launch_bounds__(FwdBounds<VPT>::threads)
+forward_kernel(SimArgs a, FwdFlags f)
+{
+    constexpr int NP = VPT / 2;
+    constexpr int G = GW;  // a compile-time constant, as in the adjoint
+    extern __shared__ float fsmem[];
+    const int warp = threadIdx.x >> 5;
+    float *ctrl = fsmem + (warp / G) * grp_ctrl_floats(G);
+    Grp g = make_grp(G, ctrl);
+    int par = 0;
+    for (;;) {
+        const int s_idx = grp_next(g, a.work, par);
+        if (s_idx >= *a.n_seg) break;
+        const Seg sg = a.seg[s_idx];
+        const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
+        const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
+        VehConst2 kc[NP];
+        State2 st[NP];
+        bool vx[NP], vy[NP];
+        load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
+        if (segment_is_d4<NP>(kc, vx, vy))
+            forward_segment<NP, true, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
+        else
+            forward_segment<NP, false, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
+    }
+}
+
+template <int VPT, int GW>
+inline void *forward_fn_t(bool count)
+{
+    return count ? (void *)forward_kernel<VPT, GW, true> : (void *)forward_kernel<VPT, GW, false>;
+}
+
 }  // namespace idm

@@ -24,13 +24,13 @@
 
 namespace idm {
 
-template <int VPT, bool BIG, bool SUB>
-__global__ void __launch_bounds__(BwdBounds<VPT, BIG>::threads, BwdBounds<VPT, BIG>::blocks)
+template <int VPT, int GW, bool SUB>
+__global__ void __launch_bounds__(BwdBounds<VPT, GW>::threads, BwdBounds<VPT, GW>::blocks)
 fit_fused_kernel(SimArgs a, long long part_stride)
 {
     constexpr int NP = VPT / 2;
+    constexpr int G = GW;
     extern __shared__ float smem[];
-    const int G = a.G;
     const int warp = threadIdx.x >> 5;
     const int gf = bwd_group_floats(VPT, false, a.tape_T, G, a.bwd_pf != 0);
     float *gbase = smem + (warp / G) * gf;
@@ -90,10 +90,21 @@ fit_fused_kernel(SimArgs a, long long part_stride)
     }
 }
 
-template <int VPT, bool BIG>
+template <int VPT, int GW>
 inline void *fused_fn_t(bool sub)
 {
-    return sub ? (void *)fit_fused_kernel<VPT, BIG, true> : (void *)fit_fused_kernel<VPT, BIG, false>;
+    return sub ? (void *)fit_fused_kernel<VPT, GW, true> : (void *)fit_fused_kernel<VPT, GW, false>;
 }
+
+// The forward, adjoint and single-launch fit kernels of one shape, as the
+// entry points declared in idm_internal.h (one translation unit per shape, so
+// the shapes compile in parallel).
+#define IDM_DEFINE_SHAPE_KERNELS(V, GW)                                                  \
+    void *forward_fn_v##V##_g##GW(bool count) { return forward_fn_t<V, GW>(count); }     \
+    void *backward_fn_v##V##_g##GW(bool dense, bool adam, bool wd, bool sub)              \
+    {                                                                                    \
+        return sub ? backward_fn_t<V, GW, true>(dense, adam, wd) : backward_fn_t<V, GW, false>(dense, adam, wd); \
+    }                                                                                    \
+    void *fused_fn_v##V##_g##GW(bool sub) { return fused_fn_t<V, GW>(sub); }
 
 }  // namespace idm

@@ -127,17 +127,20 @@ cudaError_t launch_loss_finalize_iters(const double *loss_part, long long stride
                                        int n_iter, double *out, cudaStream_t st);
 int occupancy_blocks(int vpt, int G, bool backward, bool dense_seed, bool adam, bool want_delta, int wpb, size_t smem,
                      bool sub = false);
-// Adjoint kernel variants (idm_adjoint{2,4,8}.cu): dense or target seeds,
-// fused Adam, delta gradient, 8-warp block form (4 vehicles/thread only),
-// tape blocks with sub-checkpoints.
-void *backward_fn_vpt2(bool dense, bool adam, bool wd, bool big, bool sub);
-void *backward_fn_vpt4(bool dense, bool adam, bool wd, bool big, bool sub);
-void *backward_fn_vpt8(bool dense, bool adam, bool wd, bool big, bool sub);
-// Single-launch fit variants (idm_fused{2,4,8}.cu): 8-warp block form (4
-// vehicles/thread only), tape blocks with sub-checkpoints.
-void *fused_fn_vpt2(bool big, bool sub);
-void *fused_fn_vpt4(bool big, bool sub);
-void *fused_fn_vpt8(bool big, bool sub);
+// Kernel shapes (vehicles per thread, warps per segment) with compiled
+// adjoint and single-launch fit kernels; X(V, G) per shape.
+#define IDM_SHAPES(X) \
+    X(2, 1) X(2, 2) X(2, 4) X(2, 8) X(4, 1) X(4, 2) X(4, 4) X(4, 8) X(8, 1) X(8, 2) X(8, 4) X(8, 8)
+// Per shape (idm_shape_v<V>_g<G>.cu): the forward kernel (with or without
+// event counting), the adjoint kernel for dense or target seeds, fused Adam,
+// the delta gradient and tape blocks with sub-checkpoints, and the
+// single-launch fit kernel (tape blocks or not).
+#define IDM_DECLARE_SHAPE(V, GW)                                             \
+    void *forward_fn_v##V##_g##GW(bool count);                                \
+    void *backward_fn_v##V##_g##GW(bool dense, bool adam, bool wd, bool sub); \
+    void *fused_fn_v##V##_g##GW(bool sub);
+IDM_SHAPES(IDM_DECLARE_SHAPE)
+#undef IDM_DECLARE_SHAPE
 
 // Layout (idm_layout.cu).
 cudaError_t launch_layout(int N, int n_lanes, const int32_t *lane_id, const float *pos, int32_t *perm,

@@ -138,43 +138,6 @@ cudaError_t launch_build_segments(const int *lane_off, int n_lanes, const int *s
     return cudaGetLastError();
 }
 
-// Register budgets: 8 vehicles per thread (four pairs of state and constants)
-// need more than the 128 registers of 16 warps per SM: their blocks are
-// capped at 12 warps (one block per SM, up to 168 registers).
-template <int VPT>
-struct FwdBounds {
-    static constexpr int threads = VPT == 8 ? 384 : 512;
-};
-
-template <int VPT, bool COUNT>
-__global__ void __launch_bounds__(FwdBounds<VPT>::threads)
-forward_kernel(SimArgs a, FwdFlags f)
-{
-    constexpr int NP = VPT / 2;
-    extern __shared__ float fsmem[];
-    const int G = a.G;
-    const int warp = threadIdx.x >> 5;
-    float *ctrl = fsmem + (warp / G) * grp_ctrl_floats(G);
-    Grp g = make_grp(G, ctrl);
-    int par = 0;
-    for (;;) {
-        const int s_idx = grp_next(g, a.work, par);
-        if (s_idx >= *a.n_seg) break;
-        const Seg sg = a.seg[s_idx];
-        const ScenDesc sc = a.scen_tab ? a.scen_tab[sg.scen] : a.scen0;
-        const int lb = sg.veh_begin - sc.veh_begin;  // scenario-local index of slot 0
-        VehConst2 kc[NP];
-        State2 st[NP];
-        bool vx[NP], vy[NP];
-        load_vehicles<NP>(a, sg, g.lane, g.w * 64 * NP, kc, st, vx, vy);
-        if (segment_is_d4<NP>(kc, vx, vy))
-            forward_segment<NP, true, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
-        else
-            forward_segment<NP, false, COUNT>(a, sc, s_idx, lb, g, kc, st, vx, vy, f);
-    }
-}
-
-
 // ---------------------------------------------------------------------------
 // Deterministic loss reduction over segments (fixed order).
 // ---------------------------------------------------------------------------
@@ -235,18 +198,23 @@ cudaError_t launch_loss_finalize_iters(const double *loss_part, long long stride
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
+// Forward kernels of every shape live in idm_shape_v<V>_g<G>.cu (COUNT: the
+// variant that also counts gap-floor and kink-band events).
+static void *forward_fn_v(int vpt, int G, bool count)
+{
+#define IDM_PICK(V, GW) \
+    if (vpt == V && G == GW) return forward_fn_v##V##_g##GW(count);
+    IDM_SHAPES(IDM_PICK)
+#undef IDM_PICK
+    return nullptr;
+}
+
 cudaError_t launch_forward(int vpt, int G, bool traj, bool vtraj, bool ckpt, const SimArgs &a, int grid, int wpb,
                            cudaStream_t st)
 {
     FwdFlags f{traj, vtraj, ckpt, a.eval_targets != nullptr && a.eval_part != nullptr};
-    const bool count = a.events != nullptr;
-    void *fn = nullptr;
-    switch (vpt) {
-    case 2: fn = count ? (void *)forward_kernel<2, true> : (void *)forward_kernel<2, false>; break;
-    case 4: fn = count ? (void *)forward_kernel<4, true> : (void *)forward_kernel<4, false>; break;
-    case 8: fn = count ? (void *)forward_kernel<8, true> : (void *)forward_kernel<8, false>; break;
-    default: return cudaErrorInvalidValue;
-    }
+    void *fn = forward_fn_v(vpt, G, a.events != nullptr);
+    if (!fn) return cudaErrorInvalidValue;
     const size_t smem = forward_smem_bytes(vpt, G, wpb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -267,16 +235,16 @@ size_t forward_smem_bytes(int vpt, int G, int wpb)
     return (size_t)grp_ctrl_floats(G) * (wpb / G) * sizeof(float);
 }
 
-// Adjoint variants live in idm_adjoint{2,4,8}.cu.  For 4 vehicles per
-// thread a 4-warp and an 8-warp block form; SUB: tape shallower than the
-// checkpoint interval.
-static void *backward_fn_v(int vpt, bool dense, bool adam, bool wd, int wpb, bool sub)
+// Adjoint variants of every shape live in idm_shape_v<V>_g<G>.cu (with
+// 4 vehicles per thread, segments of up to 4 warps run in 4-warp blocks and
+// 8-warp segments in 8-warp blocks); SUB: tape shallower than the checkpoint
+// interval.
+static void *backward_fn_v(int vpt, int G, bool dense, bool adam, bool wd, bool sub)
 {
-    switch (vpt) {
-    case 2: return backward_fn_vpt2(dense, adam, wd, false, sub);
-    case 4: return backward_fn_vpt4(dense, adam, wd, wpb > 4, sub);
-    case 8: return backward_fn_vpt8(dense, adam, wd, false, sub);
-    }
+#define IDM_PICK(V, GW) \
+    if (vpt == V && G == GW) return backward_fn_v##V##_g##GW(dense, adam, wd, sub);
+    IDM_SHAPES(IDM_PICK)
+#undef IDM_PICK
     return nullptr;
 }
 
@@ -294,7 +262,7 @@ cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool wan
 {
     if (dense_seed && adam) return cudaErrorInvalidValue;
     if (wpb > backward_max_warps(vpt, G) || wpb % G) return cudaErrorInvalidValue;
-    void *fn = backward_fn_v(vpt, dense_seed, adam, want_delta && !adam, wpb, a.tape_T < a.C);
+    void *fn = backward_fn_v(vpt, G, dense_seed, adam, want_delta && !adam, a.tape_T < a.C);
     if (!fn) return cudaErrorInvalidValue;
     size_t smem = backward_smem_bytes(vpt, dense_seed, a.tape_T, G, wpb, a.bwd_pf != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -305,14 +273,13 @@ cudaError_t launch_backward(int vpt, int G, bool dense_seed, bool adam, bool wan
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * wpb), params, smem, st);
 }
 
-// Single-launch fit kernels live in idm_fused{2,4,8}.cu.
-static void *fused_fn_v(int vpt, int wpb, bool sub)
+// Single-launch fit kernels of every shape live in idm_shape_v<V>_g<G>.cu.
+static void *fused_fn_v(int vpt, int G, bool sub)
 {
-    switch (vpt) {
-    case 2: return fused_fn_vpt2(false, sub);
-    case 4: return fused_fn_vpt4(wpb > 4, sub);
-    case 8: return fused_fn_vpt8(false, sub);
-    }
+#define IDM_PICK(V, GW) \
+    if (vpt == V && G == GW) return fused_fn_v##V##_g##GW(sub);
+    IDM_SHAPES(IDM_PICK)
+#undef IDM_PICK
     return nullptr;
 }
 
@@ -320,7 +287,7 @@ cudaError_t launch_fit_fused(int vpt, int G, const SimArgs &a, long long part_st
                              cudaStream_t st)
 {
     if (wpb > backward_max_warps(vpt, G) || wpb % G) return cudaErrorInvalidValue;
-    void *fn = fused_fn_v(vpt, wpb, a.tape_T < a.C);
+    void *fn = fused_fn_v(vpt, G, a.tape_T < a.C);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = backward_smem_bytes(vpt, false, a.tape_T, G, wpb, a.bwd_pf != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -344,15 +311,11 @@ int occupancy_blocks(int vpt, int G, bool backward, bool dense, bool adam, bool 
 {
     void *fn = nullptr;
     if (!backward) {
-        switch (vpt) {
-        case 2: fn = (void *)forward_kernel<2, false>; break;
-        case 4: fn = (void *)forward_kernel<4, false>; break;
-        case 8: fn = (void *)forward_kernel<8, false>; break;
-        }
+        fn = forward_fn_v(vpt, G, false);
         smem = forward_smem_bytes(vpt, G, wpb);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
-        fn = backward_fn_v(vpt, dense, adam, want_delta && !adam, wpb, sub);
+        fn = backward_fn_v(vpt, G, dense, adam, want_delta && !adam, sub);
         if (fn) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     if (!fn) return 1;
