@@ -161,6 +161,25 @@ __device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, v
     return false;
 }
 
+// mbarrier arrival that also announces `bytes` of asynchronous (TMA)
+// transactions the current phase must receive before it completes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// TMA copy of the 2D box at element coordinates (x, y) of the tensor map
+// into shared memory at dst; its bytes complete a transaction on `bar`.
+// The map (a __grid_constant__ kernel parameter) fixes the box and the
+// zero fill of rows or columns outside the tensor.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 // Whole-warp tensor-memory allocation; the address is written to shared memory.
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
 {

@@ -16,6 +16,7 @@
 //             db_l = column sums of dZ_l;
 //   update    one kernel sums the partials and applies Adam to the FP32
 //             master weights, then refreshes the bf16 copies W and W^T.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
@@ -87,6 +88,34 @@ __device__ __forceinline__ NormalCdf normal_cdf(float z)
     return r;
 }
 
+// The same arithmetic for two values at once with the packed FP32
+// instructions (every product and fused multiply-add rounds as its scalar
+// counterpart, so the results equal normal_cdf's bit for bit).
+struct NormalCdf2 {
+    float2 cdf, pdf;
+};
+__device__ __forceinline__ NormalCdf2 normal_cdf2(float2 z)
+{
+    using idm::F2;
+    using idm::fma2;
+    using idm::mul2;
+    const float2 x = make_float2(fabsf(z.x) * 0.70710678118654752f, fabsf(z.y) * 0.70710678118654752f);
+    const float2 den = fma2(F2(0.3275911f), x, F2(1.0f));
+    const float2 t = make_float2(idm::rcp_approx(den.x), idm::rcp_approx(den.y));
+    float2 poly = fma2(t, F2(1.061405429f), F2(-1.453152027f));
+    poly = fma2(t, poly, F2(1.421413741f));
+    poly = fma2(t, poly, F2(-0.284496736f));
+    poly = fma2(t, poly, F2(0.254829592f));
+    const float2 arg = mul2(mul2(make_float2(-x.x, -x.y), x), F2(1.44269504088896341f));
+    const float2 e = make_float2(idm::ex2_approx(arg.x), idm::ex2_approx(arg.y));  // exp(-x^2)
+    const float2 half_tail = mul2(mul2(mul2(F2(0.5f), t), poly), e);            // (1 - erf(x)) / 2
+    const float2 upper = idm::sub2(F2(1.0f), half_tail);
+    NormalCdf2 r;
+    r.cdf = make_float2(z.x >= 0.0f ? upper.x : half_tail.x, z.y >= 0.0f ? upper.y : half_tail.y);
+    r.pdf = mul2(F2(0.39894228040143268f), e);
+    return r;
+}
+
 __device__ __forceinline__ float gelu(float z) { return z * normal_cdf(z).cdf; }
 __device__ __forceinline__ float gelu_grad(float z)
 {
@@ -139,10 +168,19 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, 
     float h[16];
     if (MODE == GELU_FWD) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += bias[n + i];
+        for (int i = 0; i < 16; i += 2) {
+            const float2 zz = idm::add2(make_float2(v[i], v[i + 1]), make_float2(bias[n + i], bias[n + i + 1]));
+            v[i] = zz.x;
+            v[i + 1] = zz.y;
+        }
         if (g.Z && row_ok) store16_f32(g.Z + (size_t)r * g.N + n, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = gelu(v[i]);
+        for (int i = 0; i < 16; i += 2) {
+            const float2 zz = make_float2(v[i], v[i + 1]);
+            const float2 gg = idm::mul2(zz, normal_cdf2(zz).cdf);
+            h[i] = gg.x;
+            h[i + 1] = gg.y;
+        }
     } else {  // DGELU
         float z[16];
         if (row_ok) {
@@ -157,7 +195,13 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, 
             for (int i = 0; i < 16; ++i) z[i] = 0.0f;
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = v[i] * gelu_grad(z[i]);
+        for (int i = 0; i < 16; i += 2) {
+            const float2 zz = make_float2(z[i], z[i + 1]);
+            const NormalCdf2 nc = normal_cdf2(zz);
+            const float2 gg = idm::mul2(make_float2(v[i], v[i + 1]), idm::fma2(zz, nc.pdf, nc.cdf));
+            h[i] = gg.x;
+            h[i + 1] = gg.y;
+        }
     }
     if (row_ok) {
         if (g.H) store16_bf16(g.H + (size_t)r * g.N + n, h);
@@ -326,6 +370,10 @@ constexpr int EPI_WARPS = 8;    // two per tensor-memory lane quarter (column ha
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int CTL_BYTES = 8 * (2 * MAX_STAGES + 6) + 16;
 constexpr int SMEM_LIMIT = 227 * 1024;
+// A stage layout (TMA boxes of 8 K-columns): the 8 x 8 core matrices of
+// K-chunk kc and row group r8 at kc * A_LBO + r8 * 128 bytes, i.e. core
+// matrices adjacent in K are A_LBO bytes apart and 8-row groups 128 bytes.
+constexpr int A_LBO = tc::BM * 16;
 __host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
 // A stages that fit beside the resident weights (at least 2); nbias = the
 // staged bias floats
@@ -339,7 +387,7 @@ __host__ __device__ inline int smem_bytes(int N, int K, int S) { return ctl_off(
 }  // namespace ws
 
 template <int MODE>
-__global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const GemmArgs g)
+__global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const GemmArgs g, const __grid_constant__ CUtensorMap tmA)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     // this CTA's columns: [n0, n0 + N) of the product (N = g.BN, the width
@@ -364,7 +412,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), ncols);
     if (threadIdx.x == 32) {
         for (int s = 0; s < S; ++s) {
-            tc::mbar_init(full_bar(s), 32);  // one asynchronous arrival per producer lane
+            tc::mbar_init(full_bar(s), 1);  // the producer's arrival with the stage's TMA byte count
             tc::mbar_init(empty_bar(s), 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -409,20 +457,25 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
                 }
                 const int k0 = kt * tc::BK, nch = min(tc::BK, K - k0) >> 3;
                 const uint32_t dst = sA + (uint32_t)s * tc::A_STAGE_BYTES;
-                for (int c = lane; c < tc::BM * 8; c += 32) {
-                    const int row = c >> 3, kc = c & 7;
-                    if (kc >= nch) continue;
-                    const int m = m0 + row;
-                    const bool in = m < g.M_valid;
-                    tc::cp_async16(dst + tc::tile_off(row, kc), g.A + (size_t)(in ? m : 0) * K + k0 + kc * 8, in ? 16u : 0u);
+                // one TMA box per 8 K-columns: 128 rows x 16 bytes, rows of
+                // the box 16 bytes apart, boxes ws::A_LBO bytes apart (rows
+                // past M_valid arrive as zeros)
+                if (lane == 0) {
+                    tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(nch * ws::A_LBO));
+                    for (int kc = 0; kc < nch; ++kc)
+                        tc::tma_load_2d(dst + (uint32_t)(kc * ws::A_LBO), &tmA, k0 + 8 * kc, m0, full_bar(s));
                 }
-                // the stage's full barrier receives one arrival per lane once
-                // that lane's copies have landed
-                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full_bar(s)) : "memory");
+                __syncwarp();
             }
         }
-        // after a give-up some copies may still be in flight: they land
-        // before the CTA leaves (in normal operation they already have)
+        // every stage issued has landed before the CTA can leave (after a
+        // give-up the tensor core may not have consumed them)
+        if (lane == 0 && q > 0)
+            for (int s = 0; s < S && s < q; ++s) {
+                const int q_last = q - 1 - ((q - 1 - s) % S);  // last issue on stage s
+                tc::mbar_wait(full_bar(s), (uint32_t)((q_last / S) & 1));
+            }
+        __syncwarp();
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 1) {
         // ---- MMA issue (one thread) --------------------------------------------
@@ -444,7 +497,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
                     const int kw = min(tc::BK, K - kt * tc::BK);
                     const uint32_t a_buf = sA + (uint32_t)s * tc::A_STAGE_BYTES;
                     for (int ks = 0; ks < (kw >> 4); ++ks) {
-                        const uint64_t ad = tc::smem_desc(a_buf + ks * 256, 128, 1024);
+                        const uint64_t ad = tc::smem_desc(a_buf + (uint32_t)(ks * 2 * ws::A_LBO), ws::A_LBO, 128);
                         const uint64_t bd = tc::smem_desc(sW + (uint32_t)(kt * 8 + ks * 2) * 128, 128, (uint32_t)KC * 128);
                         tc::mma_bf16(tmem + (uint32_t)acc * acc_cols, ad, bd, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
                     }
@@ -494,6 +547,37 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1) mlp_gemm_ws_kernel(const Gemm
     }
 }
 
+// Tensor map of the A operand [M_valid x K] bf16 row-major for the TMA
+// boxes of the persistent GEMM: 8 columns (16 bytes) x 128 rows, no
+// swizzle, zero fill outside.  The encoder is the driver's
+// cuTensorMapEncodeTiled, looked up once.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+cudaError_t a_tensor_map(const GemmArgs &g, CUtensorMap *tm)
+{
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeTiled>(f);
+    }
+    // the row pitch and the 16-byte boxes need K % 8 == 0 and a 16-byte
+    // aligned base; an empty A has no rows to describe
+    if (g.K % 8 != 0 || g.M_valid < 1 || (reinterpret_cast<uintptr_t>(g.A) & 15u) != 0) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)g.K, (cuuint64_t)g.M_valid};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.K * sizeof(bf16)};
+    const cuuint32_t box[2] = {8, (cuuint32_t)tc::BM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(g.A), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Launch of the persistent GEMM: CTAs keep column slices of nsplit equal
 // parts of the weights; each walks row tiles (grid x) of its slice (grid y).
 template <int MODE>
@@ -517,7 +601,9 @@ cudaError_t gemm_ws(const GemmArgs &g0, int n_sm, int nsplit, cudaStream_t st)
     // (a CTA that cannot allocate would wait for another to finish)
     occ = std::max(1, std::min(occ, (int)(512 / (2 * tc::tmem_cols_for(g.BN)))));
     const int grid = std::max(1, std::min(ntiles, (n_sm * occ + nsplit - 1) / nsplit));
-    mlp_gemm_ws_kernel<MODE><<<dim3(grid, nsplit), ws::NTHREADS, smem, st>>>(g);
+    CUtensorMap tmA;
+    if ((e = a_tensor_map(g, &tmA)) != cudaSuccess) return e;
+    mlp_gemm_ws_kernel<MODE><<<dim3(grid, nsplit), ws::NTHREADS, smem, st>>>(g, tmA);
     return cudaGetLastError();
 }
 
