@@ -79,6 +79,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// Descriptor of a K-major operand tile with the 128-byte swizzle: rows of
+// 128 bytes (64 bf16 of K), 8-row groups SBO = 1024 bytes apart, the 16-byte
+// chunks of row r at chunk ^ (r & 7) (the layout a TMA box of 64 columns with
+// CU_TENSOR_MAP_SWIZZLE_128B writes); swizzling mode 2 in bits 61-63.  The
+// tile starts 1024-byte aligned; the K step of 16 columns advances the start
+// address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                  // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, bits 10-12 = 1), no negation, both operands K-major (bits
 // 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.

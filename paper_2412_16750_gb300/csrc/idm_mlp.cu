@@ -423,24 +423,20 @@ constexpr int EPI_WARPS = 8;    // two per tensor-memory lane quarter (column ha
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int CTL_BYTES = 8 * (2 * MAX_STAGES + 6) + 16;
 constexpr int SMEM_LIMIT = 227 * 1024;
-// A stage layout (TMA boxes of 8 K-columns): the 8 x 8 core matrices of
-// K-chunk kc and row group r8 at kc * A_LBO + r8 * 128 bytes, i.e. core
-// matrices adjacent in K are A_LBO bytes apart and 8-row groups 128 bytes.
-constexpr int A_LBO = tc::BM * 16;
 __host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
 // Output staging for TMA stores of the bf16 activations: per epilogue warp
-// one box of 32 rows x 64 columns (128 bytes, 128-byte swizzle), 1024-byte
-// aligned (the slack covers the rounding up of its start).
+// one box of 32 rows x 64 columns (128 bytes, 128-byte swizzle), right after
+// the A stages (1024-byte aligned like them).
 constexpr int STG_BOX_BYTES = 32 * 128;
-__host__ __device__ constexpr int stg_bytes(bool tma_out) { return tma_out ? 1024 + EPI_WARPS * STG_BOX_BYTES : 0; }
+__host__ __device__ constexpr int stg_bytes(bool tma_out) { return tma_out ? EPI_WARPS * STG_BOX_BYTES : 0; }
 // A stages that fit beside the resident weights (at least 2); nbias = the
 // staged bias floats
 __host__ __device__ inline int max_stages(int N, int K, int nbias, bool tma_out)
 {
-    const int s = (SMEM_LIMIT - w_bytes(N, K) - CTL_BYTES - 4 * nbias - stg_bytes(tma_out)) / tc::A_STAGE_BYTES;
+    const int s = (SMEM_LIMIT - w_bytes(N, K) - 1024 - CTL_BYTES - 4 * nbias - stg_bytes(tma_out)) / tc::A_STAGE_BYTES;
     return s < 2 ? 2 : (s > MAX_STAGES ? MAX_STAGES : s);
 }
-__host__ __device__ inline int stg_off(int N, int K, int S) { return w_bytes(N, K) + S * tc::A_STAGE_BYTES; }
+__host__ __device__ inline int stg_off(int N, int K, int S) { return w_bytes(N, K) + 1024 + S * tc::A_STAGE_BYTES; }
 __host__ __device__ inline int ctl_off(int N, int K, int S, bool tma_out)
 {
     return stg_off(N, K, S) + stg_bytes(tma_out);
@@ -459,7 +455,9 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
     const int nkt = (K + tc::BK - 1) / tc::BK;
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
     const uint32_t acc_cols = tc::tmem_cols_for(N), ncols = 2 * acc_cols;
-    const uint32_t sW = tc::smem_u32(smem), sA = sW + ws::w_bytes(N, K);
+    // A stages 1024-byte aligned (their 128-byte swizzle); the layout keeps
+    // 1 KB of slack for the rounding
+    const uint32_t sW = tc::smem_u32(smem), sA = (sW + (uint32_t)ws::w_bytes(N, K) + 1023u) & ~1023u;
     const int S = g.stages;
     uint8_t *ctl = smem + ws::ctl_off(N, K, S, g.tma_h != 0);
     const uint32_t bars = tc::smem_u32(ctl);
@@ -520,13 +518,12 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
                 }
                 const int k0 = kt * tc::BK, nch = min(tc::BK, K - k0) >> 3;
                 const uint32_t dst = sA + (uint32_t)s * tc::A_STAGE_BYTES;
-                // one TMA box per 8 K-columns: 128 rows x 16 bytes, rows of
-                // the box 16 bytes apart, boxes ws::A_LBO bytes apart (rows
-                // past M_valid arrive as zeros)
+                // one TMA box: 128 rows x 64 K-columns, 128-byte swizzle
+                // (rows past M_valid and columns past K arrive as zeros)
+                (void)nch;
                 if (lane == 0) {
-                    tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(nch * ws::A_LBO));
-                    for (int kc = 0; kc < nch; ++kc)
-                        tc::tma_load_2d(dst + (uint32_t)(kc * ws::A_LBO), &tmA, k0 + 8 * kc, m0, full_bar(s));
+                    tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)tc::A_STAGE_BYTES);
+                    tc::tma_load_2d(dst, &tmA, k0, m0, full_bar(s));
                 }
                 __syncwarp();
             }
@@ -560,7 +557,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
                     const int kw = min(tc::BK, K - kt * tc::BK);
                     const uint32_t a_buf = sA + (uint32_t)s * tc::A_STAGE_BYTES;
                     for (int ks = 0; ks < (kw >> 4); ++ks) {
-                        const uint64_t ad = tc::smem_desc(a_buf + (uint32_t)(ks * 2 * ws::A_LBO), ws::A_LBO, 128);
+                        const uint64_t ad = tc::smem_desc_sw128(a_buf + (uint32_t)(ks * 32));
                         const uint64_t bd = tc::smem_desc(sW + (uint32_t)(kt * 8 + ks * 2) * 128, 128, (uint32_t)KC * 128);
                         tc::mma_bf16(tmem + (uint32_t)acc * acc_cols, ad, bd, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
                     }
@@ -587,8 +584,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
         asm volatile("bar.sync 1, %0;" ::"n"(32 * ws::EPI_WARPS) : "memory");
         // this warp's staging box for the TMA stores of H (0: direct stores)
         const uint32_t stg =
-            g.tma_h ? ((sA + (uint32_t)(S * tc::A_STAGE_BYTES) + 1023u) & ~1023u) + (uint32_t)((warp - 2) * ws::STG_BOX_BYTES)
-                    : 0u;
+            g.tma_h ? sA + (uint32_t)(S * tc::A_STAGE_BYTES) + (uint32_t)((warp - 2) * ws::STG_BOX_BYTES) : 0u;
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i & 1, u = i >> 1;
@@ -617,7 +613,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
 }
 
 // Tensor map of the A operand [M_valid x K] bf16 row-major for the TMA
-// boxes of the persistent GEMM: 8 columns (16 bytes) x 128 rows, no
+// boxes of the persistent GEMM: 64 columns (128 bytes) x 128 rows, 128-byte
 // swizzle, zero fill outside.  The encoder is the driver's
 // cuTensorMapEncodeTiled, looked up once.
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -645,10 +641,10 @@ cudaError_t a_tensor_map(const GemmArgs &g, CUtensorMap *tm)
     if (g.K % 8 != 0 || g.M_valid < 1 || (reinterpret_cast<uintptr_t>(g.A) & 15u) != 0) return cudaErrorInvalidValue;
     const cuuint64_t dims[2] = {(cuuint64_t)g.K, (cuuint64_t)g.M_valid};
     const cuuint64_t strides[1] = {(cuuint64_t)g.K * sizeof(bf16)};
-    const cuuint32_t box[2] = {8, (cuuint32_t)tc::BM};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(g.A), dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
