@@ -140,7 +140,10 @@ int idm_event_counts(idm_ctx_t *ctx, void *stream, uint64_t *gap_floor_hits, uin
  * warps of one block.  vpt: vehicles per thread (2, 4 or 8; 0 = choose);
  * warps_per_segment: 1, 2, 4 or 8 (0 = choose; with both 0 the library
  * takes vpt 4 x 4 warps, 8 x 4 for lanes over 512 vehicles and 8 x 8 over
- * 1024); ckpt_interval: steps between stored checkpoints of the adjoint
+ * 1024, except for a scene small enough that its segments of 2 vehicles per
+ * thread fit 16 warps per SM, where it takes vpt 2 with the fewest warps
+ * that hold the longest lane: such a call is bound by the latency of each
+ * step, not by throughput); ckpt_interval: steps between stored checkpoints of the adjoint
  * (1..64, default 8); warps_per_block: 1..16 (default 8; rounded to a
  * multiple of warps_per_segment; the adjoint caps it by its shared-memory
  * tape and by its register budget: 4 warps for vpt 4 with segments of up to

@@ -93,7 +93,7 @@ unsigned long long *event_counters(idm_ctx *c)
     return reinterpret_cast<unsigned long long *>(static_cast<char *>(c->status.p) + STATUS_EVENTS_OFF);
 }
 
-int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
+int pick_shape(idm_ctx *c, int max_lane, long long n_vehicles, int n_lanes, int *vpt, int *G)
 {
     int v = c->vpt_req, g = c->G_req;
     if (v == 0 && g == 0) {
@@ -103,6 +103,22 @@ int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G)
         g = 4;
         if (max_lane > 512) v = 8;
         if (max_lane > 1024) g = 8;
+        // a scene whose segments fit one wave of 2-vehicle warps (16 per SM)
+        // is bound by the latency of each warp's step, not by throughput:
+        // 2 vehicles per thread (the fewest instructions per step) and the
+        // fewest warps per segment that hold the longest lane (measured on
+        // GB300, loss + gradient over 100 steps: 0.15 -> 0.11 ms at 100
+        // vehicles, 0.20 -> 0.12 ms at 16,000, 0.32 -> 0.17 ms at 64,000)
+        int g2 = 1;
+        while (64 * g2 < max_lane && g2 < 8) g2 <<= 1;
+        if (64 * g2 >= max_lane) {
+            const long long cap2 = 64LL * g2;
+            const long long segs = std::min<long long>(n_lanes, 2 * ((n_vehicles + cap2 - 1) / cap2) + 1);
+            if (segs * g2 <= 16LL * c->n_sm) {
+                v = 2;
+                g = g2;
+            }
+        }
     } else if (v == 0) {
         v = 2;
         while (32 * v * g < max_lane && v < 8) v <<= 1;
@@ -154,7 +170,7 @@ static int prepare(idm_ctx *c, const idm_scene_t *sc, const idm_params_t *pr, co
             const idm_sim_t *sim, bool need_ckpt, bool need_loss, int obs_stride, Prep *P, cudaStream_t st)
 {
     int rc;
-    if ((rc = pick_shape(c, sc->max_lane, &P->vpt, &P->G))) return rc;
+    if ((rc = pick_shape(c, sc->max_lane, sc->n_vehicles, sc->n_lanes, &P->vpt, &P->G))) return rc;
     const int N = sc->n_vehicles, L = sc->n_lanes;
     const int G = P->G;
     if ((rc = ensure(c, c->seg, sizeof(Seg) * (size_t)L, "segments"))) return rc;
@@ -233,6 +249,8 @@ int forward_grid(idm_ctx *c, Prep *P, int L)
     // 8 vehicles per thread: blocks of up to 12 warps (their register budget,
     // one block per SM); otherwise the context's warps per block
     P->wpb_f = P->vpt_f == 8 ? std::max(G, (12 / G) * G) : std::max(G, (c->wpb / G) * G);
+    // few segments: fewer per block, so that they spread over more SMs
+    P->wpb_f = std::min(P->wpb_f, G * std::max(1, (L + c->n_sm - 1) / c->n_sm));
     const int warps_needed = L * G;  // segments <= lanes
     const int blocks_needed = (warps_needed + P->wpb_f - 1) / P->wpb_f;
     int occ_f = idm::occupancy_blocks(P->vpt_f, G, false, false, false, false, P->wpb_f, 0);
@@ -291,6 +309,7 @@ int backward_grid(idm_ctx *c, Prep *P, bool dense, bool adam, bool want_delta, i
     const size_t per_group = idm::backward_smem_bytes(P->vpt, dense, T, G, G, pf);
     int groups = std::max(1, std::min(c->wpb / G, (int)(smem_max / per_group)));
     groups = std::max(1, std::min(groups, idm::backward_max_warps(P->vpt, G) / G));
+    groups = std::min(groups, std::max(1, (L + c->n_sm - 1) / c->n_sm));  // few segments: spread over the SMs
     P->wpb_b = groups * G;
     size_t smem = per_group * groups;
     int occ_b = idm::occupancy_blocks(P->vpt, G, true, dense, adam, want_delta, P->wpb_b, smem, T < C);

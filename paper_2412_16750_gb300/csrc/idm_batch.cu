@@ -140,7 +140,7 @@ int prepare_batch(idm_ctx *c, const idm_batch_t *b, const idm_params_t *pr, cons
     for (int l = 0; l < b->n_lanes; ++l) max_lane = std::max(max_lane, b->lane_off_host[l + 1] - b->lane_off_host[l]);
     if (max_lane > idm_max_lane_supported())
         return fail(c, IDM_ERR_ARG, "a lane has %d vehicles, more than %d", max_lane, idm_max_lane_supported());
-    if ((rc = pick_shape(c, max_lane, &Pp->vpt, &Pp->G))) return rc;
+    if ((rc = pick_shape(c, max_lane, b->n_vehicles, b->n_lanes, &Pp->vpt, &Pp->G))) return rc;
     const int G = Pp->G;
     // the checkpoint interval, at most the longest horizon (same segments,
     // shallower adjoint tape)

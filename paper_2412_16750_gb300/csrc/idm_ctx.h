@@ -78,7 +78,10 @@ constexpr size_t STATUS_BYTES = 32;
 constexpr size_t STATUS_EVENTS_OFF = 16;
 // Event counters for a forward launch of this context (NULL when off).
 unsigned long long *event_counters(idm_ctx *c);
-int pick_shape(idm_ctx *c, int max_lane, int *vpt, int *G);
+// Kernel shape for a call: the context's request, else 4 x 4 (8 x 4, 8 x 8
+// for longer lanes), or for a scene that fits one wave of 2-vehicle warps
+// the latency shape 2 x G.
+int pick_shape(idm_ctx *c, int max_lane, long long n_vehicles, int n_lanes, int *vpt, int *G);
 // Forward shape for the segment capacity of the adjoint shape (vpt, G).
 void forward_shape(int vpt, int G, int *vpt_f, int *G_f);
 // Parameter arrays: required unless the scene has no vehicles.

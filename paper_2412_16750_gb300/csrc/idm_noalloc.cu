@@ -109,7 +109,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
                                      int32_t obs_stride, double *loss_out, idm_params_t *grad, float *grad_p_init,
                                      float *grad_v_init, uint32_t *status_out, void *stream)
 {
-    // launch plan with the default kernel shape; a stack context provides
+    // launch plan with the context-free default kernel shape; a stack context provides
     // the argument checks and the planning helpers and is never allowed to
     // allocate (its ensure() fails instead)
     idm_ctx c;
@@ -126,7 +126,7 @@ extern "C" int idm_loss_grad_noalloc(const idm_scene_t *sc, const idm_params_t *
         cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess)
         return IDM_ERR_CUDA;
     Prep P;
-    if ((rc = pick_shape(&c, sc->max_lane, &P.vpt, &P.G))) return rc;
+    if ((rc = pick_shape(&c, sc->max_lane, sc->n_vehicles, sc->n_lanes, &P.vpt, &P.G))) return rc;
     const size_t N = (size_t)sc->n_vehicles, L = (size_t)sc->n_lanes;
     const int G = P.G;
     const int C = std::min(c.C, sim->K);  // as idm_loss_grad: at most the horizon

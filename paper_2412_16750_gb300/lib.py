@@ -449,7 +449,12 @@ def make_scene(lane_off, length, max_lane):
 
 
 def make_params(theta):
-    """theta: float32 CUDA tensor (6, N), rows v0, T, s0, a_max, b, delta (contiguous rows)."""
+    """theta: float32 CUDA tensor (6, N), rows v0, T, s0, a_max, b, delta (contiguous rows).
+    The row pointers come from the base pointer and the row stride (no row
+    views are created: six views cost tens of microseconds per call)."""
+    if theta.dim() == 2 and theta.stride(1) == 1:
+        base, step = theta.data_ptr(), theta.stride(0) * theta.element_size()
+        return idm_params_t(*[base + q * step for q in range(6)])
     return idm_params_t(*[theta[q].data_ptr() for q in range(6)])
 
 
