@@ -162,18 +162,20 @@ struct State2 {
 };
 
 // Explicit Euler step (Eq. 3): positions use the old speeds, so the gap moves
-// by dt (vh - v).  The position is accumulated with TwoSum plus the exact
-// rounding error of dt*v (en = d - dt*v, so the error is -en) and the speed's
-// compensation (-dt vc), keeping ph + pl within ~1e-10 relative of the sum of
-// dt times the speeds.  The speed takes dt a* by Kahan's compensated
-// summation.
+// by dt (vh - v).  The position is accumulated with Dekker's Fast2Sum plus
+// the exact rounding error of dt*v (en = d - dt*v, so the error is -en) and
+// the speed's compensation (-dt vc), keeping ph + pl within ~1e-10 relative
+// of the sum of dt times the speeds.  Fast2Sum's error term is exact while
+// |ph| >= |d| (a step is at most a few metres); in the one or two steps in
+// which a vehicle passes within |d| of position 0 it is off by at most half
+// an ulp of the sum (~5e-7 m), three operations fewer per step than TwoSum.
+// The speed takes dt a* by Kahan's compensated summation.
 __device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, f2 vch, float dt)
 {
     const f2 d = mul2(F2(dt), s.v);
     const f2 en = fma2(F2(-dt), s.v, d);
     const f2 t = add2(s.ph, d);
-    const f2 bb = sub2(t, s.ph);
-    const f2 err = add2(sub2(s.ph, sub2(t, bb)), sub2(d, bb));
+    const f2 err = sub2(d, sub2(t, s.ph));
     s.ph = t;
     s.pl = fma2(F2(-dt), s.vc, add2(s.pl, sub2(err, en)));
     s.gap = fma2(F2(dt), add2(sub2(vh, s.v), sub2(s.vc, vch)), s.gap);
