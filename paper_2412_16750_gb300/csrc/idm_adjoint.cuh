@@ -73,7 +73,7 @@ __device__ __forceinline__ void fold_sums(const SimArgs &a, int s_idx, const Grp
 // parameter and moment arrays may alias as far as the compiler knows, so a
 // store would otherwise hold back each later load for a full memory round
 // trip (this epilogue was half of a short-horizon fit iteration).
-template <int NP, bool ADAM, bool WD>
+template <int NP, bool ADAM, bool WD, bool D4>
 __device__ __forceinline__ void segment_epilogue(const SimArgs &a, const Seg &sg, int lane, int wb,
                                                  const VehConst2 (&kc)[NP], const f2 (&sacc)[6][NP],
                                                  const f2 (&lp)[NP], const f2 (&lv)[NP], const bool (&vx)[NP],
@@ -113,7 +113,7 @@ __device__ __forceinline__ void segment_epilogue(const SimArgs &a, const Seg &sg
             }
             const float v0 = tv[0], b = tv[4];
             const float am = c ? kc[p].am.y : kc[p].am.x, cc = c ? kc[p].c.y : kc[p].c.x;
-            const float dl = c ? kc[p].delta.y : kc[p].delta.x;
+            const float dl = D4 ? 4.0f : (c ? kc[p].delta.y : kc[p].delta.x);
             const float A0 = c ? sacc[0][p].y : sacc[0][p].x, A1 = c ? sacc[1][p].y : sacc[1][p].x;
             const float A2 = c ? sacc[2][p].y : sacc[2][p].x, A3 = c ? sacc[3][p].y : sacc[3][p].x;
             const float A4 = c ? sacc[4][p].y : sacc[4][p].x, A5 = c ? sacc[5][p].y : sacc[5][p].x;
@@ -174,9 +174,10 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
 
     // lp, lv: adjoints of position and speed; sacc: the six factored
     // gradient sums of every slot, accumulated in registers over all steps
-    f2 lp[NP], lv[NP], sacc[6][NP];
+    f2 lp[NP], lv[NP], sacc[6][NP], qc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
+        qc[p] = D4 ? mul2(mul2(kc[p].am, F2(4.0f)), kc[p].inv_v0) : F2(0.0f);  // 4 a_max / v0
         lp[p] = F2(0.0f);
         lv[p] = F2(0.0f);
 #pragma unroll
@@ -311,7 +312,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 const int q = 64 * p + 2 * lane;
                 const f2 v = lds2(rv + q);
                 const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
-                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
             }
         }
         for (int s = n - 1; s >= 0; --s) {
@@ -338,7 +339,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     const int q = 64 * p + 2 * lane;
                     const f2 v = lds2(rv + q);
                     const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
-                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
                 }
             }
             float in_p, in_v;
@@ -381,7 +382,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
     }
     if (n_ck > fold_every) fold_sums<NP, WD>(a, s_idx, g, sacc, true, true);
 
-    segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
+    segment_epilogue<NP, ADAM, WD, D4>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {
         const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
         if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;
@@ -415,9 +416,10 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
 
     // lp, lv: adjoints of position and speed; sacc: the six factored
     // gradient sums of every slot, accumulated in registers over all steps
-    f2 lp[NP], lv[NP], sacc[6][NP];
+    f2 lp[NP], lv[NP], sacc[6][NP], qc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
+        qc[p] = D4 ? mul2(mul2(kc[p].am, F2(4.0f)), kc[p].inv_v0) : F2(0.0f);  // 4 a_max / v0
         lp[p] = F2(0.0f);
         lv[p] = F2(0.0f);
 #pragma unroll
@@ -613,7 +615,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 const int q = 64 * p + 2 * lane;
                 const f2 v = lds2(rv + q);
                 const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
-                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
             }
         }
         for (int s = n - 1; s >= 0; --s) {
@@ -640,7 +642,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                     const int q = 64 * p + 2 * lane;
                     const f2 v = lds2(rv + q);
                     const f2 vh = make_float2(wb + q > 0 ? rv[q - 1] : 0.0f, v.x);
-                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min);
+                    J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
                 }
             }
             float in_p, in_v;
@@ -684,7 +686,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
     }
     if (n_ck > fold_every) fold_sums<NP, WD>(a, s_idx, g, sacc, true, true);
 
-    segment_epilogue<NP, ADAM, WD>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
+    segment_epilogue<NP, ADAM, WD, D4>(a, sg, lane, wb, kc, sacc, lp, lv, vx, vy);
     if (!DENSE) {
         const double part = warp_sum_double((double)lsum - (double)lcomp) * (double)sc.inv_nobs;
         if (lane == 0) a.loss_part[(size_t)s_idx * g.G + g.w] = part;

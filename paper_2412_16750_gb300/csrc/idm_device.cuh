@@ -248,9 +248,11 @@ struct AdjJac2 {
     f2 w0n, w0nv, w0nvdv, fa, frd, frdl;
 };
 
+// qc: with D4, the per-vehicle constant 4 a_max / v0 of the free-road term's
+// speed derivative (ignored otherwise).
 template <bool WANT_DELTA, bool D4>
 __device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const VehConst2 &k, float inv_dt,
-                                                float a_min)
+                                                float a_min, f2 qc = F2(0.0f))
 {
     AdjJac2 J;
     const bool fx = gap_raw.x < IDM_GAP_FLOOR, fy = gap_raw.y < IDM_GAP_FLOOR;
@@ -258,8 +260,9 @@ __device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const V
     const f2 dv = sub2(v, vh);
     const f2 s_opt = fma2(v, fma2(dv, k.c, k.T), k.s0);
     const Soft2 s1 = softplus2(s_opt);
-    f2 sig1, sig1n;
-    sigmoid2(s_opt, s1.e, sig1, sig1n);
+    // sigma(s_opt) = exp(s_opt - sp(s_opt)): the exponent is <= 0 and carries
+    // no cancellation of note (sp(x) - x = sp(-x)); no selects on the sign
+    const f2 sig1 = ex2(mul2(sub2(s_opt, s1.sp), F2(LOG2E)));
     const f2 inv_gap = rcp2(gap);
     const f2 z = mul2(s1.sp, inv_gap);
     const f2 r = mul2(v, k.inv_v0);
@@ -288,8 +291,7 @@ __device__ __forceinline__ AdjJac2 adjoint_jac2(f2 v, f2 gap_raw, f2 vh, const V
     G.x = fx ? 0.0f : G.x;
     G.y = fy ? 0.0f : G.y;
     const f2 w0n = mul2(mul2(sig2, Sn), sig1);
-    const f2 dl = D4 ? F2(4.0f) : k.delta;
-    const f2 q = mul2(mul2(k.am, dl), mul2(rdm1, k.inv_v0));    // -d(free term)/dv
+    const f2 q = D4 ? mul2(qc, rdm1) : mul2(mul2(k.am, k.delta), mul2(rdm1, k.inv_v0));  // -d(free term)/dv
     f2 beta_term = mul2(one_m_sig2, F2(inv_dt));
     beta_term.x = bx ? beta_term.x : 0.0f;
     beta_term.y = by ? beta_term.y : 0.0f;
