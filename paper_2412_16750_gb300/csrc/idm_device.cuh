@@ -178,8 +178,6 @@ __device__ __forceinline__ void euler2(State2 &s, f2 a_star, f2 vh, f2 vch, floa
     const f2 err = sub2(d, sub2(t, s.ph));
     s.ph = t;
     s.pl = fma2(F2(-dt), s.vc, add2(s.pl, sub2(err, en)));
-    // (vh - v) first: close speeds subtract exactly, and the compensations
-    // (~1e-6 m/s, below an ulp of the speeds) keep their digits
     s.gap = fma2(F2(dt), add2(sub2(vh, s.v), sub2(s.vc, vch)), s.gap);
     const f2 y = sub2(mul2(F2(dt), a_star), s.vc);
     const f2 tv = add2(s.v, y);
