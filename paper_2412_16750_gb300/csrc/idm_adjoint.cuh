@@ -30,6 +30,12 @@ namespace idm {
 // ---------------------------------------------------------------------------
 constexpr int FOLD_STEPS = GSUM_FOLD_STEPS;
 
+// A compile-time flag passed as a value (to a generic lambda).
+template <bool B>
+struct BoolC {
+    static constexpr bool value = B;
+};
+
 template <int NP, bool WD>
 __device__ __forceinline__ void fold_sums(const SimArgs &a, int s_idx, const Grp &g, f2 (&sacc)[6][NP], bool have,
                                           bool last)
@@ -315,7 +321,10 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
             }
         }
-        for (int s = n - 1; s >= 0; --s) {
+        // one reverse step; the coefficients of step s - 1 are evaluated inside
+        // it (next_j) for every step but the last, which is peeled off so that
+        // the loop body has no branch around them
+        auto reverse_step = [&](const int s, auto next_j) {
             const int k = c0 + s;
             f2 to_lp[NP], to_lv[NP], t1[NP], nlv[NP];
 #pragma unroll
@@ -332,7 +341,7 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 sacc[4][p] = fma2(mu, J[p].frd, sacc[4][p]);
                 if (WD) sacc[5][p] = fma2(mu, J[p].frdl, sacc[5][p]);
             }
-            if (s > 0) {
+            if constexpr (decltype(next_j)::value) {
                 const float *rv = tv + (s - 1) * SLG + wb, *rg = tg + (s - 1) * SLG + wb;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
@@ -374,7 +383,9 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 obs_hi -= sc.obs_stride;
                 --row_hi;
             }
-        }
+        };
+        for (int s = n - 1; s >= 1; --s) reverse_step(s, BoolC<true>{});
+        reverse_step(0, BoolC<false>{});
         // a fold window is fold_every checkpoint segments, counted from the last
         if (cs > 0 && (n_ck - cs) % fold_every == 0)
             fold_sums<NP, WD>(a, s_idx, g, sacc, n_ck - cs > fold_every, false);
@@ -618,7 +629,10 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 J[p] = adjoint_jac2<WD, D4>(v, lds2(rg + q), vh, kc[p], sc.inv_dt, sc.a_min, qc[p]);
             }
         }
-        for (int s = n - 1; s >= 0; --s) {
+        // one reverse step; the coefficients of step s - 1 are evaluated inside
+        // it (next_j) for every step but the last, which is peeled off so that
+        // the loop body has no branch around them
+        auto reverse_step = [&](const int s, auto next_j) {
             const int k = c0 + s;
             f2 to_lp[NP], to_lv[NP], t1[NP], nlv[NP];
 #pragma unroll
@@ -635,7 +649,7 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 sacc[4][p] = fma2(mu, J[p].frd, sacc[4][p]);
                 if (WD) sacc[5][p] = fma2(mu, J[p].frdl, sacc[5][p]);
             }
-            if (s > 0) {
+            if constexpr (decltype(next_j)::value) {
                 const float *rv = tv + (s - 1) * SLG + wb, *rg = tg + (s - 1) * SLG + wb;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
@@ -677,7 +691,9 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 obs_hi -= sc.obs_stride;
                 --row_hi;
             }
-        }
+        };
+        for (int s = n - 1; s >= 1; --s) reverse_step(s, BoolC<true>{});
+        reverse_step(0, BoolC<false>{});
         grp_sync(g);  // the tape may be overwritten by the next block
         if (a.bwd_pf) par ^= 1;
       }
