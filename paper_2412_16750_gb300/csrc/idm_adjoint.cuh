@@ -248,8 +248,12 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
         }
         if (a.bwd_pf && cs > 0) prefetch_segment(cs - 1);  // lands while this segment runs
         f2 lseg = F2(0.0f);
-        // recompute the segment into the tape
-        for (int s = 0; s < n; ++s) {
+        // recompute the segment into the tape.  The observation handling has no
+        // branch (an unobserved step's residual, read from a row the copies
+        // did not fill, is selected to 0), and the last step is peeled off:
+        // the state after it is needed only at the end of the horizon (the
+        // seed of step K)
+        auto recompute_step = [&](const int s, const bool advance) {
             const int k = c0 + s;
             float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
 #pragma unroll
@@ -258,26 +262,26 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                 sts2(rv + q, st[p].v);
                 sts2(rg + q, st[p].gap);
             }
-            if (!DENSE && k == obs_k) {
-                if (obs_row < sc.n_obs) {
-                    float *rr = tr + s * SLG + wb;
+            if constexpr (!DENSE) {
+                const bool hit = k == obs_k;
+                const bool obs = hit && obs_row < sc.n_obs;
+                float *rr = tr + s * SLG + wb;
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const int q = 64 * p + 2 * lane;
-                        f2 r = residual2(st[p], lds2(rr + q));
-                        r.x = vx[p] ? r.x : 0.0f;
-                        r.y = vy[p] ? r.y : 0.0f;
-                        sts2(rr + q, mul2(seed_scale, r));
-                        lseg = fma2(r, r, lseg);
-                    }
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    f2 r = residual2(st[p], lds2(rr + q));
+                    r.x = obs && vx[p] ? r.x : 0.0f;
+                    r.y = obs && vy[p] ? r.y : 0.0f;
+                    sts2(rr + q, mul2(seed_scale, r));
+                    lseg = fma2(r, r, lseg);
                 }
-                obs_k += sc.obs_stride;
-                ++obs_row;
+                obs_k += hit ? sc.obs_stride : 0;
+                obs_row += hit ? 1 : 0;
             }
-            // the state after the segment's last step is needed only at the
-            // end of the horizon (the seed of step K)
-            if (s + 1 < n || cs == n_ck - 1) step_pairs<NP, D4>(g, st, kc, sc, xp);
-        }
+            if (advance) step_pairs<NP, D4>(g, st, kc, sc, xp);
+        };
+        for (int s = 0; s + 1 < n; ++s) recompute_step(s, true);
+        recompute_step(n - 1, cs == n_ck - 1);
         if (cs == n_ck - 1) {  // state is now at step K: seed of the final step
             if (DENSE) {
                 const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
@@ -365,23 +369,21 @@ __device__ __forceinline__ void backward_segment(const SimArgs &a, const ScenDes
                     lv[p] = add2(nlv[p], from_v[p]);
                     if (a.gV) lv[p] = add2(lv[p], load_pair(a.gV + row, q, vx[p], vy[p]));
                 }
-            } else if (k == obs_hi && k >= 1 && row_hi <= sc.n_obs) {
+            } else {
+                // the step's seed, selected to 0 where the step is not observed
+                const bool hit = k == obs_hi;
+                const bool on = hit && k >= 1 && row_hi <= sc.n_obs;
                 const float *rr = tr + s * SLG + wb;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    lp[p] = add2(add2(t1[p], from_p[p]), lds2(rr + 64 * p + 2 * lane));
+                    f2 sd = lds2(rr + 64 * p + 2 * lane);
+                    sd.x = on ? sd.x : 0.0f;
+                    sd.y = on ? sd.y : 0.0f;
+                    lp[p] = add2(add2(t1[p], from_p[p]), sd);
                     lv[p] = add2(nlv[p], from_v[p]);
                 }
-            } else {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    lp[p] = add2(t1[p], from_p[p]);
-                    lv[p] = add2(nlv[p], from_v[p]);
-                }
-            }
-            if (!DENSE && k == obs_hi) {
-                obs_hi -= sc.obs_stride;
-                --row_hi;
+                obs_hi -= hit ? sc.obs_stride : 0;
+                row_hi -= hit ? 1 : 0;
             }
         };
         for (int s = n - 1; s >= 1; --s) reverse_step(s, BoolC<true>{});
@@ -558,8 +560,12 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
             }
         }
         f2 lseg = F2(0.0f);
-        // recompute the segment into the tape
-        for (int s = 0; s < n; ++s) {
+        // recompute the segment into the tape.  The observation handling has no
+        // branch (an unobserved step's residual, read from a row the copies
+        // did not fill, is selected to 0), and the last step is peeled off:
+        // the state after it is needed only at the end of the horizon (the
+        // seed of step K)
+        auto recompute_step = [&](const int s, const bool advance) {
             const int k = c0 + s;
             float *rv = tv + s * SLG + wb, *rg = tg + s * SLG + wb;
 #pragma unroll
@@ -568,24 +574,26 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                 sts2(rv + q, st[p].v);
                 sts2(rg + q, st[p].gap);
             }
-            if (!DENSE && k == obs_k) {
-                if (obs_row < sc.n_obs) {
-                    float *rr = tr + s * SLG + wb;
+            if constexpr (!DENSE) {
+                const bool hit = k == obs_k;
+                const bool obs = hit && obs_row < sc.n_obs;
+                float *rr = tr + s * SLG + wb;
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const int q = 64 * p + 2 * lane;
-                        f2 r = residual2(st[p], lds2(rr + q));
-                        r.x = vx[p] ? r.x : 0.0f;
-                        r.y = vy[p] ? r.y : 0.0f;
-                        sts2(rr + q, mul2(seed_scale, r));
-                        lseg = fma2(r, r, lseg);
-                    }
+                for (int p = 0; p < NP; ++p) {
+                    const int q = 64 * p + 2 * lane;
+                    f2 r = residual2(st[p], lds2(rr + q));
+                    r.x = obs && vx[p] ? r.x : 0.0f;
+                    r.y = obs && vy[p] ? r.y : 0.0f;
+                    sts2(rr + q, mul2(seed_scale, r));
+                    lseg = fma2(r, r, lseg);
                 }
-                obs_k += sc.obs_stride;
-                ++obs_row;
+                obs_k += hit ? sc.obs_stride : 0;
+                obs_row += hit ? 1 : 0;
             }
-            if (s + 1 < n || c0 + n == sc.K) step_pairs<NP, D4>(g, st, kc, sc, xp);
-        }
+            if (advance) step_pairs<NP, D4>(g, st, kc, sc, xp);
+        };
+        for (int s = 0; s + 1 < n; ++s) recompute_step(s, true);
+        recompute_step(n - 1, c0 + n == sc.K);
         if (c0 + n == sc.K) {  // state is now at step K: seed of the final step
             if (DENSE) {
                 const size_t row = sc.traj_off + (size_t)sc.K * Ns + wl;
@@ -673,23 +681,21 @@ __device__ __forceinline__ void backward_segment_blocks(const SimArgs &a, const 
                     lv[p] = add2(nlv[p], from_v[p]);
                     if (a.gV) lv[p] = add2(lv[p], load_pair(a.gV + row, q, vx[p], vy[p]));
                 }
-            } else if (k == obs_hi && k >= 1 && row_hi <= sc.n_obs) {
+            } else {
+                // the step's seed, selected to 0 where the step is not observed
+                const bool hit = k == obs_hi;
+                const bool on = hit && k >= 1 && row_hi <= sc.n_obs;
                 const float *rr = tr + s * SLG + wb;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    lp[p] = add2(add2(t1[p], from_p[p]), lds2(rr + 64 * p + 2 * lane));
+                    f2 sd = lds2(rr + 64 * p + 2 * lane);
+                    sd.x = on ? sd.x : 0.0f;
+                    sd.y = on ? sd.y : 0.0f;
+                    lp[p] = add2(add2(t1[p], from_p[p]), sd);
                     lv[p] = add2(nlv[p], from_v[p]);
                 }
-            } else {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    lp[p] = add2(t1[p], from_p[p]);
-                    lv[p] = add2(nlv[p], from_v[p]);
-                }
-            }
-            if (!DENSE && k == obs_hi) {
-                obs_hi -= sc.obs_stride;
-                --row_hi;
+                obs_hi -= hit ? sc.obs_stride : 0;
+                row_hi -= hit ? 1 : 0;
             }
         };
         for (int s = n - 1; s >= 1; --s) reverse_step(s, BoolC<true>{});
