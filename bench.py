@@ -312,15 +312,21 @@ def adjoint_roofline(N, K, ckpt, bwd_avg_ms, n_sm, peaks, peak_kind):
 def run_e2e(a, e2e_steps, step, barrier, max_over_ranks, stream, dev, u_lane, u_p, u_v, u_len, u_th, u_Y, s_th,
             hist, h, lib):
     """Time e2e_steps steps whose inputs start in pinned host memory and whose
-    fitted parameters and loss history end in pinned host memory."""
+    fitted parameters and loss history end in pinned host memory.  The inputs
+    of step i + 1 are copied on a second stream into the other of two device
+    buffers while step i computes (a copy waits until the step two back has
+    released its buffer; a step waits for its own copy); every copy is inside
+    the timed region."""
     import torch
     h_lane = u_lane.cpu().pin_memory()
     h_p, h_v, h_len = u_p.cpu().pin_memory(), u_v.cpu().pin_memory(), u_len.cpu().pin_memory()
     h_th = u_th.cpu().pin_memory()
     h_Y = u_Y.cpu().pin_memory()
-    d_lane, d_p, d_v, d_len = torch.empty_like(u_lane), torch.empty_like(u_p), torch.empty_like(u_v), \
-        torch.empty_like(u_len)
-    d_th, d_Y = torch.empty_like(u_th), torch.empty_like(u_Y)
+    srcs = (h_lane, h_p, h_v, h_len, h_th, h_Y)
+    bufs = [tuple(torch.empty_like(t) for t in (u_lane, u_p, u_v, u_len, u_th, u_Y)) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
     out_th = torch.empty(s_th.shape).pin_memory()
     out_hist = torch.empty(hist.shape, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in (h_lane, h_p, h_v, h_len, h_th, h_Y))
@@ -331,17 +337,31 @@ def run_e2e(a, e2e_steps, step, barrier, max_over_ranks, stream, dev, u_lane, u_
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    for _ in range(e2e_steps):
-        for dst, src in ((d_lane, h_lane), (d_p, h_p), (d_v, h_v), (d_len, h_len), (d_th, h_th), (d_Y, h_Y)):
-            dst.copy_(src, non_blocking=True)
-        step(d_lane, d_p, d_v, d_len, d_th, d_Y)
+    copy_stream.wait_event(e2)  # no copy starts before the timed region
+
+    def issue_copy(i):
+        b = i % 2
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(free[b])  # the step two back is done with buffer b
+            for dst, src in zip(bufs[b], srcs):
+                dst.copy_(src, non_blocking=True)
+            ready[b].record(copy_stream)
+
+    issue_copy(0)
+    for i in range(e2e_steps):
+        b = i % 2
+        if i + 1 < e2e_steps:
+            issue_copy(i + 1)
+        stream.wait_event(ready[b])
+        step(*bufs[b])
+        free[b].record(stream)
         out_th.copy_(s_th, non_blocking=True)
         out_hist.copy_(hist, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms = max_over_ranks(e2.elapsed_time(e3))
-    del h_Y, d_Y
+    del h_Y, bufs
     return ms, h2d, d2h
 
 
