@@ -636,8 +636,8 @@ cudaError_t a_tensor_map(const GemmArgs &g, CUtensorMap *tm)
 {
     const EncodeTiled encode = encoder();
     if (!encode) return cudaErrorNotSupported;
-    // the row pitch and the 16-byte boxes need K % 8 == 0 and a 16-byte
-    // aligned base; an empty A has no rows to describe
+    // the row pitch must be a multiple of 16 bytes (K % 8 == 0) and the base
+    // 16-byte aligned; an empty A has no rows to describe
     if (g.K % 8 != 0 || g.M_valid < 1 || (reinterpret_cast<uintptr_t>(g.A) & 15u) != 0) return cudaErrorInvalidValue;
     const cuuint64_t dims[2] = {(cuuint64_t)g.K, (cuuint64_t)g.M_valid};
     const cuuint64_t strides[1] = {(cuuint64_t)g.K * sizeof(bf16)};
