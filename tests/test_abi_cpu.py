@@ -84,3 +84,23 @@ def test_missing_library_fails_loudly(tmp_path):
             lib.load(str(tmp_path / "nope.so"))
     finally:
         lib._lib = saved
+
+
+def test_param_row_pointers_without_views():
+    """make_params builds the six row pointers from the base pointer and the
+    row stride; they equal the rows' own data pointers, also for a (6, N)
+    slice of a wider tensor, and a tensor whose rows are not contiguous falls
+    back to the rows' pointers."""
+    import torch
+    from paper_2412_16750_gb300 import lib
+
+    def rows(s):
+        return [getattr(s, f[0]) for f in s._fields_]
+
+    t = torch.zeros(6, 1000)
+    assert rows(lib.make_params(t)) == [t[q].data_ptr() for q in range(6)]
+    wide = torch.zeros(6, 1500)
+    sl = wide[:, 100:1100]
+    assert rows(lib.make_params(sl)) == [sl[q].data_ptr() for q in range(6)]
+    tr = torch.zeros(1000, 6).t()  # rows with stride 6
+    assert rows(lib.make_params(tr)) == [tr[q].data_ptr() for q in range(6)]
