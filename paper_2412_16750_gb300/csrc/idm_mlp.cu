@@ -61,7 +61,6 @@ struct GemmArgs {
     float lo[OUT], hi[OUT];
     unsigned *status;
     int stages;          // A stages of the persistent kernel
-    int tma_h;           // persistent kernel: H leaves through TMA stores of 32 x 64 boxes
     unsigned wait_iters; // polls per tensor-core wait before giving up (tc::WAIT_ITERS normally)
 };
 
@@ -157,11 +156,9 @@ __device__ __forceinline__ double warp_sum(double x)
 }
 
 // 16 accumulator columns [n, n + 16) of row r after the tensor-memory load.
-// With hpack set the bf16 outputs go to hpack[0..7] (column pairs, low half
-// first) instead of to H (the caller stages them for a TMA store).
 template <int MODE>
 __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, int split, const float *bias,
-                                               float (&v)[16], uint32_t *hpack = nullptr)
+                                               float (&v)[16])
 {
     const bool row_ok = r < g.M_rows;
     if (MODE == F32_PART) {
@@ -211,15 +208,8 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, 
             h[i + 1] = gg.y;
         }
     }
-    if (hpack) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(h[2 * i], h[2 * i + 1]);
-            hpack[i] = *reinterpret_cast<const uint32_t *>(&b2);
-        }
-    }
     if (row_ok) {
-        if (g.H && !hpack) store16_bf16(g.H + (size_t)r * g.N + n, h);
+        if (g.H) store16_bf16(g.H + (size_t)r * g.N + n, h);
         if (g.HT) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) g.HT[(size_t)(n + i) * g.ldt + r] = __float2bfloat16_rn(h[i]);
@@ -231,13 +221,9 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, int r, int n, 
 // memory address of this row's column 0 of the tile, columns [c0, c1) of the
 // tile (global column n0 + c), split = K-split index (F32_PART), loss_slot =
 // this warp's loss partial (OUT_TRAIN, written by lane 0).
-// stage / tmH (persistent kernel with g.tma_h): this warp's 1024-byte
-// aligned staging box and the tensor map of H; the warp's rows are
-// r - lane .. r - lane + 31 and [c0, c1) is whole 64-column boxes.
 template <int MODE>
 __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t tw, int n0, int c0, int c1, bool empty,
-                                             int split, int loss_slot, const float *bias, uint32_t stage = 0,
-                                             const void *tmH = nullptr)
+                                             int split, int loss_slot, const float *bias)
 {
     const bool row_ok = r < g.M_rows;
     if constexpr (MODE == OUT_TRAIN || MODE == OUT_INFER) {
@@ -283,40 +269,6 @@ __device__ __forceinline__ void epilogue_row(const GemmArgs &g, int r, uint32_t 
         l = warp_sum(l);
         if ((threadIdx.x & 31) == 0) g.loss_part[loss_slot] = l * (double)g.scale;
     } else {
-        if constexpr (MODE == GELU_FWD || MODE == DGELU) {
-            if (stage) {
-                // 64 columns at a time: bf16 results packed in registers, written
-                // to the staging box in the 128-byte swizzled order of the TMA
-                // map (16-byte chunk j of row l at chunk j ^ (l & 7): no bank
-                // conflicts), then one TMA store per box
-                const int lane = threadIdx.x & 31;
-                for (int c = c0; c < c1; c += 64) {
-                    float w[64];
-                    tc::tmem_ld64(tw + (uint32_t)c, w);
-                    uint32_t pk[32];
-#pragma unroll
-                    for (int part = 0; part < 4; ++part) {
-                        float v[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = w[16 * part + i];
-                        epilogue_chunk<MODE>(g, r, n0 + c + 16 * part, split, bias, v, pk + 8 * part);
-                    }
-                    if (lane == 0) tc::bulk_wait_read();  // the previous box has left the staging buffer
-                    __syncwarp();
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const uint32_t a = stage + (uint32_t)lane * 128u + (uint32_t)((j ^ (lane & 7)) << 4);
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(pk[4 * j]),
-                                     "r"(pk[4 * j + 1]), "r"(pk[4 * j + 2]), "r"(pk[4 * j + 3])
-                                     : "memory");
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the TMA unit
-                    __syncwarp();
-                    if (lane == 0) tc::tma_store_2d(tmH, n0 + c, r - lane, stage);
-                }
-                return;
-            }
-        }
         // 64 columns per tensor-memory load where the range allows, else 16
         for (int c = c0; c < c1;) {
             if (c + 64 <= c1) {
@@ -424,29 +376,20 @@ constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int CTL_BYTES = 8 * (2 * MAX_STAGES + 6) + 16;
 constexpr int SMEM_LIMIT = 227 * 1024;
 __host__ __device__ constexpr int w_bytes(int N, int K) { return N * K * 2; }
-// Output staging for TMA stores of the bf16 activations: per epilogue warp
-// one box of 32 rows x 64 columns (128 bytes, 128-byte swizzle), right after
-// the A stages (1024-byte aligned like them).
-constexpr int STG_BOX_BYTES = 32 * 128;
-__host__ __device__ constexpr int stg_bytes(bool tma_out) { return tma_out ? EPI_WARPS * STG_BOX_BYTES : 0; }
 // A stages that fit beside the resident weights (at least 2); nbias = the
 // staged bias floats
-__host__ __device__ inline int max_stages(int N, int K, int nbias, bool tma_out)
+__host__ __device__ inline int max_stages(int N, int K, int nbias)
 {
-    const int s = (SMEM_LIMIT - w_bytes(N, K) - 1024 - CTL_BYTES - 4 * nbias - stg_bytes(tma_out)) / tc::A_STAGE_BYTES;
+    const int s = (SMEM_LIMIT - w_bytes(N, K) - 1024 - CTL_BYTES - 4 * nbias) / tc::A_STAGE_BYTES;
     return s < 2 ? 2 : (s > MAX_STAGES ? MAX_STAGES : s);
 }
-__host__ __device__ inline int stg_off(int N, int K, int S) { return w_bytes(N, K) + 1024 + S * tc::A_STAGE_BYTES; }
-__host__ __device__ inline int ctl_off(int N, int K, int S, bool tma_out)
-{
-    return stg_off(N, K, S) + stg_bytes(tma_out);
-}
-__host__ __device__ inline int smem_bytes(int N, int K, int S, bool tma_out) { return ctl_off(N, K, S, tma_out) + CTL_BYTES; }
+__host__ __device__ inline int ctl_off(int N, int K, int S) { return w_bytes(N, K) + 1024 + S * tc::A_STAGE_BYTES; }
+__host__ __device__ inline int smem_bytes(int N, int K, int S) { return ctl_off(N, K, S) + CTL_BYTES; }
 }  // namespace ws
 
 template <int MODE>
 __global__ void __launch_bounds__(ws::NTHREADS, 1)
-    mlp_gemm_ws_kernel(const GemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmH)
+    mlp_gemm_ws_kernel(const GemmArgs g, const __grid_constant__ CUtensorMap tmA)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     // this CTA's columns: [n0, n0 + N) of the product (N = g.BN, the width
@@ -459,7 +402,7 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
     // 1 KB of slack for the rounding
     const uint32_t sW = tc::smem_u32(smem), sA = (sW + (uint32_t)ws::w_bytes(N, K) + 1023u) & ~1023u;
     const int S = g.stages;
-    uint8_t *ctl = smem + ws::ctl_off(N, K, S, g.tma_h != 0);
+    uint8_t *ctl = smem + ws::ctl_off(N, K, S);
     const uint32_t bars = tc::smem_u32(ctl);
     auto full_bar = [&](int s) { return bars + 8u * s; };
     auto empty_bar = [&](int s) { return bars + 8u * (ws::MAX_STAGES + s); };
@@ -578,13 +521,10 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
         const int c0 = 16 * ((nch * part) / nparts), c1 = 16 * ((nch * (part + 1)) / nparts);
         const bool out_mode = MODE == OUT_TRAIN || MODE == OUT_INFER;
         // the bias, once per CTA, in shared memory (read as broadcasts)
-        float *bias_s = reinterpret_cast<float *>(smem + ws::smem_bytes(N, K, S, g.tma_h != 0));  // all g.N columns
+        float *bias_s = reinterpret_cast<float *>(smem + ws::smem_bytes(N, K, S));  // all g.N columns
         if (g.bias)
             for (int c = threadIdx.x - 64; c < g.N; c += 32 * ws::EPI_WARPS) bias_s[c] = g.bias[c];
         asm volatile("bar.sync 1, %0;" ::"n"(32 * ws::EPI_WARPS) : "memory");
-        // this warp's staging box for the TMA stores of H (0: direct stores)
-        const uint32_t stg =
-            g.tma_h ? sA + (uint32_t)(S * tc::A_STAGE_BYTES) + (uint32_t)((warp - 2) * ws::STG_BOX_BYTES) : 0u;
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i & 1, u = i >> 1;
@@ -595,13 +535,11 @@ __global__ void __launch_bounds__(ws::NTHREADS, 1)
             const uint32_t tw = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)acc * acc_cols;
             const int r = tile * tc::BM + quarter * 32 + lane;
             if (out_mode ? part == 0 : c1 > c0)
-                epilogue_row<MODE>(g, r, tw, n0, c0, c1, false, 0, tile * 4 + quarter, bias_s, stg, &tmH);
+                epilogue_row<MODE>(g, r, tw, n0, c0, c1, false, 0, tile * 4 + quarter, bias_s);
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tempty_bar(acc));
         }
-        if (stg && lane == 0) tc::bulk_wait_all();  // this warp's TMA stores have completed
-        __syncwarp();
     }
     if (threadIdx.x == 0 && *abort) atomicOr(g.status, IDM_STATUS_TIMEOUT);
     tc::fence_before_sync();
@@ -649,24 +587,6 @@ cudaError_t a_tensor_map(const GemmArgs &g, CUtensorMap *tm)
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Tensor map of the output H [M_rows x N] bf16 row-major for the epilogue's
-// TMA stores: boxes of 64 columns (128 bytes) x 32 rows, 128-byte swizzle
-// (the staging order of epilogue_row), rows past M_rows not written.
-cudaError_t h_tensor_map(const GemmArgs &g, CUtensorMap *tm)
-{
-    const EncodeTiled encode = encoder();
-    if (!encode) return cudaErrorNotSupported;
-    if (g.N % 64 != 0 || g.M_rows < 1 || (reinterpret_cast<uintptr_t>(g.H) & 15u) != 0) return cudaErrorInvalidValue;
-    const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M_rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)g.N * sizeof(bf16)};
-    const cuuint32_t box[2] = {64, 32};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.H, dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 // Launch of the persistent GEMM: CTAs keep column slices of nsplit equal
 // parts of the weights; each walks row tiles (grid x) of its slice (grid y).
 template <int MODE>
@@ -676,12 +596,9 @@ cudaError_t gemm_ws(const GemmArgs &g0, int n_sm, int nsplit, cudaStream_t st)
     g.BN = g.N / nsplit;
     // with split columns every CTA has few row tiles: 4 stages (a whole
     // K = 256 tile) leave room for a second resident CTA
-    // the activations leave through TMA stores when each epilogue warp's
-    // column share (half the slice) is whole 64-column boxes
-    g.tma_h = (MODE == GELU_FWD || MODE == DGELU) && g.H != nullptr && (g.BN / 2) % 64 == 0 ? 1 : 0;
-    g.stages = ws::max_stages(g.BN, g.K, g.N, g.tma_h != 0);
+    g.stages = ws::max_stages(g.BN, g.K, g.N);
     if (nsplit > 1 && g.stages > 4) g.stages = 4;
-    const int smem = ws::smem_bytes(g.BN, g.K, g.stages, g.tma_h != 0) + 4 * g.N;  // + the bias
+    const int smem = ws::smem_bytes(g.BN, g.K, g.stages) + 4 * g.N;  // + the bias
     cudaError_t e = cudaFuncSetAttribute(mlp_gemm_ws_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int ntiles = (g.M_rows + tc::BM - 1) / tc::BM;
@@ -693,11 +610,9 @@ cudaError_t gemm_ws(const GemmArgs &g0, int n_sm, int nsplit, cudaStream_t st)
     // (a CTA that cannot allocate would wait for another to finish)
     occ = std::max(1, std::min(occ, (int)(512 / (2 * tc::tmem_cols_for(g.BN)))));
     const int grid = std::max(1, std::min(ntiles, (n_sm * occ + nsplit - 1) / nsplit));
-    CUtensorMap tmA, tmH;
-    memset(&tmH, 0, sizeof tmH);
+    CUtensorMap tmA;
     if ((e = a_tensor_map(g, &tmA)) != cudaSuccess) return e;
-    if (g.tma_h && (e = h_tensor_map(g, &tmH)) != cudaSuccess) return e;
-    mlp_gemm_ws_kernel<MODE><<<dim3(grid, nsplit), ws::NTHREADS, smem, st>>>(g, tmA, tmH);
+    mlp_gemm_ws_kernel<MODE><<<dim3(grid, nsplit), ws::NTHREADS, smem, st>>>(g, tmA);
     return cudaGetLastError();
 }
 
